@@ -1,0 +1,461 @@
+"""Pins for the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: hand-worked
+fixtures from the paper's examples (tests/golden), exact rational arithmetic,
+brute-force enumeration written from the paper's definitions, a library routine
+(scipy's dense ranking), symmetry invariants, and the properties the paper
+proves or reports (no FP / FT, relaxed bound).
+"""
+import itertools
+import math
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from golden_io import grid, ints, load
+from paper_2602_17552_gb300 import synth
+
+R, MIN, SAD, MAX = 0, 1, 2, 3
+
+
+# ------------------------------------------------------------------ helpers
+
+def header_q(buf):
+    h = oracle.header(buf)
+    return h, np.float32(h["w_f"]), np.float32(h["h_f"])
+
+
+def bin_codes(a, buf):
+    """Codes from the stream's own constants, computed here in float32 numpy:
+    q = floor(fl(fl(a * r) + 0.5)) (Section II-C round-half-up)."""
+    h = oracle.header(buf)
+    r = np.float32(h["r_f"])
+    x = (np.asarray(a, np.float32) * r).astype(np.float32)
+    y = (x + np.float32(0.5)).astype(np.float32)
+    return np.floor(y).astype(np.int64)
+
+
+def brute_labels_2d(a):
+    """Section IV-A(1) written out with the paper's t/d/l/r names; corners use two
+    neighbours, edges three; a saddle needs all four."""
+    ny, nx = a.shape
+    out = np.zeros(a.shape, np.uint8)
+    for y in range(ny):
+        for x in range(nx):
+            p = a[y, x]
+            t = a[y - 1, x] if y > 0 else None
+            d = a[y + 1, x] if y + 1 < ny else None
+            l = a[y, x - 1] if x > 0 else None
+            r = a[y, x + 1] if x + 1 < nx else None
+            avail = [v for v in (t, d, l, r) if v is not None]
+            if not avail:
+                continue
+            if all(p < v for v in avail):
+                out[y, x] = MIN
+            elif all(p > v for v in avail):
+                out[y, x] = MAX
+            elif None not in (t, d, l, r) and (
+                    (p < t and p < d and p > l and p > r) or (p > t and p > d and p < l and p < r)):
+                out[y, x] = SAD
+    return out
+
+
+# ----------------------------------------------------------- QZ (Section II-C)
+
+def test_fig2_bins_and_lost_maximum():
+    g = load("fig2_lost_max.txt")
+    a = grid(g["field"], np.float32).astype(np.float32)
+    eps = float(g["eps"])
+    buf = oracle.compress(a, eps, rel=False)
+    assert (bin_codes(a, buf) == grid(g["bins"], int)).all()
+    p = oracle.qparams(a, False, eps)
+    assert (oracle.quantize(a, p).reshape(a.shape) == grid(g["bins"], int)).all()
+    assert (oracle.critical_points(a) == grid(g["labels"], int)).all()
+    out, d0, d1, stats = oracle.decompress(buf, a.shape, stages=True)
+    # QZ^ alone loses the maximum (Fig. 2) ...
+    assert (oracle.critical_points(d0) == grid(g["labels_d0"], int)).all()
+    # ... and the maxima stencil restores it to max_nbr + 1 ulp
+    w = np.float32(oracle.header(buf)["w_f"])
+    assert d0[1, 1] == w
+    assert out[1, 1] == np.nextafter(w, np.float32(np.inf))
+    assert (oracle.critical_points(out) == grid(g["labels"], int)).all()
+    assert abs(float(out[1, 1]) - float(a[1, 1])) <= eps
+
+
+def test_quantizer_is_round_half_up_of_exact_quotient():
+    """q equals floor(a / w + 1/2) in exact rational arithmetic, except within the
+    binary32 rounding distance of a bin boundary."""
+    rng = np.random.default_rng(11)
+    a = np.concatenate([rng.normal(0, 3, 4000), rng.uniform(-1e3, 1e3, 2000)]).astype(np.float32)
+    for eps in (1e-3, 0.37, 2.5):
+        p = oracle.qparams(a, False, eps)
+        q = oracle.quantize(a, p)
+        w = Fraction(float(np.float32(p.w_f)))
+        checked = 0
+        for v, qq in zip(a.tolist(), q.tolist()):
+            t = Fraction(v) / w + Fraction(1, 2)
+            fl = math.floor(t)
+            tol = abs(float(t)) * 2.0 ** -22 + 2.0 ** -20   # binary32 rounding of a*r and +0.5
+            if float(t - fl) < tol or 1 - float(t - fl) < tol:
+                continue        # within rounding distance of a boundary
+            assert qq == fl
+            checked += 1
+        assert checked > 5000
+
+
+@pytest.mark.parametrize("scale", [1.0, 1e3, 1e-6])
+def test_pointwise_bound_exact(scale):
+    """|a - QZ^(QZ(a))| <= eps checked in exact rationals, including values just
+    either side of every bin boundary and the largest |a| the bound admits."""
+    rng = np.random.default_rng(5)
+    eps = 1e-3 * scale
+    base = rng.uniform(-1, 1, 3000) * scale
+    edges = (np.arange(-50, 50) + 0.5) * 2 * eps
+    near = np.concatenate([edges, np.nextafter(edges.astype(np.float32), np.float32(np.inf)),
+                           np.nextafter(edges.astype(np.float32), np.float32(-np.inf))])
+    big = np.array([eps * 2 ** 19.9, -eps * 2 ** 19.9])
+    a = np.concatenate([base, near, big]).astype(np.float32)
+    p = oracle.qparams(a, False, eps)
+    assert p.h_f <= eps and p.h_f >= eps / 2
+    q = oracle.quantize(a, p)
+    ah = oracle.dequantize(q, p)
+    e = Fraction(eps)
+    for v, r in zip(a.tolist(), ah.tolist()):
+        assert abs(Fraction(v) - Fraction(r)) <= e
+
+
+def test_quantizer_monotone():
+    """Section III-B relies on a1 < a2 => a^1 <= a^2; checked on sorted floats."""
+    rng = np.random.default_rng(3)
+    a = np.sort(np.concatenate([rng.normal(0, 10, 20000),
+                                np.linspace(-1, 1, 5001)]).astype(np.float32))
+    for eps in (1e-4, 3e-3, 0.1):
+        p = oracle.qparams(a, False, eps)
+        q = oracle.quantize(a, p)
+        ah = oracle.dequantize(q, p)
+        assert (np.diff(q) >= 0).all()
+        assert (np.diff(ah) >= 0).all()
+
+
+def test_eb_too_small_and_constant_field():
+    a = np.linspace(0, 1e3, 64, dtype=np.float32).reshape(8, 8)
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.compress(a, 1e3 * 2 ** -21, rel=False)
+    assert ei.value.status == oracle.EB_TOO_SMALL
+    c = np.full((5, 7), -3.25, np.float32)
+    buf = oracle.compress(c, 1e-3, rel=True)        # eps = 0 on a constant field
+    assert (oracle.decompress(buf, c.shape) == c).all()
+    bad = a.copy()
+    bad[2, 3] = np.nan
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.compress(bad, 1e-2, rel=True)
+    assert ei.value.status == oracle.NONFINITE
+
+
+# --------------------------------------------------------- CD (Section IV-A(1))
+
+def test_cd_hand_3x3():
+    g = load("h3_cd_3x3.txt")
+    a = grid(g["field"], np.float32).astype(np.float32)
+    assert (oracle.critical_points(a) == grid(g["labels"], int)).all()
+
+
+def test_cd_hand_3x3x3():
+    g = load("h3d_cd_3x3x3.txt")
+    a = np.zeros((3, 3, 3), np.float32)          # [z, y, x]
+    for z, y, x in itertools.product(range(3), repeat=3):
+        odd = (x == 1) + (y == 1) + (z == 1)
+        if odd == 3:
+            a[z, y, x] = 5
+        elif odd == 2:                           # face centre: the axis not at 1
+            a[z, y, x] = 9 if x != 1 else (1 if y != 1 else 2)
+        elif odd == 1:
+            a[z, y, x] = 3
+    want = np.stack([grid(g[f"labels_z{z}"], int) for z in range(3)])
+    assert (oracle.critical_points(a) == want).all()
+
+
+def test_cd_brute_force_all_3x3_over_three_values():
+    """Every 3x3 grid over {0,1,2} (3^9 of them) against the paper's 2D rule."""
+    vals = np.array(list(itertools.product((0.0, 1.0, 2.0), repeat=9)), np.float32)
+    for v in vals:
+        a = v.reshape(3, 3)
+        assert (oracle.critical_points(a) == brute_labels_2d(a)).all()
+
+
+@pytest.mark.parametrize("shape", [(5, 5), (4, 7), (1, 9), (9, 1), (1, 1), (2, 2), (6, 5)])
+def test_cd_brute_force_random(shape):
+    rng = np.random.default_rng(sum(shape))
+    for _ in range(40):
+        a = rng.integers(0, 4, size=shape).astype(np.float32)
+        assert (oracle.critical_points(a) == brute_labels_2d(a)).all()
+
+
+def test_cd_symmetries_3d():
+    """Axis permutations permute the labels; negation swaps m and M; a positive
+    affine map changes nothing -- catches stride, index and sign slips."""
+    rng = np.random.default_rng(9)
+    swap = np.array([R, MAX, SAD, MIN], np.uint8)
+    for shape in [(4, 5, 6), (3, 3, 7), (1, 4, 4)]:
+        a = rng.integers(0, 5, size=shape).astype(np.float32)
+        lab = oracle.critical_points(a)
+        for perm in itertools.permutations(range(3)):
+            b = np.ascontiguousarray(a.transpose(perm))
+            assert (oracle.critical_points(b) == lab.transpose(perm)).all()
+        assert (oracle.critical_points(-a) == swap[lab]).all()
+        assert (oracle.critical_points(3 * a + 7) == lab).all()
+    # 2D transpose
+    a = rng.normal(size=(13, 17)).astype(np.float32)
+    assert (oracle.critical_points(np.ascontiguousarray(a.T)) == oracle.critical_points(a).T).all()
+
+
+def test_no_adjacent_strict_maxima():
+    a = synth.adversarial_small(4, (16, 12, 5)).numpy()
+    lab = oracle.critical_points(a)
+    for ax in range(3):
+        m = lab == MAX
+        sl0 = [slice(None)] * 3
+        sl1 = [slice(None)] * 3
+        sl0[ax] = slice(0, -1)
+        sl1[ax] = slice(1, None)
+        assert not (m[tuple(sl0)] & m[tuple(sl1)]).any()
+
+
+# ----------------------------------------------------------- RP (IV-A(2))
+
+def test_fig5_ranks_and_restored_order():
+    g = load("fig5_rank_order.txt")
+    a = grid(g["field"], np.float32).astype(np.float32)
+    eps = float(g["eps"])
+    lab = oracle.critical_points(a)
+    assert (lab == grid(g["labels"], int)).all()
+    p = oracle.qparams(a, False, eps)
+    assert list(oracle.ranks(a, lab, p)) == ints(g["delta_seq"])
+    out = oracle.decompress(oracle.compress(a, eps, rel=False), a.shape)
+    m1, m2 = out[1, 1], out[1, 5]
+    assert m1 < m2                                # M1 < M2 restored (Fig. 5)
+    assert (oracle.critical_points(out) == lab).all()
+
+
+def test_ranks_match_scipy_dense_rank_per_bin():
+    """RP equals scipy's dense ranking inside each (type, bin) group; maxima
+    ranked upward, minima downward."""
+    from scipy.stats import rankdata
+    a = synth.adversarial_small(7, (40, 30)).numpy()
+    a = a + np.float32(0.01) * synth.gaussian_bumps_2d(30, 40, count=6, seed=2).numpy()
+    a = a.astype(np.float32)
+    lab = oracle.critical_points(a)
+    p = oracle.qparams(a, True, 2e-2)
+    delta = oracle.ranks(a, lab, p)
+    flat, lf = a.ravel(), lab.ravel()
+    q = oracle.quantize(flat, p)
+    want = {}
+    for t in (MIN, MAX):
+        for b in np.unique(q[lf == t]):
+            idx = np.nonzero((lf == t) & (q == b))[0]
+            vals = flat[idx] if t == MAX else -flat[idx]
+            for i, rk in zip(idx, rankdata(vals, method="dense")):
+                want[i] = int(rk)
+    seq = [want[i] for i in np.nonzero((lf == MIN) | (lf == MAX))[0]]
+    assert list(delta) == seq
+    assert delta.min() >= 1 and (delta > 1).any()
+
+
+# ------------------------------------------------ B + LZ + BE (II-C, IV-A)
+
+def test_codec_hand_block():
+    g = load("codec_block.txt")
+    codes = np.array(ints(g["codes"]), np.float32).reshape(1, -1)
+    buf = oracle.compress(codes, float(g["eps"]), rel=False)
+    h = oracle.header(buf)
+    b = np.frombuffer(buf, np.uint8)
+    u32 = lambda off, cnt: np.frombuffer(b[off:off + 4 * cnt].tobytes(), "<u4")
+    assert u32(h["off_s1"], 1)[0] == int(g["const_bitmap_word0"], 0)
+    assert list(b[h["off_s2"]:h["off_s2"] + 2]) == ints(g["widths"])
+    assert list(np.frombuffer(b[h["off_s4"]:h["off_s4"] + 8].tobytes(), "<i4")) == ints(g["firsts"])
+    assert list(u32(h["off_s5"], h["pay_words"])) == ints(g["payload"])
+    assert u32(h["off_s6"], 1)[0] == int(g["labels_word0"], 0)
+    assert h["k_min"] == 1 and h["k_max"] == 1
+    # rank stream: one constant block with first value 1
+    s7 = h["off_s7"]
+    assert u32(s7, 1)[0] == 1
+    w = np.float32(h["w_f"])
+    assert (oracle.decompress(buf, codes.shape) == (codes * w).astype(np.float32)).all()
+
+
+def _expected_size(q, n, topo, k_delta):
+    """Closed-form stream size from the per-block widths (Section IV-A layout)."""
+    def a16(x):
+        return (x + 15) // 16 * 16
+
+    def blocks(seq):
+        nb = -(-len(seq) // 32)
+        pad = np.concatenate([seq, np.repeat(seq[-1:], nb * 32 - len(seq))]) if len(seq) else seq
+        words = 0
+        for b in range(nb):
+            blk = pad[b * 32:(b + 1) * 32].astype(np.int64)
+            d = np.abs(np.diff(blk))
+            w = int(d.max()).bit_length() if d.size else 0
+            words += (1 + w) if w else 0
+        return nb, words
+    nb, words = blocks(q)
+    off = a16(256 + 4 * (-(-nb // 32)))
+    off = a16(off + nb)
+    off = a16(off + 4 * nb)
+    off = a16(off + (4 * (-(-n // 16)) if topo else 0))
+    end = off + 4 * words
+    if topo:
+        nbd, rw = blocks(k_delta)
+        off = a16(end)
+        off = a16(off + 4 * (-(-nbd // 32)))
+        off = a16(off + nbd)
+        off = a16(off + 4 * nbd)
+        end = off + 4 * rw
+    return end
+
+
+@pytest.mark.parametrize("n", [1, 31, 32, 33, 64, 65, 1000])
+def test_codec_roundtrip_and_size_adversarial(n):
+    rng = np.random.default_rng(n)
+    seqs = [np.zeros(n), np.full(n, 7.0),
+            (np.arange(n) % 2) * 2.0 ** 18 - 2.0 ** 17,
+            rng.integers(-2 ** 18, 2 ** 18, n).astype(np.float64),
+            np.cumsum(rng.integers(-3, 4, n)).astype(np.float64)]
+    for s in seqs:
+        a = s.astype(np.float32).reshape(1, n)
+        buf = oracle.compress(a, 0.5, rel=False, no_topo=True)
+        out = oracle.decompress(buf, a.shape)
+        q = bin_codes(a, buf).ravel()
+        if s.min() != s.max() and np.abs(s).max() < 2 ** 16:
+            assert (q == s).all()                        # codes equal the integers at eps = 0.5
+        w = np.float32(oracle.header(buf)["w_f"])
+        assert (out.ravel() == (q.astype(np.float32) * w).astype(np.float32)).all()
+        assert len(buf) == _expected_size(q, n, False, None)
+
+
+def test_stream_size_closed_form_with_topology():
+    a = synth.gaussian_bumps_2d(45, 70, count=12, seed=4).numpy()
+    buf = oracle.compress(a, 1e-3, rel=True)
+    lab = oracle.critical_points(a)
+    p = oracle.qparams(a, True, 1e-3)
+    delta = oracle.ranks(a, lab, p)
+    q = bin_codes(a, buf).ravel()
+    assert len(buf) == _expected_size(q, a.size, True, delta)
+    h = oracle.header(buf)
+    # Section IV-A stream order: const info, block metadata, first elements,
+    # labels (fixed-size sections), then sign+magnitude planes, then ranks
+    offs = [h[k] for k in ("off_s1", "off_s2", "off_s4", "off_s6", "off_s5", "off_s7")]
+    assert offs == sorted(offs) and all(o % 16 == 0 for o in offs)
+
+
+# -------------------------------------------------- decompression (IV-B)
+
+def test_saddle_refinement_hand_case():
+    g = load("h4_saddle.txt")
+    a = grid(g["field"], np.float32).astype(np.float32)
+    eps = float(g["eps"])
+    assert (oracle.critical_points(a) == grid(g["labels"], int)).all()
+    buf = oracle.compress(a, eps, rel=False, rbf_k=3, rbf_sigma=1.0)
+    assert (bin_codes(a, buf) == grid(g["bins"], int)).all()
+    h, w, hf = header_q(buf)
+    out, d0, d1, stats = oracle.decompress(buf, a.shape, stages=True)
+    assert (d0 == grid(g["bins"], int).astype(np.float32) * w).all()
+    assert oracle.critical_points(d0)[2, 2] == R          # saddle lost by QZ^
+    assert (d1 == d0).all()                               # no extrema stencil fires
+    want = d0.copy()
+    want[2, 2] = np.float32(w + np.float32(np.float32(0.1) * hf))
+    assert (out == want).all()
+    assert (oracle.critical_points(out) == grid(g["labels"], int)).all()
+    assert stats[2] == 1
+
+
+def test_exp_neg_against_libm():
+    for t in np.linspace(0, 20, 401):
+        e = oracle.exp_neg(float(t))
+        assert abs(e - math.exp(-t)) <= 1e-12 * math.exp(-t)
+
+
+def test_rbf_weights_in_header():
+    a = synth.gaussian_bumps_2d(40, 40, count=5, seed=8).numpy()
+    buf = oracle.compress(a, 1e-3, rel=True)
+    h = oracle.header(buf)
+    s = float(np.float32(h["rbf_sigma"]))
+    assert 0.5 <= s <= 1.0 and h["rbf_k"] in (3, 5, 7)
+    want = np.array([math.exp(-d2 / (2 * s * s)) for d2 in range(1, 10)], np.float32)
+    assert np.allclose(h["g"], want, rtol=1e-6, atol=0)
+
+
+def _fields_small():
+    yield "bumps", synth.gaussian_bumps_2d(64, 80, count=20, seed=5).numpy()
+    yield "climate", synth.climate_2d(60, 96, seed=2).numpy()
+    yield "turb", synth.turbulence_3d(20, seed=3).numpy()
+    yield "adv2", synth.adversarial_small(1, (33, 17)).numpy()
+    yield "adv3", synth.adversarial_small(2, (9, 8, 7)).numpy()
+
+
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+def test_invariants_no_fp_no_ft_bound(eb):
+    """Section III-B / Table II: TopoSZp output has zero FP and zero FT; lost
+    extrema are all restored unless the bound forbids it (counted); the
+    relaxed bound |a - a'| <= eps + h < 2 eps holds (Table I, eps_topo)."""
+    for name, a in _fields_small():
+        buf = oracle.compress(a, eb, rel=True)
+        h = oracle.header(buf)
+        out, d0, d1, stats = oracle.decompress(buf, a.shape, stages=True)
+        la, lo, l0 = (oracle.critical_points(x) for x in (a, out, d0))
+        err = oracle.topo_errors(la, lo)
+        assert err[1].sum() == 0 and err[2].sum() == 0, (name, err)
+        assert err[0][MIN] + err[0][MAX] == stats[1], (name, err, stats)
+        e0 = oracle.topo_errors(la, l0)
+        assert e0[1].sum() == 0 and e0[2].sum() == 0          # SZp alone: FN only
+        assert err[0].sum() <= e0[0].sum()
+        dev = np.abs(a.astype(np.float64) - out.astype(np.float64)).max()
+        assert dev <= h["eps"] + float(np.float32(h["h_f"])) * (1 + 2 ** -20)
+        assert dev <= 2 * h["eps"]
+        assert np.abs(a.astype(np.float64) - d0).max() <= h["eps"]
+
+
+def test_szp_only_fn_has_same_bin_neighbour():
+    """Section III-B: a critical point can only be lost when a neighbour shares
+    its bin; with the topology layers switched off, FP = FT = 0."""
+    a = synth.climate_2d(50, 80, seed=6).numpy()
+    buf = oracle.compress(a, 1e-2, rel=True, no_topo=True)
+    out = oracle.decompress(buf, a.shape)
+    la, lo = oracle.critical_points(a), oracle.critical_points(out)
+    q = bin_codes(a, buf)
+    e = oracle.topo_errors(la, lo)
+    assert e[1].sum() == 0 and e[2].sum() == 0 and e[0].sum() > 0
+    ny, nx = a.shape
+    for y, x in zip(*np.nonzero((la != R) & (lo == R))):
+        nb = [(y + dy, x + dx) for dy, dx in ((-1, 0), (1, 0), (0, -1), (0, 1))
+              if 0 <= y + dy < ny and 0 <= x + dx < nx]
+        assert any(q[j] == q[y, x] for j in nb)
+
+
+def test_topo_errors_brute_force():
+    rng = np.random.default_rng(1)
+    a = rng.integers(0, 4, 500).astype(np.uint8)
+    b = rng.integers(0, 4, 500).astype(np.uint8)
+    got = oracle.topo_errors(a, b)
+    want = np.zeros((3, 4), np.uint64)
+    for x, y in zip(a, b):
+        if x != y:
+            if y == R:
+                want[0, x] += 1
+            elif x == R:
+                want[1, y] += 1
+            else:
+                want[2, x] += 1
+    assert (got == want).all()
+
+
+def test_corrupt_stream_rejected():
+    a = synth.gaussian_bumps_2d(20, 24, count=4, seed=1).numpy()
+    buf = bytearray(oracle.compress(a, 1e-3, rel=True))
+    for bad in (bytes(buf[:100]), bytes(b"XXXX" + buf[4:])):
+        with pytest.raises(oracle.OracleError):
+            oracle.decompress(bad, a.shape)
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(bytes(buf), (a.shape[0] + 1, a.shape[1]))
