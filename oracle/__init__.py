@@ -71,6 +71,9 @@ def lib():
                                 ctypes.c_void_p]
         L.orc_exp_neg.restype = ctypes.c_double
         L.orc_exp_neg.argtypes = [ctypes.c_double]
+        L.orc_colour.restype = ctypes.c_int
+        L.orc_colour.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                 ctypes.POINTER(ctypes.c_int)]
         L.orc_topo_errors.restype = None
         L.orc_topo_errors.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_uint64, ctypes.c_void_p]
         _lib = L
@@ -148,6 +151,12 @@ def ranks(a, labels, p: QParams) -> np.ndarray:
 
 def exp_neg(t: float) -> float:
     return lib().orc_exp_neg(float(t))
+
+
+def colour(ndim: int, x: int, y: int, z: int = 0):
+    nc = ctypes.c_int(0)
+    c = lib().orc_colour(ndim, x, y, z, ctypes.byref(nc))
+    return c, nc.value
 
 
 def compress_bound(shape) -> int:

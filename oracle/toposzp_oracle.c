@@ -487,6 +487,13 @@ static int step_ulps(float x, int64_t k, float* res) {
 
 typedef struct { uint64_t idx; float v; } upd_t;
 
+/* Colour classes of the saddle rounds: (x + 2y) mod 5 in 2D, (x + 2y + 3z) mod 7
+ * in 3D; returns the number of classes in *ncol. */
+int orc_colour(int ndim, uint64_t x, uint64_t y, uint64_t z, int* ncol) {
+    *ncol = ndim == 2 ? 5 : 7;
+    return (int)((x + 2 * y + (ndim == 3 ? 3 * z : 0)) % (uint64_t)*ncol);
+}
+
 int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
                    float* d0, float* d1, uint64_t stats[4]) {
     if (size < HDR) return ORC_CORRUPT;
@@ -597,7 +604,8 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
      * share a neighbour; all reads use the field at the start of the colour and
      * accepted values are written afterwards (R18). */
     int r = kk / 2;
-    int ncol = ndim == 2 ? 5 : 7;
+    int ncol;
+    orc_colour(ndim, 0, 0, 0, &ncol);
     int rz = ndim == 3 ? r : 0;
     upd_t* upd = (upd_t*)malloc((n + 1) * sizeof(upd_t));
     for (uint32_t sw = 0; sw < sweeps; sw++) {
@@ -606,8 +614,8 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
             for (uint64_t i = 0; i < n; i++) {
                 if (lab[i] != ORC_SAD) continue;
                 uint64_t c[3] = {i % dims[0], (i / dims[0]) % dims[1], i / (dims[0] * dims[1])};
-                uint64_t colour = (c[0] + 2 * c[1] + 3 * c[2]) % (uint64_t)ncol;
-                if ((int)colour != col) continue;
+                int nc;
+                if (orc_colour(ndim, c[0], c[1], c[2], &nc) != col) continue;
                 if (orc_classify(F, ndim, d3, i) == ORC_SAD) continue;   /* not lost */
                 float Fp = F[i];
                 /* tolerance eps_RBF = min(0.1 h, half the smallest nonzero local gap) (R15) */

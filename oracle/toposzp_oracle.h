@@ -48,6 +48,7 @@ void orc_critical_points(const float* a, int ndim, const uint64_t dims[3], uint8
 uint64_t orc_ranks(const float* a, const uint8_t* labels, uint64_t n, const orc_qparams* p,
                    int32_t* delta_seq);
 double orc_exp_neg(double t);                                    /* exp(-t), t >= 0 */
+int orc_colour(int ndim, uint64_t x, uint64_t y, uint64_t z, int* ncol);   /* RS^ rounds */
 
 /* --- whole pipeline --- */
 uint64_t orc_compress_bound(int ndim, const uint64_t dims[3]);

@@ -371,6 +371,26 @@ def test_saddle_refinement_hand_case():
     assert stats[2] == 1
 
 
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_saddle_colouring_is_distance_two(ndim):
+    """Within one colour round no two candidates may share a face neighbour, so
+    every same-colour pair must be at Manhattan distance >= 3 (brute force over a
+    patch larger than the colour period)."""
+    rng = range(9)
+    pts = list(itertools.product(rng, rng, range(9) if ndim == 3 else [0]))
+    col = {p: oracle.colour(ndim, *p) for p in pts}
+    assert {c[1] for c in col.values()} == {5 if ndim == 2 else 7}
+    assert len({c[0] for c in col.values()}) == (5 if ndim == 2 else 7)
+    for p in pts:
+        for dx, dy, dz in itertools.product(range(-2, 3), repeat=3):
+            if ndim == 2 and dz:
+                continue
+            dist = abs(dx) + abs(dy) + abs(dz)
+            q = (p[0] + dx, p[1] + dy, p[2] + dz)
+            if 0 < dist <= 2 and q in col:
+                assert col[q][0] != col[p][0]
+
+
 def test_exp_neg_against_libm():
     for t in np.linspace(0, 20, 401):
         e = oracle.exp_neg(float(t))
