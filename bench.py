@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the TopoSZp hot path on GB300.
+
+One step = compress + decompress of one synthetic field through the C ABI
+(toposzp_compress then toposzp_decompress on one stream, inputs resident in
+HBM).  Prints ONE JSON line (rank 0):
+
+  value      uncompressed bytes of all ranks / max-over-ranks time, GB/s
+             (compress + decompress round trip)
+  roofline   the dominant kernel's algorithmic bytes per launch / its mean
+             launch time (CUDA events recorded by the library between its
+             stages on the launching stream), against the measured HBM copy
+             bandwidth (MEASURED_PEAKS.json)
+  e2e        the same metric through the public Python API with host buffers:
+             pinned host field -> device -> compress -> compressed bytes to host
+             -> device -> decompress -> field to host, copies inside the timing
+  cpu_baseline  the CPU oracle (single thread) on a bounded sample
+
+`--impl reference` times the CPU oracle itself as the reference arm.
+Multi-GPU (torchrun): independent replicas, one field per rank (weak scaling),
+a barrier and a max over ranks for timing only.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NOMINAL_HBM_GBS = 8000.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256"])
+    ap.add_argument("--eb", type=float, default=1e-3)
+    ap.add_argument("--no-topo", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU-baseline work")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload_spec(name, eb):
+    from paper_2602_17552_gb300 import synth
+    if name == "turb512":
+        return synth.turb_512(eb)
+    if name == "climate":
+        return synth.climate_1800x3600(eb)
+    return synth.bumps_256()
+
+
+def describe(spec):
+    if spec.kind == "turb":
+        return (f"3D float32 {spec.dims[0]}^3 turbulence-like log-normal GRF (energy spectrum k^-5/3), "
+                f"relative eb {spec.eb:g}")
+    if spec.kind == "climate":
+        return f"2D float32 1800x3600 climate-like GRF (PSD k^-3), relative eb {spec.eb:g}"
+    return "2D float32 256x256 sum of 40 Gaussian bumps, abs eb 1e-3*(max-min)"
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.rows = []
+        if self.proc is None:
+            return False
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+        return False
+
+    def summary(self):
+        rows = getattr(self, "rows", [])
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0])]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(rows[0][1]), "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((num(r[2]) or 0.0) for r in rows)}
+
+
+# ------------------------------------------------------------ CPU baseline
+
+def cpu_sample(spec, field_cpu, eb_abs_or_rel, seconds):
+    """Time the oracle (compress + decompress) on leading slabs of the field
+    until about `seconds` of single-thread CPU work; returns (GB/s, description)."""
+    import numpy as np
+    import oracle
+    a = field_cpu.numpy()
+    if a.ndim == 3:
+        planes = max(1, min(a.shape[0], 8))
+        sub = np.ascontiguousarray(a[:planes])
+        unit = f"{planes} of {a.shape[0]} z-planes"
+    else:
+        rows = max(1, min(a.shape[0], 200))
+        sub = np.ascontiguousarray(a[:rows])
+        unit = f"{rows} of {a.shape[0]} rows"
+    rel = spec.eb_mode == "rel"
+    eb = spec.eb if rel else eb_abs_or_rel
+    t_total, nbytes, reps = 0.0, 0, 0
+    while t_total < seconds and reps < 1000:
+        t0 = time.perf_counter()
+        buf = oracle.compress(sub, eb, rel=rel)
+        oracle.decompress(buf, sub.shape)
+        t_total += time.perf_counter() - t0
+        nbytes += sub.nbytes
+        reps += 1
+    return nbytes / t_total / 1e9, f"oracle compress+decompress of {unit} ({sub.nbytes / 1e6:.1f} MB) x {reps}", t_total
+
+
+# ------------------------------------------------------------------- main
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    import torch
+    ws, rank, local = dist_setup(args)
+    if rank != 0:
+        return
+    spec = workload_spec(args.workload, args.eb)
+    field = spec.make("cuda" if torch.cuda.is_available() else "cpu").cpu()
+    eb_abs = args.eb * float(field.max() - field.min()) if spec.eb_mode != "rel" else args.eb
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        cpu_sample(spec, field, eb_abs, per_step)
+    vals, descs, tsum = [], None, 0.0
+    for _ in range(args.steps):
+        v, descs, t = cpu_sample(spec, field, eb_abs, per_step)
+        vals.append(v)
+        tsum += t
+    value = statistics.mean(vals)
+    line = {
+        "impl": "reference", "metric": "compress+decompress throughput (uncompressed bytes / round-trip time)",
+        "value": round(value, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * tsum / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": describe(spec), "sample": descs},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": descs},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_2602_17552_gb300 import _lib, codec
+
+    ws_n, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws_n > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    spec = workload_spec(args.workload, args.eb)
+    from dataclasses import replace
+    spec = replace(spec, seed=spec.seed + 1000 * rank)
+    field = spec.make(dev)
+    rel = spec.eb_mode == "rel"
+    eb = args.eb if rel else 1e-3 * float(field.max() - field.min())
+    mode = "rel" if rel else "abs"
+    n = field.numel()
+    L = _lib.load()
+    params = codec.make_params(no_topo=args.no_topo)
+    out = torch.empty(codec.compress_bound(field.shape), dtype=torch.uint8, device=dev)
+    cws = torch.empty(codec.compress_workspace_size(field.shape), dtype=torch.uint8, device=dev)
+    dws = torch.empty(codec.decompress_workspace_size(field.shape), dtype=torch.uint8, device=dev)
+    size = torch.zeros(1, dtype=torch.int64, device=dev)
+    st_c = torch.zeros(1, dtype=torch.int32, device=dev)
+    st_d = torch.zeros(1, dtype=torch.int32, device=dev)
+    rec = torch.empty_like(field)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(events=None):
+        if events is not None:
+            arr = (ctypes.c_void_p * 9)(*[e.cuda_event for e in events])
+            L.toposzp_set_stage_events(arr, 9)
+        codec.compress_async(field, eb, mode, params=params, out=out, ws=cws, size=size, status=st_c)
+        codec.decompress_async(out, field.shape, out=rec, ws=dws, status=st_d)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    if int(st_c.item()) or int(st_d.item()):
+        raise RuntimeError(f"device status compress={st_c.item()} decompress={st_d.item()}")
+    info = codec.inspect(out)
+    csize = int(size.item())
+
+    # ---- timed region
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(args.steps)]
+    outer = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        outer[0].record(stream)
+        for s in range(args.steps):
+            arr = (ctypes.c_void_p * 9)(*[e.cuda_event for e in ev[s]])
+            L.toposzp_set_stage_events(arr, 9)
+            codec.compress_async(field, eb, mode, params=params, out=out, ws=cws, size=size, status=st_c)
+            mids[s].record(stream)
+            codec.decompress_async(out, field.shape, out=rec, ws=dws, status=st_d)
+            outer[s + 1].record(stream)
+        torch.cuda.synchronize()
+    L.toposzp_set_stage_events(None, 0)
+    total_ms = outer[0].elapsed_time(outer[-1])
+    if pg:
+        t = torch.tensor([total_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_ms = float(t.item())
+        pg.barrier()
+    if int(st_c.item()) or int(st_d.item()):
+        raise RuntimeError("device status set during the timed region")
+    comp_ms = statistics.mean(outer[s].elapsed_time(mids[s]) for s in range(args.steps))
+    dec_ms = statistics.mean(mids[s].elapsed_time(outer[s + 1]) for s in range(args.steps))
+
+    def stage_ms(i, j):
+        return statistics.mean(ev[s][i].elapsed_time(ev[s][j]) for s in range(args.steps))
+
+    topo = not args.no_topo
+    k = int(info.k_min + info.k_max)
+    h = oracle_free_header(out)
+    nb = (n + 31) // 32
+    lab_bytes = 4 * ((n + 15) // 16) if topo else 0
+    field_sections = (h["off_s6"] - h["off_s1"]) + 4 * h["pay_words"]   # S1, S2, S4, S5 (+ padding)
+    kernels = {
+        "k_range_cd": (stage_ms(0, 1), 4 * n + lab_bytes),
+        "k_encode_field": (stage_ms(1, 2), 4 * n + lab_bytes + field_sections + 8 * k),
+        "rank_stages": (stage_ms(2, 3), None),
+        "k_decode_field": (stage_ms(5, 6), nb + 4 * nb + 4 * h["pay_words"] + lab_bytes + 4 * n + 4 * k),
+        "k_decode_ranks": (stage_ms(6, 7), None),
+        "k_fixup": (stage_ms(7, 8), None),
+    }
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
+    peak_src = "measured" if peaks else "fallback"
+    kout = {}
+    for name, (ms, nbytes) in kernels.items():
+        d = {"ms": round(ms, 4)}
+        if nbytes:
+            gbs = nbytes / (ms * 1e-3) / 1e9
+            d.update({"alg_bytes": int(nbytes), "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4),
+                      "frac_nominal_8tbs": round(gbs / NOMINAL_HBM_GBS, 4)})
+        kout[name] = d
+    dom = max((kname for kname in kout if "alg_bytes" in kout[kname]), key=lambda kk: kout[kk]["ms"])
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": kout[dom]["achieved_gbs"], "peak": peak,
+                "unit": "GB/s", "frac": kout[dom]["frac"], "traffic": None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
+    nbytes_all = 4 * n * ws_n
+    value = nbytes_all * args.steps / (total_ms * 1e-3) / 1e9
+    launches_c = 22 if topo else 5
+    launches_d = 4
+    result = {
+        "metric": "compress+decompress throughput (uncompressed bytes / round-trip time)",
+        "value": round(value, 2), "unit": "GB/s", "n_gpus": ws_n, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": describe(spec), "n": n, "field_bytes": 4 * n, "eb_mode": mode, "eb": args.eb,
+                   "topology": topo, "l2": "inputs larger than L2 (field 537 MB > 129 MB)" if n * 4 > 129e6
+                   else "field fits in L2: no flush between steps", "parallelism": f"replicas x{ws_n}"},
+        "compress_gbs": round(4 * n / (comp_ms * 1e-3) / 1e9, 2),
+        "decompress_gbs": round(4 * n / (dec_ms * 1e-3) / 1e9, 2),
+        "compress_ms": round(comp_ms, 4), "decompress_ms": round(dec_ms, 4),
+        "compressed_bytes": csize, "ratio": round(4 * n / csize, 3), "bit_rate": round(32 * csize / (4 * n), 3),
+        "k_extrema": k, "k_saddle": int(info.k_saddle),
+        "kernels": kout, "roofline": roofline, "gpu_launches": (launches_c + launches_d) * args.steps,
+        "clocks": clk.summary(),
+    }
+    # ---- end to end through the public API with host buffers (every rank)
+    if args.e2e_steps > 0:
+        host = field.cpu().pin_memory()
+        hout = torch.empty(csize, dtype=torch.uint8).pin_memory()
+        hrec = torch.empty(field.shape, dtype=torch.float32).pin_memory()
+        times = []
+        for i in range(args.e2e_steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            d_in = host.to(dev, non_blocking=True)
+            buf = codec.compress(d_in, eb, mode, no_topo=args.no_topo)
+            hout[:buf.numel()].copy_(buf, non_blocking=True)
+            d_buf = hout[:buf.numel()].to(dev, non_blocking=True)
+            r = codec.decompress(d_buf, tuple(field.shape))
+            hrec.copy_(r, non_blocking=True)
+            torch.cuda.synchronize()
+            if i:
+                times.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(times)
+        if pg:
+            t = torch.tensor([e2e_s], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        result["e2e"] = {"value": round(4 * n * ws_n / e2e_s / 1e9, 3), "unit": "GB/s",
+                         "h2d_bytes_per_step": int(4 * n + csize), "d2h_bytes_per_step": int(csize + 4 * n)}
+    if rank == 0 and not args.no_cpu_baseline:
+        gbs, desc, _ = cpu_sample(spec, field.cpu(), eb, args.cpu_seconds)
+        result["cpu_baseline"] = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                  "sample": desc}
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def oracle_free_header(buf):
+    """Header fields read straight from the stream bytes (no oracle import)."""
+    import numpy as np
+    b = buf[:256].cpu().numpy().tobytes()
+    u64 = lambda o: int(np.frombuffer(b[o:o + 8], "<u8")[0])
+    return {"off_s1": u64(152), "off_s2": u64(160), "off_s4": u64(168), "off_s6": u64(176),
+            "off_s5": u64(184), "off_s7": u64(192), "total": u64(200), "pay_words": u64(208)}
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

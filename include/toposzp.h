@@ -1,0 +1,156 @@
+/* toposzp.h -- C ABI of the GB300 TopoSZp compression library (sm_103a).
+ *
+ * TopoSZp (arXiv 2602.17552) is an error-bounded lossy compressor for 2D/3D
+ * float32 scalar fields that keeps critical points (minima, maxima, saddles)
+ * and their relative order.  Compression (Section IV-A) runs CD + RP (critical
+ * point labels and per-bin ranks), then SZp's QZ (quantisation), B + LZ
+ * (blocking + Lorenzo) and BE (fixed-length encoding); decompression
+ * (Section IV-B) inverts SZp, then applies the extrema stencils (CP^ + RP^) and
+ * the RBF saddle refinement (RS^) under the relaxed bound |a - a'| < 2 eps.
+ *
+ * Conventions for every call:
+ *  - Pointers are DEVICE pointers unless the comment says "host".
+ *  - Calls are asynchronous and ordered on `stream` (a cudaStream_t; NULL = the
+ *    legacy default stream).  The library allocates no memory and never
+ *    synchronises: the caller owns every buffer (field, output, workspace,
+ *    status word).
+ *  - The returned status covers argument checks done on the host before any
+ *    work is queued.  Errors found on the device (non-finite input, bound too
+ *    small, corrupt stream, a bounded wait that ran out) are written to the
+ *    caller's device word `*status` (0 = OK), to be read after the stream is
+ *    synchronised; later kernels of the same call then skip their work.
+ *  - Fields are row-major with dims[0] = nx the fastest axis; ndim is 2
+ *    (dims[2] ignored, treated as 1) or 3.  A 1D signal is a 2D field with
+ *    ny = 1.  The number of points n must be below 2^31.
+ *  - `field`, `out` and `workspace` must be 16-byte aligned (any torch or
+ *    cudaMalloc allocation is).
+ */
+#ifndef TOPOSZP_H
+#define TOPOSZP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void* toposzp_stream;   /* a cudaStream_t */
+
+typedef enum {
+    TOPOSZP_OK = 0,
+    TOPOSZP_ERR_INVALID_ARG = 1,     /* bad pointer, size, ndim, eb, params */
+    TOPOSZP_ERR_NONFINITE = 2,       /* NaN or Inf in the input field */
+    TOPOSZP_ERR_EB_TOO_SMALL = 3,    /* eps < ~2^-20 max|a|: codes would not fit */
+    TOPOSZP_ERR_BUFFER_TOO_SMALL = 4,/* output capacity or workspace too small */
+    TOPOSZP_ERR_CORRUPT_STREAM = 5,  /* header / section / payload inconsistent */
+    TOPOSZP_ERR_TIMEOUT = 6,         /* a bounded device wait gave up */
+    TOPOSZP_ERR_CUDA = 7,            /* a CUDA launch or copy failed */
+    TOPOSZP_ERR_UNSUPPORTED = 8      /* outside this build's limits (n >= 2^31) */
+} toposzp_status;
+
+typedef enum {
+    TOPOSZP_EB_ABS = 0,   /* eps = eb (the paper's absolute bound, Section V-A) */
+    TOPOSZP_EB_REL = 1    /* eps = eb * (max(a) - min(a)), value-range relative */
+} toposzp_eb_mode;
+
+/* flags */
+#define TOPOSZP_NO_TOPO 1u   /* SZp only: no labels, ranks or fix-ups (Fig. 9 baseline) */
+
+typedef struct {
+    uint32_t flags;       /* TOPOSZP_NO_TOPO or 0 */
+    uint32_t rs_sweeps;   /* passes over the saddle colour rounds; 0 means 1 */
+    int32_t rbf_k;        /* RBF kernel size 3, 5 or 7; 0 = adaptive (Section IV-B(3)) */
+    float rbf_sigma;      /* Gaussian width; 0 = adaptive in [0.5, 1] */
+} toposzp_params;
+
+/* Host.  flags 0, one sweep, adaptive RBF parameters. */
+void toposzp_default_params(toposzp_params* p);
+
+/* Host.  Human-readable name of a status code (static string). */
+const char* toposzp_status_string(toposzp_status s);
+
+/* Host.  Upper bound on the compressed size in bytes for these dims (0 if the
+ * dims are invalid); out_capacity >= this guarantees no overflow. */
+uint64_t toposzp_compress_bound(int ndim, const uint64_t dims[3]);
+
+/* Host.  Device workspace bytes needed by toposzp_compress /
+ * toposzp_decompress for a field of these dims (0 if invalid).  Worst case:
+ * it covers fields where every other point is an extremum. */
+uint64_t toposzp_compress_workspace_size(int ndim, const uint64_t dims[3]);
+uint64_t toposzp_decompress_workspace_size(int ndim, const uint64_t dims[3]);
+
+/* Compress one field (Section IV-A: CD + RP, QZ, B + LZ, BE).
+ *   field        device float32[n], read only
+ *   ndim, dims   host; grid shape, dims[0] fastest
+ *   mode, eb     error bound (eb > 0, finite)
+ *   params       host, may be NULL for the defaults
+ *   out          device byte buffer of out_capacity >= toposzp_compress_bound
+ *   out_size     device uint64, receives the stream length (0 on a device error)
+ *   workspace    device scratch of ws_bytes >= toposzp_compress_workspace_size;
+ *                its contents on entry do not matter and are clobbered
+ *   status       device int32, set to 0 then to the first device error
+ * The stream layout (header and sections) is described in the design notes;
+ * sections follow the paper's order with the fixed-size ones first. */
+toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dims[3],
+                                toposzp_eb_mode mode, double eb, const toposzp_params* params,
+                                void* out, uint64_t out_capacity, uint64_t* out_size,
+                                void* workspace, uint64_t ws_bytes, int32_t* status,
+                                toposzp_stream stream);
+
+/* Host.  Parse the first 256 bytes of a stream (a host copy) and report its
+ * shape and sizes.  Returns CORRUPT_STREAM if the header is not a valid
+ * TopoSZp v1 header. */
+typedef struct {
+    int ndim;
+    uint64_t dims[3];
+    uint64_t n;
+    uint64_t total_size;       /* bytes of the whole stream */
+    double eps;                /* absolute error bound used */
+    uint32_t flags;
+    uint64_t k_min, k_max, k_saddle;
+    int32_t rbf_k;
+    float rbf_sigma;
+} toposzp_info;
+toposzp_status toposzp_inspect(const void* header_host, uint64_t header_bytes, toposzp_info* info);
+
+/* Decompress a stream (Section IV-B: BE^, LZ^ + B^, QZ^, MD^, CP^ + RP^, RS^).
+ *   in, in_size  device stream bytes (in_size >= the stream's total size)
+ *   out          device float32[n_out]; n_out must equal the stream's n
+ *   workspace    device scratch of ws_bytes >= toposzp_decompress_workspace_size
+ *   status       device int32 (0 = OK; CORRUPT_STREAM if the stream is bad)
+ * The output satisfies |a - out| <= eps + h < 2 eps (Table I's eps_topo). */
+toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, uint64_t n_out,
+                                  void* workspace, uint64_t ws_bytes, int32_t* status,
+                                  toposzp_stream stream);
+
+/* Critical point detection alone (Section IV-A(1)) on any field.
+ *   labels_packed  device uint32[ceil(n/16)] or NULL: point i's code at bits
+ *                  2(i mod 16) of word i/16; r = 0, m = 1, s = 2, M = 3
+ *   counts4        device uint64[4] or NULL: number of r, m, s, M points
+ *   status         device int32 (NaN compares false: such points are regular) */
+toposzp_status toposzp_critical_points(const float* field, int ndim, const uint64_t dims[3],
+                                       uint32_t* labels_packed, uint64_t* counts4,
+                                       int32_t* status, toposzp_stream stream);
+
+/* Topological error counts between two packed label maps (Section III-B):
+ * out12[kind*4 + type], kind 0 = false negative (a critical point of `orig`
+ * that is regular in `dec`), 1 = false positive (indexed by the new type),
+ * 2 = false type (indexed by the original type).  out12 is overwritten. */
+toposzp_status toposzp_topo_errors(const uint32_t* labels_orig, const uint32_t* labels_dec,
+                                   uint64_t n, uint64_t* out12, toposzp_stream stream);
+
+/* Host.  Profiling hook (no counterpart in the paper).  After a call with
+ * count > 0, every toposzp_compress records events[0..4] (cudaEvent_t handles
+ * owned by the caller) on its stream: before the range + CD kernel, after it,
+ * after the field encoder, after the rank stages, at the end; and every
+ * toposzp_decompress records events[5..8]: at the start, after the field
+ * decoder, after the rank decoder, at the end.  count must be 0 (off) or 9.
+ * The setting is process-wide and not thread-safe; it is meant for a
+ * single-threaded benchmark. */
+toposzp_status toposzp_set_stage_events(void* const* events, int count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOPOSZP_H */

@@ -57,6 +57,9 @@ int orc_qparams_compute(const float* a, uint64_t n, int rel, double eb, orc_qpar
         if (v < vmin) vmin = v;
         if (v > vmax) vmax = v;
     }
+    /* -0 and +0 compare equal; store the range with +0 so its bits are unique */
+    if (vmin == 0.0f) vmin = 0.0f;
+    if (vmax == 0.0f) vmax = 0.0f;
     p->vmin = vmin;
     p->vmax = vmax;
     double eps = rel ? eb * ((double)vmax - (double)vmin) : eb;

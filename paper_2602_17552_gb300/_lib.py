@@ -1,0 +1,87 @@
+"""ctypes binding of libtoposzp.so (the C ABI in include/toposzp.h).
+
+Argument marshalling only.  The shared library is built in-tree by
+``paper_2602_17552_gb300.build``; if it is missing this module raises instead of
+falling back to any other implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtoposzp.so")
+
+STATUS = {
+    0: "OK", 1: "INVALID_ARG", 2: "NONFINITE", 3: "EB_TOO_SMALL", 4: "BUFFER_TOO_SMALL",
+    5: "CORRUPT_STREAM", 6: "TIMEOUT", 7: "CUDA", 8: "UNSUPPORTED",
+}
+OK, INVALID_ARG, NONFINITE, EB_TOO_SMALL, BUFFER_TOO_SMALL, CORRUPT_STREAM, TIMEOUT, CUDA, UNSUPPORTED = range(9)
+EB_ABS, EB_REL = 0, 1
+NO_TOPO = 1
+
+
+class TopoSZpError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_uint32), ("rs_sweeps", ctypes.c_uint32),
+                ("rbf_k", ctypes.c_int32), ("rbf_sigma", ctypes.c_float)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_uint64 * 3), ("n", ctypes.c_uint64),
+                ("total_size", ctypes.c_uint64), ("eps", ctypes.c_double), ("flags", ctypes.c_uint32),
+                ("k_min", ctypes.c_uint64), ("k_max", ctypes.c_uint64), ("k_saddle", ctypes.c_uint64),
+                ("rbf_k", ctypes.c_int32), ("rbf_sigma", ctypes.c_float)]
+
+
+EXPORTS = ("toposzp_default_params", "toposzp_status_string", "toposzp_compress_bound",
+           "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size", "toposzp_compress",
+           "toposzp_inspect", "toposzp_decompress", "toposzp_critical_points", "toposzp_topo_errors",
+           "toposzp_set_stage_events")
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Load the library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'` (there is no fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u64, c_int, i32p = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int, ctypes.c_void_p
+    dims_t = ctypes.POINTER(ctypes.c_uint64)
+    L.toposzp_default_params.argtypes = [ctypes.POINTER(Params)]
+    L.toposzp_default_params.restype = None
+    L.toposzp_status_string.argtypes = [c_int]
+    L.toposzp_status_string.restype = ctypes.c_char_p
+    for f in ("toposzp_compress_bound", "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size"):
+        getattr(L, f).argtypes = [c_int, dims_t]
+        getattr(L, f).restype = u64
+    L.toposzp_compress.argtypes = [vp, c_int, dims_t, c_int, ctypes.c_double, ctypes.POINTER(Params),
+                                   vp, u64, vp, vp, u64, i32p, vp]
+    L.toposzp_compress.restype = c_int
+    L.toposzp_inspect.argtypes = [vp, u64, ctypes.POINTER(Info)]
+    L.toposzp_inspect.restype = c_int
+    L.toposzp_decompress.argtypes = [vp, u64, vp, u64, vp, u64, i32p, vp]
+    L.toposzp_decompress.restype = c_int
+    L.toposzp_critical_points.argtypes = [vp, c_int, dims_t, vp, vp, i32p, vp]
+    L.toposzp_critical_points.restype = c_int
+    L.toposzp_topo_errors.argtypes = [vp, vp, u64, vp, vp]
+    L.toposzp_topo_errors.restype = c_int
+    L.toposzp_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), c_int]
+    L.toposzp_set_stage_events.restype = c_int
+    _lib = L
+    return L
+
+
+def dims3(ndim: int, dims) -> "ctypes.Array":
+    d = list(dims) + [1] * (3 - len(dims))
+    return (ctypes.c_uint64 * 3)(*[int(x) for x in d[:3]])

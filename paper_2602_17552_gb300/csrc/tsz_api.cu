@@ -1,0 +1,317 @@
+// tsz_api.cu -- the extern "C" entry points declared in include/toposzp.h.
+//
+// Host side only: argument validation, carving of the caller's workspace, and
+// the launch sequence.  No allocation, no synchronisation, no host reads of
+// device data; every data-dependent size is consumed on the device.
+#include <cmath>
+#include <cstring>
+
+#include "../../include/toposzp.h"
+#include "tsz_internal.h"
+
+namespace tsz {
+
+static uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+
+constexpr uint64_t CTRL_BYTES = 4096;
+constexpr int SORT_G = 1024;   // CTAs per list in the rank sort (fixed: sizes the workspace)
+
+static_assert(sizeof(Ctrl) <= CTRL_BYTES, "control block too large");
+
+static int sm_count() {
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        return 148;
+    return sms;
+}
+
+static bool make_geo(int ndim, const uint64_t dims[3], Geo& g) {
+    if (!dims || (ndim != 2 && ndim != 3)) return false;
+    uint64_t nx = dims[0], ny = dims[1], nz = ndim == 3 ? dims[2] : 1;
+    if (nx == 0 || ny == 0 || nz == 0) return false;
+    if (nx >= (1ull << 31) || ny >= (1ull << 31) || nz >= (1ull << 31)) return false;
+    uint64_t nxy = nx * ny;
+    if (nxy >= (1ull << 31) || nxy * nz >= (1ull << 31)) return false;
+    g.ndim = ndim;
+    g.nx = (uint32_t)nx;
+    g.ny = (uint32_t)ny;
+    g.nz = (uint32_t)nz;
+    g.nxy = (uint32_t)nxy;
+    g.n = (uint32_t)(nxy * nz);
+    g.nb = (uint32_t)cdiv(g.n, L);
+    return true;
+}
+
+CompressWs compress_ws(uint64_t n) {
+    CompressWs w;
+    const uint64_t nb = cdiv(n, L);
+    w.G = SORT_G;
+    w.list_cap = (uint32_t)(cdiv(n, 2) + 1);
+    w.ntiles = (uint32_t)cdiv(nb, TILE_BLOCKS);
+    w.rank_tiles = (uint32_t)cdiv(cdiv(n + 2, L), TILE_BLOCKS) + 1;
+    w.agg_stride = (uint32_t)cdiv(w.list_cap, RANK_TILE) + 1;
+    uint64_t o = 0;
+    w.ctrl = o; o = a256(o + CTRL_BYTES);
+    w.desc = o; o = a256(o + 16ull * (w.ntiles + 1));
+    w.rdesc = o; o = a256(o + 16ull * (w.rank_tiles + 1));
+    w.listM = o; o = a256(o + 8ull * w.list_cap);
+    w.listm = o; o = a256(o + 8ull * w.list_cap);
+    w.tmpM = o; o = a256(o + 8ull * w.list_cap);
+    w.tmpm = o; o = a256(o + 8ull * w.list_cap);
+    w.hist = o; o = a256(o + 4ull * 2 * 256 * SORT_G);
+    w.agg = o; o = a256(o + 8ull * 2 * w.agg_stride);
+    w.delta = o; o = a256(o + 4ull * (n + 2));
+    w.end = o;
+    return w;
+}
+
+DecompressWs decompress_ws(uint64_t n) {
+    DecompressWs w;
+    const uint64_t nb = cdiv(n, L);
+    w.ntiles = (uint32_t)cdiv(nb, TILE_BLOCKS);
+    w.rank_tiles = (uint32_t)cdiv(cdiv(n + 2, L), TILE_BLOCKS) + 1;
+    w.sad_cap = (uint32_t)n;
+    uint64_t o = 0;
+    w.ctrl = o; o = a256(o + CTRL_BYTES);
+    w.desc = o; o = a256(o + 16ull * (w.ntiles + 1));
+    w.rdesc = o; o = a256(o + 16ull * (w.rank_tiles + 1));
+    w.cp_idx = o; o = a256(o + 4ull * (n + 2));
+    w.delta = o; o = a256(o + 4ull * (n + 2));
+    w.newv = o; o = a256(o + 4ull * (n + 2));
+    w.sad = o; o = a256(o + 4ull * (n + 1));
+    w.sadv = o; o = a256(o + 4ull * (n + 1));
+    w.end = o;
+    return w;
+}
+
+__global__ void k_init_ctrl(Ctrl* c, Geo g, int rel, double eb, uint32_t flags, int sweeps) {
+    c->g = g;
+    c->rel = rel;
+    c->eb = eb;
+    c->flags = flags;
+    c->rs_sweeps = sweeps;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+static cudaEvent_t g_stage_ev[9];
+static bool g_stage_on = false;
+static void stage(int i, cudaStream_t st) {
+    if (g_stage_on) cudaEventRecord(g_stage_ev[i], st);
+}
+
+}  // namespace tsz
+
+using namespace tsz;
+
+extern "C" {
+
+void toposzp_default_params(toposzp_params* p) {
+    if (!p) return;
+    p->flags = 0;
+    p->rs_sweeps = 1;
+    p->rbf_k = 0;
+    p->rbf_sigma = 0.0f;
+}
+
+const char* toposzp_status_string(toposzp_status s) {
+    switch (s) {
+        case TOPOSZP_OK: return "ok";
+        case TOPOSZP_ERR_INVALID_ARG: return "invalid argument";
+        case TOPOSZP_ERR_NONFINITE: return "non-finite value in the input field";
+        case TOPOSZP_ERR_EB_TOO_SMALL: return "error bound too small for the field's magnitude";
+        case TOPOSZP_ERR_BUFFER_TOO_SMALL: return "output buffer or workspace too small";
+        case TOPOSZP_ERR_CORRUPT_STREAM: return "corrupt or mismatched compressed stream";
+        case TOPOSZP_ERR_TIMEOUT: return "a bounded device wait timed out";
+        case TOPOSZP_ERR_CUDA: return "CUDA launch or copy failed";
+        case TOPOSZP_ERR_UNSUPPORTED: return "outside the supported limits";
+    }
+    return "unknown status";
+}
+
+uint64_t toposzp_compress_bound(int ndim, const uint64_t dims[3]) {
+    Geo g;
+    if (!make_geo(ndim, dims, g)) return 0;
+    const uint64_t n = g.n, nb = g.nb, nbd = cdiv(n + 2, L);
+    return HDR + 16 * 10 + 4 * cdiv(nb, 32) + nb + 4 * nb + 4 * cdiv(n, 16) + 4 * (L + 1) * nb +
+           4 * cdiv(nbd, 32) + nbd + 4 * nbd + 4 * (L + 1) * nbd;
+}
+
+uint64_t toposzp_compress_workspace_size(int ndim, const uint64_t dims[3]) {
+    Geo g;
+    if (!make_geo(ndim, dims, g)) return 0;
+    return compress_ws(g.n).end;
+}
+
+uint64_t toposzp_decompress_workspace_size(int ndim, const uint64_t dims[3]) {
+    Geo g;
+    if (!make_geo(ndim, dims, g)) return 0;
+    return decompress_ws(g.n).end;
+}
+
+toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dims[3],
+                                toposzp_eb_mode mode, double eb, const toposzp_params* params,
+                                void* out, uint64_t out_capacity, uint64_t* out_size, void* workspace,
+                                uint64_t ws_bytes, int32_t* status, toposzp_stream stream) {
+    Geo g;
+    if (!dims || (ndim != 2 && ndim != 3)) return TOPOSZP_ERR_INVALID_ARG;
+    if (!make_geo(ndim, dims, g)) {
+        const uint64_t nz = ndim == 3 ? dims[2] : 1;
+        if (dims[0] && dims[1] && nz) return TOPOSZP_ERR_UNSUPPORTED;
+        return TOPOSZP_ERR_INVALID_ARG;
+    }
+    toposzp_params p;
+    toposzp_default_params(&p);
+    if (params) p = *params;
+    if (p.rs_sweeps == 0) p.rs_sweeps = 1;
+    if (!field || !out || !out_size || !workspace || !status) return TOPOSZP_ERR_INVALID_ARG;
+    if (!aligned16(field) || !aligned16(out) || !aligned16(workspace)) return TOPOSZP_ERR_INVALID_ARG;
+    if (mode != TOPOSZP_EB_ABS && mode != TOPOSZP_EB_REL) return TOPOSZP_ERR_INVALID_ARG;
+    if (!(eb > 0.0) || !std::isfinite(eb)) return TOPOSZP_ERR_INVALID_ARG;
+    if (p.flags & ~TOPOSZP_NO_TOPO) return TOPOSZP_ERR_INVALID_ARG;
+    if (p.rs_sweeps > 16) return TOPOSZP_ERR_INVALID_ARG;
+    if (p.rbf_k != 0 && p.rbf_k != 3 && p.rbf_k != 5 && p.rbf_k != 7) return TOPOSZP_ERR_INVALID_ARG;
+    if (!(p.rbf_sigma >= 0.0f) || !std::isfinite(p.rbf_sigma)) return TOPOSZP_ERR_INVALID_ARG;
+    if (out_capacity < toposzp_compress_bound(ndim, dims)) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
+    const CompressWs w = compress_ws(g.n);
+    if (ws_bytes < w.end) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
+
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* ws = reinterpret_cast<uint8_t*>(workspace);
+    uint8_t* o = reinterpret_cast<uint8_t*>(out);
+    Ctrl* c = reinterpret_cast<Ctrl*>(ws + w.ctrl);
+    Desc* desc = reinterpret_cast<Desc*>(ws + w.desc);
+    Desc* rdesc = reinterpret_cast<Desc*>(ws + w.rdesc);
+    uint2* listM = reinterpret_cast<uint2*>(ws + w.listM);
+    uint2* listm = reinterpret_cast<uint2*>(ws + w.listm);
+    const bool topo = !(p.flags & TOPOSZP_NO_TOPO);
+    const int sms = sm_count();
+    Layout lo;
+    make_layout(g.n, g.nb, topo, 0, 0, 0, lo);
+    uint32_t* labels = reinterpret_cast<uint32_t*>(o + lo.s6);
+
+    cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(ws, 0, w.listM, st);   // control block and both look-back descriptor arrays
+    k_init_ctrl<<<1, 1, 0, st>>>(c, g, mode == TOPOSZP_EB_REL ? 1 : 0, eb, p.flags, (int)p.rs_sweeps);
+    stage(0, st);
+    launch_range_cd(field, g, c, labels, topo, sms, st);
+    stage(1, st);
+    launch_qparams(c, status, st);
+    launch_encode_field(field, labels, c, desc, o, lo, listM, listm, topo, g.nb, sms, status, st);
+    stage(2, st);
+    if (topo) {
+        launch_ranks(c, listM, listm, reinterpret_cast<uint2*>(ws + w.tmpM),
+                     reinterpret_cast<uint2*>(ws + w.tmpm), reinterpret_cast<uint32_t*>(ws + w.hist),
+                     reinterpret_cast<uint2*>(ws + w.agg), w.agg_stride,
+                     reinterpret_cast<int32_t*>(ws + w.delta), w.G, status, st);
+        launch_encode_ranks(reinterpret_cast<int32_t*>(ws + w.delta), c, rdesc, o, w.rank_tiles, sms,
+                            status, st);
+        launch_count_saddles(labels, c, g.n, sms, status, st);
+    }
+    stage(3, st);
+    launch_finalize(c, o, out_size, p.rbf_k, p.rbf_sigma, status, st);
+    stage(4, st);
+    return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;
+}
+
+toposzp_status toposzp_inspect(const void* header_host, uint64_t header_bytes, toposzp_info* info) {
+    if (!header_host || !info || header_bytes < HDR) return TOPOSZP_ERR_INVALID_ARG;
+    const uint8_t* h = reinterpret_cast<const uint8_t*>(header_host);
+    auto u32 = [&](int off) { uint32_t v; std::memcpy(&v, h + off, 4); return v; };
+    auto u64 = [&](int off) { uint64_t v; std::memcpy(&v, h + off, 8); return v; };
+    if (u32(0) != MAGIC || u32(4) != VERSION || u32(12) != L) return TOPOSZP_ERR_CORRUPT_STREAM;
+    std::memset(info, 0, sizeof(*info));
+    info->ndim = (int)u32(8);
+    info->dims[0] = u64(16);
+    info->dims[1] = u64(24);
+    info->dims[2] = u64(32);
+    if ((info->ndim != 2 && info->ndim != 3) || !info->dims[0] || !info->dims[1] || !info->dims[2])
+        return TOPOSZP_ERR_CORRUPT_STREAM;
+    info->n = u64(104);
+    if (info->n != info->dims[0] * info->dims[1] * info->dims[2]) return TOPOSZP_ERR_CORRUPT_STREAM;
+    info->total_size = u64(200);
+    std::memcpy(&info->eps, h + 56, 8);
+    info->flags = u32(40);
+    info->k_min = u64(120);
+    info->k_max = u64(128);
+    info->k_saddle = u64(136);
+    info->rbf_k = (int32_t)u32(88);
+    std::memcpy(&info->rbf_sigma, h + 92, 4);
+    return TOPOSZP_OK;
+}
+
+toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, uint64_t n_out,
+                                  void* workspace, uint64_t ws_bytes, int32_t* status,
+                                  toposzp_stream stream) {
+    if (!in || !out || !workspace || !status || n_out == 0) return TOPOSZP_ERR_INVALID_ARG;
+    if (n_out >= (1ull << 31)) return TOPOSZP_ERR_UNSUPPORTED;
+    if (!aligned16(in) || !aligned16(out) || !aligned16(workspace)) return TOPOSZP_ERR_INVALID_ARG;
+    const DecompressWs w = decompress_ws(n_out);
+    if (ws_bytes < w.end) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* ws = reinterpret_cast<uint8_t*>(workspace);
+    const uint8_t* src = reinterpret_cast<const uint8_t*>(in);
+    Ctrl* c = reinterpret_cast<Ctrl*>(ws + w.ctrl);
+    const int sms = sm_count();
+    cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    cudaMemsetAsync(ws, 0, w.cp_idx, st);   // control block and look-back descriptors
+    launch_parse_header(src, in_size, n_out, c, status, st);
+    stage(5, st);
+    launch_decode_field(src, c, reinterpret_cast<Desc*>(ws + w.desc), out,
+                        reinterpret_cast<uint32_t*>(ws + w.cp_idx), w.ntiles, sms, status, st);
+    stage(6, st);
+    launch_decode_ranks(src, c, reinterpret_cast<Desc*>(ws + w.rdesc),
+                        reinterpret_cast<int32_t*>(ws + w.delta), w.rank_tiles, sms, status, st);
+    stage(7, st);
+    cudaError_t e = launch_fixup(src, c, out, reinterpret_cast<uint32_t*>(ws + w.cp_idx),
+                                 reinterpret_cast<int32_t*>(ws + w.delta), reinterpret_cast<float*>(ws + w.newv),
+                                 reinterpret_cast<uint32_t*>(ws + w.sad), reinterpret_cast<float*>(ws + w.sadv),
+                                 w.sad_cap, sms, status, st);
+    if (e != cudaSuccess) return TOPOSZP_ERR_CUDA;
+    stage(8, st);
+    return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;
+}
+
+toposzp_status toposzp_set_stage_events(void* const* events, int count) {
+    if (count == 0) {
+        g_stage_on = false;
+        return TOPOSZP_OK;
+    }
+    if (count != 9 || !events) return TOPOSZP_ERR_INVALID_ARG;
+    for (int i = 0; i < 9; i++) {
+        if (!events[i]) return TOPOSZP_ERR_INVALID_ARG;
+        g_stage_ev[i] = reinterpret_cast<cudaEvent_t>(events[i]);
+    }
+    g_stage_on = true;
+    return TOPOSZP_OK;
+}
+
+toposzp_status toposzp_critical_points(const float* field, int ndim, const uint64_t dims[3],
+                                       uint32_t* labels_packed, uint64_t* counts4, int32_t* status,
+                                       toposzp_stream stream) {
+    Geo g;
+    if (!field || !status || (!labels_packed && !counts4)) return TOPOSZP_ERR_INVALID_ARG;
+    if (!make_geo(ndim, dims, g)) return TOPOSZP_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(field) & 3u) || (reinterpret_cast<uintptr_t>(labels_packed) & 3u) ||
+        (reinterpret_cast<uintptr_t>(counts4) & 7u))
+        return TOPOSZP_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(status, 0, sizeof(int32_t), st);
+    if (counts4) cudaMemsetAsync(counts4, 0, 4 * sizeof(uint64_t), st);
+    launch_critical_points(field, g, labels_packed, reinterpret_cast<unsigned long long*>(counts4),
+                           sm_count(), st);
+    return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;
+}
+
+toposzp_status toposzp_topo_errors(const uint32_t* labels_orig, const uint32_t* labels_dec, uint64_t n,
+                                   uint64_t* out12, toposzp_stream stream) {
+    if (!labels_orig || !labels_dec || !out12 || n == 0) return TOPOSZP_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    cudaMemsetAsync(out12, 0, 12 * sizeof(uint64_t), st);
+    launch_topo_errors(labels_orig, labels_dec, n, reinterpret_cast<unsigned long long*>(out12), sm_count(),
+                       st);
+    return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,302 @@
+// tsz_common.cuh -- device-side building blocks shared by the TopoSZp kernels.
+//
+// Everything here is compiled with --fmad=false, -ftz=false, -prec-div=true:
+// each float expression below is one IEEE-754 binary32 (or binary64) operation
+// rounded to nearest, so results are reproducible bit for bit.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace tsz {
+
+constexpr uint32_t L = 32;               // block length of the B stage (Section II-C)
+constexpr uint32_t HDR = 256;            // stream header bytes
+constexpr uint32_t MAGIC = 0x505A5354u;  // "TSZP"
+constexpr uint32_t VERSION = 1;
+constexpr uint32_t FLAG_NO_TOPO = 1;
+
+// labels of Section IV-A(1): r = 00, m = 01, s = 10, M = 11
+constexpr int LAB_R = 0, LAB_MIN = 1, LAB_SAD = 2, LAB_MAX = 3;
+
+// status codes (same values as toposzp_status)
+constexpr int ST_OK = 0, ST_INVALID = 1, ST_NONFINITE = 2, ST_EB_SMALL = 3, ST_BUF_SMALL = 4,
+              ST_CORRUPT = 5, ST_TIMEOUT = 6;
+
+// Codec tile: one CTA of 8 warps, each warp owns 8 consecutive blocks of 32.
+constexpr int TILE_WARPS = 8;
+constexpr int BPW = 8;
+constexpr int TILE_BLOCKS = TILE_WARPS * BPW;   // 64 blocks = 2048 points
+constexpr uint32_t FULL = 0xFFFFFFFFu;
+
+// Bounded waits: a look-back spin gives up after this many polls (each poll
+// sleeps up to 256 ns), sets ST_TIMEOUT and lets the kernel finish.
+constexpr uint32_t SPIN_LIMIT = 1u << 22;
+
+__host__ __device__ inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+template <class T>
+__host__ __device__ inline T hmin(T a, T b) { return a < b ? a : b; }
+__host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
+
+struct Geo {
+    int ndim;
+    uint32_t nx, ny, nz;   // nz = 1 in 2D
+    uint32_t n;            // nx * ny * nz < 2^31
+    uint32_t nxy;
+    uint32_t nb;           // blocks of L
+};
+
+// Stream layout of Section IV-A as placed in this format: header, (1) const
+// bitmap, (2) widths, (4) first values, (6) labels, (3)+(5) planes, (7) ranks.
+struct Layout {
+    uint64_t s1, s2, s4, s6, s5, s5_end, s7, r1, r2, r4, r5, end;
+};
+
+__host__ __device__ inline void make_layout(uint64_t n, uint64_t nb, bool topo, uint64_t pay_words,
+                                            uint64_t k, uint64_t rank_words, Layout& lo) {
+    lo.s1 = HDR;
+    lo.s2 = align16(lo.s1 + 4 * cdiv(nb, 32));
+    lo.s4 = align16(lo.s2 + nb);
+    lo.s6 = align16(lo.s4 + 4 * nb);
+    lo.s5 = align16(lo.s6 + (topo ? 4 * cdiv(n, 16) : 0));
+    lo.s5_end = lo.s5 + 4 * pay_words;
+    if (topo) {
+        uint64_t nbd = cdiv(k, L);
+        lo.s7 = align16(lo.s5_end);
+        lo.r1 = lo.s7;
+        lo.r2 = align16(lo.r1 + 4 * cdiv(nbd, 32));
+        lo.r4 = align16(lo.r2 + nbd);
+        lo.r5 = align16(lo.r4 + 4 * nbd);
+        lo.end = lo.r5 + 4 * rank_words;
+    } else {
+        lo.s7 = lo.r1 = lo.r2 = lo.r4 = lo.r5 = lo.end = lo.s5_end;
+    }
+}
+
+// Device control block, first bytes of every workspace; zeroed by the host
+// wrapper before the first kernel of a call.
+struct Ctrl {
+    // range pass
+    unsigned int min_inv, max_key, nonfinite, pad0;
+    // quantiser (Section II-C) and geometry, filled by the parameter kernel or
+    // by the header parser
+    int const_field, rel, rbf_k, rs_sweeps;
+    float w_f, r_f, h_f, rbf_sigma;
+    float vmin, vmax;
+    uint32_t flags, pad1;
+    double eps, eb;
+    Geo g;
+    // tile allocators of the persistent codec kernels
+    unsigned int tile_enc, tile_rank, tile_dec, tile_rdec;
+    // extrema lists (compress) and counts
+    unsigned int cnt_max, cnt_min, pad2, pad3;
+    unsigned long long sum_abs;
+    unsigned long long pay_words, k_total, rank_words, k_sad;
+    unsigned long long counts[4];
+    // decode-side bookkeeping
+    unsigned long long stat_restored, stat_skipped, stat_saddle;
+    unsigned int sad_cnt[8];
+    Layout lo;
+    float g_rbf[9];
+};
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ void set_status(int* st, int code) {
+    if (code) atomicCAS(st, 0, code);
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Order-preserving map of binary32 onto uint32 (-0 folded onto +0).
+__device__ __forceinline__ uint32_t ord_key(float v) {
+    uint32_t b = __float_as_uint(v);
+    if (b == 0x80000000u) b = 0u;
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+    uint32_t b = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+    return __uint_as_float(b);
+}
+
+// QZ: round-half-up of a / w as floor(fl(fl(a * r) + 0.5)) (Section II-C).
+__device__ __forceinline__ int32_t quantize(float a, float r) {
+    float x = __fmul_rn(a, r);
+    float y = __fadd_rn(x, 0.5f);
+    return (int32_t)floorf(y);
+}
+// QZ^: bin centre q * w.
+__device__ __forceinline__ float dequantize(int32_t q, float w) {
+    return __fmul_rn(__int2float_rn(q), w);
+}
+
+// spread the low 16 bits of x to the even bit positions
+__device__ __forceinline__ uint32_t spread16(uint32_t x) {
+    x &= 0xFFFFu;
+    x = (x | (x << 8)) & 0x00FF00FFu;
+    x = (x | (x << 4)) & 0x0F0F0F0Fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+
+__device__ __forceinline__ int label_at(const uint32_t* labels, uint32_t i) {
+    return (int)((labels[i >> 4] >> ((i & 15u) * 2u)) & 3u);
+}
+
+// CD of Section IV-A(1) at point i with coordinates (x, y, z): strict
+// comparisons with the face neighbours inside the grid.  m: all higher; M: all
+// lower; s: both neighbours on every axis, each pair entirely higher (H) or
+// entirely lower (L), at least one H and one L pair (the 2D rule of the paper
+// and its 3D extension).  `val(j)` returns the field value at index j.
+template <class Val>
+__device__ __forceinline__ int classify(const Val& val, const Geo& g, uint32_t i, uint32_t x,
+                                        uint32_t y, uint32_t z, float v) {
+    int nn = 0, nhi = 0, nlo = 0, ph = 0, pl = 0, px = 0;
+    bool interior = true;
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        if (ax == 2 && g.ndim != 3) break;
+        uint32_t c = ax == 0 ? x : (ax == 1 ? y : z);
+        uint32_t d = ax == 0 ? g.nx : (ax == 1 ? g.ny : g.nz);
+        uint32_t s = ax == 0 ? 1u : (ax == 1 ? g.nx : g.nxy);
+        bool lo = c > 0, hi = c + 1 < d;
+        int hc = 0, lc = 0;
+        if (lo) {
+            float u = val(i - s);
+            nn++;
+            if (u > v) { nhi++; hc++; } else if (u < v) { nlo++; lc++; }
+        }
+        if (hi) {
+            float u = val(i + s);
+            nn++;
+            if (u > v) { nhi++; hc++; } else if (u < v) { nlo++; lc++; }
+        }
+        if (lo && hi) {
+            if (hc == 2) ph++;
+            else if (lc == 2) pl++;
+            else px++;
+        } else {
+            interior = false;
+        }
+    }
+    if (nn == 0) return LAB_R;
+    if (nhi == nn) return LAB_MIN;
+    if (nlo == nn) return LAB_MAX;
+    if (interior && px == 0 && ph > 0 && pl > 0) return LAB_SAD;
+    return LAB_R;
+}
+
+struct GlobalVal {
+    const float* F;
+    __device__ __forceinline__ float operator()(uint32_t j) const { return F[j]; }
+};
+
+__device__ __forceinline__ void coords(const Geo& g, uint32_t i, uint32_t& x, uint32_t& y,
+                                       uint32_t& z) {
+    x = i % g.nx;
+    uint32_t t = i / g.nx;
+    y = t % g.ny;
+    z = t / g.ny;
+}
+
+// ----------------------------------------------------- decoupled look-back
+//
+// Single-pass exclusive scan over tiles of (payload words, extremum count).
+// Each tile publishes two 64-bit words; the top two bits carry the state
+// (1 = tile aggregate, 2 = inclusive prefix).  A reader accepts a pair only
+// when both words carry the same state, so no fence is needed between them.
+
+struct Desc {
+    unsigned long long a, b;
+};
+constexpr unsigned long long ST_AGG = 1ull << 62, ST_INC = 2ull << 62, VAL_MASK = (1ull << 62) - 1;
+
+__device__ __forceinline__ void desc_store(Desc* d, unsigned long long state, unsigned long long va,
+                                           unsigned long long vb) {
+    volatile unsigned long long* p = reinterpret_cast<volatile unsigned long long*>(d);
+    p[0] = state | va;
+    p[1] = state | vb;
+}
+
+// Called by one full warp.  Returns the exclusive prefix (va, vb) of tile t
+// and publishes its inclusive value.  Tiles are handed out in increasing order
+// by an atomic counter, so every tile waited on belongs to a running CTA.
+__device__ __forceinline__ void lookback(Desc* desc, uint32_t t, unsigned long long agg_a,
+                                         unsigned long long agg_b, unsigned long long& pre_a,
+                                         unsigned long long& pre_b, int* status) {
+    const int lane = threadIdx.x & 31;
+    pre_a = 0;
+    pre_b = 0;
+    if (t == 0) {
+        if (lane == 0) desc_store(&desc[0], ST_INC, agg_a, agg_b);
+        return;
+    }
+    if (lane == 0) desc_store(&desc[t], ST_AGG, agg_a, agg_b);
+    __threadfence();
+    long long base = (long long)t - 1;
+    uint32_t spins = 0;
+    bool timed_out = false;
+    while (true) {
+        long long j = base - lane;
+        unsigned long long A = 0, B = 0;
+        int st;
+        if (j >= 0) {
+            volatile unsigned long long* p = reinterpret_cast<volatile unsigned long long*>(&desc[j]);
+            A = p[0];
+            B = p[1];
+            st = ((A >> 62) == (B >> 62)) ? (int)(A >> 62) : 0;
+        } else {
+            st = 2;   // before tile 0: inclusive prefix 0
+        }
+        uint32_t inc = __ballot_sync(FULL, st == 2);
+        uint32_t none = __ballot_sync(FULL, st == 0);
+        int first = inc ? __ffs(inc) - 1 : 32;
+        uint32_t need = first >= 31 ? FULL : ((2u << first) - 1u);
+        if (none & need) {
+            if (++spins > SPIN_LIMIT) {
+                timed_out = true;
+                break;
+            }
+            __nanosleep(spins < 64 ? 32 : 256);
+            continue;
+        }
+        unsigned long long va = (lane <= first) ? (A & VAL_MASK) : 0;
+        unsigned long long vb = (lane <= first) ? (B & VAL_MASK) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            va += __shfl_xor_sync(FULL, va, o);
+            vb += __shfl_xor_sync(FULL, vb, o);
+        }
+        pre_a += va;
+        pre_b += vb;
+        if (first < 32) break;
+        base -= 32;
+    }
+    if (timed_out && lane == 0) set_status(status, ST_TIMEOUT);
+    if (lane == 0) desc_store(&desc[t], ST_INC, pre_a + agg_a, pre_b + agg_b);
+}
+
+// exp(-t), t >= 0, by scaling and squaring with a 12-term Taylor polynomial:
+// only binary64 + * /, so host and device give identical bits.
+__host__ __device__ inline double exp_neg(double t) {
+#ifdef __CUDA_ARCH__
+    double y = __ddiv_rn(-t, 1024.0);
+    double e = 1.0;
+    for (int j = 12; j >= 1; j--) e = __dadd_rn(1.0, __dmul_rn(__ddiv_rn(y, (double)j), e));
+    for (int i = 0; i < 10; i++) e = __dmul_rn(e, e);
+    return e;
+#else
+    double y = -t / 1024.0;
+    double e = 1.0;
+    for (int j = 12; j >= 1; j--) e = 1.0 + (y / (double)j) * e;
+    for (int i = 0; i < 10; i++) e = e * e;
+    return e;
+#endif
+}
+
+}  // namespace tsz

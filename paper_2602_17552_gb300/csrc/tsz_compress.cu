@@ -1,0 +1,920 @@
+// tsz_compress.cu -- compression kernels (Section IV-A of arXiv 2602.17552).
+//
+// Pipeline on one stream:
+//   k_range_cd      one read of the field: value range (min, max) and, unless
+//                   NO_TOPO, the CD labels written straight into section (6)
+//   k_qparams       one thread: eps, bin width w, its reciprocal r, half-width h
+//   k_encode<Field> one read of field + labels: QZ, B + LZ, BE with a
+//                   single-pass decoupled look-back for the payload offsets and
+//                   the positions of extrema; extrema keys go to two lists
+//   radix sort      per list, LSD 8-bit digits on order-preserving keys
+//   k_rank_*        dense rank per (type, bin) segment = RP's delta
+//   k_encode<Rank>  the same codec on the delta sequence (no QZ)
+//   k_finalize      header, section padding, stream size
+#include "tsz_internal.h"
+
+namespace tsz {
+
+// ================================================================ range + CD
+
+// One warp owns chunks of 512 consecutive points: lane l handles points
+// base + 32k + l (k = 0..15), so every load is a coalesced 128-byte row; the
+// 2-bit labels of 32 points are gathered with two ballots and interleaved into
+// two label words.
+template <bool TOPO, bool COUNTS, bool STATS>
+__global__ void __launch_bounds__(256) k_range_cd(const float* __restrict__ a, const Geo g, Ctrl* c,
+                                                  uint32_t* __restrict__ labels,
+                                                  unsigned long long* counts) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = (g.n + 511) / 512;
+    const uint32_t nwords = (g.n + 15) / 16;
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    uint32_t kmin = 0, kmax = 0;   // min as max of ~key
+    bool bad = false;
+    unsigned long long cm = 0, cs = 0, cM = 0;
+    GlobalVal val{a};
+    for (uint32_t ch = warp0; ch < nchunks; ch += nwarps) {
+        const uint32_t base = ch * 512u;
+        uint32_t x, y, z;
+        uint32_t i0 = base + lane;
+        coords(g, i0 < g.n ? i0 : 0, x, y, z);
+        uint32_t word = 0;
+#pragma unroll 4
+        for (int k = 0; k < 16; k++) {
+            const uint32_t i = base + 32u * k + lane;
+            int lab = 0;
+            if (i < g.n) {
+                float v = __ldg(a + i);
+                if (!isfinite(v)) bad = true;
+                uint32_t key = ord_key(v);
+                kmax = max(kmax, key);
+                kmin = max(kmin, ~key);
+                if (TOPO) lab = classify(val, g, i, x, y, z, v);
+            }
+            if (TOPO) {
+                uint32_t b0 = __ballot_sync(FULL, lab & 1);
+                uint32_t b1 = __ballot_sync(FULL, lab >> 1);
+                if (lane == 2 * k) word = spread16(b0) | (spread16(b1) << 1);
+                if (lane == 2 * k + 1) word = spread16(b0 >> 16) | (spread16(b1 >> 16) << 1);
+            }
+            x += 32;
+            while (x >= g.nx) {
+                x -= g.nx;
+                if (++y == g.ny) { y = 0; ++z; }
+            }
+        }
+        if (TOPO) {
+            uint32_t wi = ch * 32u + lane;
+            if (wi < nwords) {
+                if (labels) labels[wi] = word;
+                if (COUNTS) {
+                    uint32_t lo = word & 0x55555555u, hi = (word >> 1) & 0x55555555u;
+                    cm += __popc(lo & ~hi);
+                    cs += __popc(hi & ~lo);
+                    cM += __popc(lo & hi);
+                }
+            }
+        }
+    }
+    // reduce and publish
+    kmax = __reduce_max_sync(FULL, kmax);
+    kmin = __reduce_max_sync(FULL, kmin);
+    bool anybad = __any_sync(FULL, bad);
+    if (STATS && lane == 0) {
+        if (kmax) atomicMax(&c->max_key, kmax);
+        if (kmin) atomicMax(&c->min_inv, kmin);
+        if (anybad) atomicExch(&c->nonfinite, 1u);
+    }
+    if (COUNTS) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cm += __shfl_xor_sync(FULL, cm, o);
+            cs += __shfl_xor_sync(FULL, cs, o);
+            cM += __shfl_xor_sync(FULL, cM, o);
+        }
+        if (lane == 0) {
+            if (cm) atomicAdd(&counts[1], cm);
+            if (cs) atomicAdd(&counts[2], cs);
+            if (cM) atomicAdd(&counts[3], cM);
+        }
+    }
+}
+
+// counts[0] = n - (m + s + M)
+__global__ void k_count_regular(uint32_t n, unsigned long long* counts) {
+    counts[0] = (unsigned long long)n - counts[1] - counts[2] - counts[3];
+}
+
+// ============================================================ quantiser setup
+
+// Section II-C with the readings of the design notes: eps from the bound mode;
+// bins of width w = 2h, h = eps - (M + eps) 2^-21 so the binary32 round trip
+// stays within eps; constant fields are coded exactly.
+__global__ void k_qparams(Ctrl* c, int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (c->nonfinite) {
+        set_status(status, ST_NONFINITE);
+        return;
+    }
+    float vmin = key_float(~c->min_inv);
+    float vmax = key_float(c->max_key);
+    c->vmin = vmin;
+    c->vmax = vmax;
+    double eps = c->rel ? __dmul_rn(c->eb, __dsub_rn((double)vmax, (double)vmin)) : c->eb;
+    c->eps = eps;
+    if (vmax == vmin) {
+        float w = (vmin == 0.0f) ? 1.0f : fabsf(vmin);
+        c->const_field = 1;
+        c->w_f = w;
+        c->r_f = __double2float_rn(__ddiv_rn(1.0, (double)w));
+        c->h_f = 0.0f;
+        return;
+    }
+    if (!(eps > 0.0) || !isfinite(eps)) {
+        set_status(status, ST_EB_SMALL);
+        return;
+    }
+    double M = fmax(fabs((double)vmin), fabs((double)vmax));
+    double h = __dsub_rn(eps, __dmul_rn(__dadd_rn(M, eps), 0x1p-21));
+    if (!(h >= __dmul_rn(eps, 0.5))) {
+        set_status(status, ST_EB_SMALL);
+        return;
+    }
+    if (!(__dmul_rn(2.0, h) <= (double)3.0e38f)) {
+        set_status(status, ST_INVALID);
+        return;
+    }
+    float w = __double2float_rd(__dmul_rn(2.0, h));
+    c->w_f = w;
+    c->r_f = __double2float_rn(__ddiv_rn(1.0, (double)w));
+    c->h_f = __double2float_rd(h);
+}
+
+// ====================================================================== codec
+//
+// B + LZ + BE (Sections II-C, IV-A): block b holds codes q[32b .. 32b+31] (the
+// tail block repeats its last code); Lorenzo residuals d_0 = 0,
+// d_j = q_j - q_{j-1}; w_b = bit length of max|d|; w_b = 0 is a constant block.
+// A non-constant block stores a sign plane and w_b magnitude planes, one
+// ballot each, at its exclusive prefix offset from the look-back.
+
+struct EncOut {
+    uint32_t* cbits;
+    uint8_t* width;
+    int32_t* first;
+    uint32_t* pay;
+};
+
+// Field encoder.  TOPO also reads the labels, counts the extrema of each tile
+// (carried through the same look-back as the payload size, giving each
+// extremum its position in the delta sequence) and appends (key, position)
+// pairs to the maxima / minima lists.
+template <bool TOPO>
+__global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ a,
+                                                      const uint32_t* __restrict__ labels, Ctrl* c,
+                                                      Desc* desc, EncOut o, uint2* listM, uint2* listm,
+                                                      int* status) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_w[TILE_WARPS], s_cp[TILE_WARPS], s_M[TILE_WARPS], s_m[TILE_WARPS];
+    __shared__ unsigned long long s_pre_w, s_pre_cp;
+    __shared__ uint32_t s_baseM, s_basem;
+    __shared__ uint32_t s_cbits[2];
+    if (*status) return;
+    const Geo g = c->g;
+    const float r = c->r_f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    const uint32_t ncw = (g.nb + 31) / 32;
+    unsigned long long sum_abs = 0;
+    if (threadIdx.x < 2) s_cbits[threadIdx.x] = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_enc, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t blk0 = tile * TILE_BLOCKS + warp * BPW;
+        int32_t dreg[BPW];
+        float areg[BPW];
+        uint32_t labbits = 0;   // 2 bits per block j for this lane
+        uint32_t my_w = 0;
+        int32_t my_first = 0;
+        uint32_t wwords = 0, wcp = 0, wM = 0, wm = 0;
+#pragma unroll
+        for (int j = 0; j < BPW; j++) {
+            const uint32_t b = blk0 + j;
+            dreg[j] = 0;
+            areg[j] = 0.0f;
+            if (b < g.nb) {
+                const uint32_t i = b * 32u + lane;
+                const uint32_t nvalid = min(32u, g.n - b * 32u);
+                float v = (lane < nvalid) ? __ldg(a + i) : 0.0f;
+                int32_t q = quantize(v, r);
+                int32_t qlast = __shfl_sync(FULL, q, nvalid - 1);
+                if (lane >= nvalid) q = qlast;
+                int32_t prev = __shfl_up_sync(FULL, q, 1);
+                int32_t d = lane ? q - prev : 0;
+                uint32_t m = (uint32_t)(d < 0 ? -d : d);
+                uint32_t mx = __reduce_max_sync(FULL, m);
+                uint32_t w = 32u - __clz(mx);
+                int32_t first = __shfl_sync(FULL, q, 0);
+                uint32_t sm = __reduce_add_sync(FULL, m);
+                if (lane == 0) sum_abs += sm;
+                if (lane == j) {
+                    my_w = w;
+                    my_first = first;
+                }
+                dreg[j] = d;
+                areg[j] = v;
+                wwords += w ? 1u + w : 0u;
+                if (TOPO) {
+                    int lab = (lane < nvalid) ? label_at(labels, i) : 0;
+                    labbits |= (uint32_t)lab << (2 * j);
+                    uint32_t bM = __ballot_sync(FULL, lab == LAB_MAX);
+                    uint32_t bm = __ballot_sync(FULL, lab == LAB_MIN);
+                    wM += __popc(bM);
+                    wm += __popc(bm);
+                }
+            }
+        }
+        wcp = wM + wm;
+        if (lane == 0) {
+            s_w[warp] = wwords;
+            s_cp[warp] = wcp;
+            s_M[warp] = wM;
+            s_m[warp] = wm;
+        }
+        // constant-block bits of this warp's 8 blocks
+        {
+            uint32_t cb = __ballot_sync(FULL, lane < BPW && blk0 + lane < g.nb && my_w == 0) & 0xFFu;
+            if (lane == 0 && cb) atomicOr(&s_cbits[warp >> 2], cb << ((warp & 3) * 8));
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t vw = lane < TILE_WARPS ? s_w[lane] : 0, vc = lane < TILE_WARPS ? s_cp[lane] : 0;
+            uint32_t vM = lane < TILE_WARPS ? s_M[lane] : 0, vm = lane < TILE_WARPS ? s_m[lane] : 0;
+            // inclusive scans over the 8 warps
+            uint32_t iw = vw, ic = vc, iM = vM, im = vm;
+#pragma unroll
+            for (int o = 1; o < TILE_WARPS; o <<= 1) {
+                uint32_t t0 = __shfl_up_sync(FULL, iw, o), t1 = __shfl_up_sync(FULL, ic, o);
+                uint32_t t2 = __shfl_up_sync(FULL, iM, o), t3 = __shfl_up_sync(FULL, im, o);
+                if (lane >= o) { iw += t0; ic += t1; iM += t2; im += t3; }
+            }
+            uint32_t tw = __shfl_sync(FULL, iw, TILE_WARPS - 1), tc = __shfl_sync(FULL, ic, TILE_WARPS - 1);
+            uint32_t tM = __shfl_sync(FULL, iM, TILE_WARPS - 1), tm = __shfl_sync(FULL, im, TILE_WARPS - 1);
+            unsigned long long pw, pc;
+            lookback(desc, tile, tw, tc, pw, pc, status);
+            uint32_t bM = 0, bm = 0;
+            if (TOPO && lane == 0) {
+                if (tM) bM = atomicAdd(&c->cnt_max, tM);
+                if (tm) bm = atomicAdd(&c->cnt_min, tm);
+            }
+            bM = __shfl_sync(FULL, bM, 0);
+            bm = __shfl_sync(FULL, bm, 0);
+            if (lane < TILE_WARPS) {   // exclusive offsets per warp
+                s_w[lane] = iw - vw;
+                s_cp[lane] = ic - vc;
+                s_M[lane] = bM + iM - vM;
+                s_m[lane] = bm + im - vm;
+            }
+            if (lane == 0) {
+                s_pre_w = pw;
+                s_pre_cp = pc;
+                if (tile == ntiles - 1) {
+                    c->pay_words = pw + tw;
+                    c->k_total = pc + tc;
+                }
+            }
+        }
+        __syncthreads();
+        // ---- phase 2: write this warp's blocks
+        unsigned long long woff = s_pre_w + s_w[warp];
+        unsigned long long cpoff = s_pre_cp + s_cp[warp];
+        uint32_t offM = s_M[warp], offm = s_m[warp];
+        const uint32_t lt = lanemask_lt();
+#pragma unroll
+        for (int j = 0; j < BPW; j++) {
+            const uint32_t b = blk0 + j;
+            if (b >= g.nb) break;
+            const uint32_t w = __shfl_sync(FULL, my_w, j);
+            const int32_t d = dreg[j];
+            if (w) {
+                const uint32_t m = (uint32_t)(d < 0 ? -d : d);
+                uint32_t word = __ballot_sync(FULL, d < 0);
+                for (uint32_t p = 0; p < w; p++) {
+                    uint32_t bp = __ballot_sync(FULL, (m >> p) & 1u);
+                    if (lane == p + 1) word = bp;
+                }
+                if (lane <= w) o.pay[woff + lane] = word;
+                woff += 1 + w;
+            }
+            if (TOPO) {
+                const int lab = (labbits >> (2 * j)) & 3;
+                const uint32_t bM = __ballot_sync(FULL, lab == LAB_MAX);
+                const uint32_t bm = __ballot_sync(FULL, lab == LAB_MIN);
+                const uint32_t bb = bM | bm;
+                if (lab == LAB_MAX || lab == LAB_MIN) {
+                    uint32_t pos = (uint32_t)(cpoff + __popc(bb & lt));
+                    uint32_t key = ord_key(areg[j]);
+                    if (lab == LAB_MAX) listM[offM + __popc(bM & lt)] = make_uint2(key, pos);
+                    else listm[offm + __popc(bm & lt)] = make_uint2(~key, pos);
+                }
+                cpoff += __popc(bb);
+                offM += __popc(bM);
+                offm += __popc(bm);
+            }
+        }
+        if (lane < BPW && blk0 + lane < g.nb) {
+            o.width[blk0 + lane] = (uint8_t)my_w;
+            o.first[blk0 + lane] = my_first;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            uint32_t wi = tile * 2 + threadIdx.x;
+            if (wi < ncw) o.cbits[wi] = s_cbits[threadIdx.x];
+            s_cbits[threadIdx.x] = 0;
+        }
+    }
+    if (lane == 0 && sum_abs) atomicAdd(&c->sum_abs, sum_abs);
+}
+
+// Rank-sequence encoder: the same codec on the delta sequence (Section IV-A:
+// B + LZ and BE again, no QZ).  Length and output offsets are read from the
+// control block, so the launch does not depend on data-dependent sizes.
+__global__ void __launch_bounds__(256) k_encode_ranks(const int32_t* __restrict__ delta, Ctrl* c,
+                                                      Desc* desc, uint8_t* out, int* status) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_w[TILE_WARPS];
+    __shared__ unsigned long long s_pre_w;
+    __shared__ uint32_t s_cbits[2];
+    if (*status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t k = c->k_total;
+    const uint32_t nbd = (uint32_t)cdiv(k, L);
+    const uint32_t ntiles = (nbd + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    const uint32_t ncw = (nbd + 31) / 32;
+    Layout lo;
+    make_layout(c->g.n, c->g.nb, true, c->pay_words, k, 0, lo);
+    uint32_t* cbits = reinterpret_cast<uint32_t*>(out + lo.r1);
+    uint8_t* width = out + lo.r2;
+    int32_t* first = reinterpret_cast<int32_t*>(out + lo.r4);
+    uint32_t* pay = reinterpret_cast<uint32_t*>(out + lo.r5);
+    if (threadIdx.x < 2) s_cbits[threadIdx.x] = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_rank, 1u);
+        __syncthreads();
+        const uint32_t tile = s_tile;
+        if (tile >= ntiles) break;
+        const uint32_t blk0 = tile * TILE_BLOCKS + warp * BPW;
+        int32_t dreg[BPW];
+        uint32_t my_w = 0;
+        int32_t my_first = 0;
+        uint32_t wwords = 0;
+#pragma unroll
+        for (int j = 0; j < BPW; j++) {
+            const uint32_t b = blk0 + j;
+            dreg[j] = 0;
+            if (b < nbd) {
+                const uint64_t i = (uint64_t)b * 32u + lane;
+                const uint32_t nvalid = (uint32_t)min((uint64_t)32, k - (uint64_t)b * 32u);
+                int32_t q = (lane < nvalid) ? delta[i] : 0;
+                int32_t qlast = __shfl_sync(FULL, q, nvalid - 1);
+                if (lane >= nvalid) q = qlast;
+                int32_t prev = __shfl_up_sync(FULL, q, 1);
+                int32_t d = lane ? q - prev : 0;
+                uint32_t m = (uint32_t)(d < 0 ? -d : d);
+                uint32_t w = 32u - __clz(__reduce_max_sync(FULL, m));
+                int32_t f = __shfl_sync(FULL, q, 0);
+                if (lane == j) {
+                    my_w = w;
+                    my_first = f;
+                }
+                dreg[j] = d;
+                wwords += w ? 1u + w : 0u;
+            }
+        }
+        if (lane == 0) s_w[warp] = wwords;
+        {
+            uint32_t cb = __ballot_sync(FULL, lane < BPW && blk0 + lane < nbd && my_w == 0) & 0xFFu;
+            if (lane == 0 && cb) atomicOr(&s_cbits[warp >> 2], cb << ((warp & 3) * 8));
+        }
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t vw = lane < TILE_WARPS ? s_w[lane] : 0, iw = vw;
+#pragma unroll
+            for (int o = 1; o < TILE_WARPS; o <<= 1) {
+                uint32_t t0 = __shfl_up_sync(FULL, iw, o);
+                if (lane >= o) iw += t0;
+            }
+            uint32_t tw = __shfl_sync(FULL, iw, TILE_WARPS - 1);
+            unsigned long long pw, pc;
+            lookback(desc, tile, tw, 0, pw, pc, status);
+            if (lane < TILE_WARPS) s_w[lane] = iw - vw;
+            if (lane == 0) {
+                s_pre_w = pw;
+                if (tile == ntiles - 1) c->rank_words = pw + tw;
+            }
+        }
+        __syncthreads();
+        unsigned long long woff = s_pre_w + s_w[warp];
+#pragma unroll
+        for (int j = 0; j < BPW; j++) {
+            const uint32_t b = blk0 + j;
+            if (b >= nbd) break;
+            const uint32_t w = __shfl_sync(FULL, my_w, j);
+            if (w) {
+                const int32_t d = dreg[j];
+                const uint32_t m = (uint32_t)(d < 0 ? -d : d);
+                uint32_t word = __ballot_sync(FULL, d < 0);
+                for (uint32_t p = 0; p < w; p++) {
+                    uint32_t bp = __ballot_sync(FULL, (m >> p) & 1u);
+                    if (lane == p + 1) word = bp;
+                }
+                if (lane <= w) pay[woff + lane] = word;
+                woff += 1 + w;
+            }
+        }
+        if (lane < BPW && blk0 + lane < nbd) {
+            width[blk0 + lane] = (uint8_t)my_w;
+            first[blk0 + lane] = my_first;
+        }
+        __syncthreads();
+        if (threadIdx.x < 2) {
+            uint32_t wi = tile * 2 + threadIdx.x;
+            if (wi < ncw) cbits[wi] = s_cbits[threadIdx.x];
+            s_cbits[threadIdx.x] = 0;
+        }
+    }
+}
+
+// ================================================================ rank sort
+//
+// LSD radix sort of (key, position) pairs, 8-bit digits, stable.  Both lists
+// (maxima: key = ord(v); minima: key = ~ord(v)) are sorted in the same
+// launches (blockIdx.y selects the list).  Each CTA owns one contiguous range of
+// the list; per-CTA digit histograms are scanned digit-major, so the scatter
+// keeps the input order within a digit.
+
+__device__ __forceinline__ void list_range(uint32_t k, int G, uint32_t& beg, uint32_t& end) {
+    uint32_t chunk = (uint32_t)cdiv(cdiv(k, (uint64_t)G), SORT_TILE) * SORT_TILE;
+    beg = min(k, blockIdx.x * chunk);
+    end = min(k, beg + chunk);
+}
+
+__global__ void __launch_bounds__(256) k_sort_hist(const uint2* src0, const uint2* src1, const Ctrl* c,
+                                                   uint32_t* hist, int shift, int G, const int* status) {
+    __shared__ uint32_t h[256];
+    if (*status) return;
+    const int list = blockIdx.y;
+    const uint2* src = list ? src1 : src0;
+    const uint32_t k = list ? c->cnt_min : c->cnt_max;
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    uint32_t beg, end;
+    list_range(k, G, beg, end);
+    for (uint32_t i = beg + threadIdx.x; i < end; i += blockDim.x)
+        atomicAdd(&h[(src[i].x >> shift) & 0xFFu], 1u);
+    __syncthreads();
+    hist[(size_t)list * 256 * G + (size_t)threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of 256 * G counters per list (one CTA per list)
+__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int G, const int* status) {
+    __shared__ uint32_t part[1024];
+    if (*status) return;
+    uint32_t* hst = hist + (size_t)blockIdx.x * 256 * G;
+    const uint32_t total = 256u * G;
+    const uint32_t per = (total + 1023) / 1024;
+    const uint32_t b = threadIdx.x * per, e = min(total, b + per);
+    uint32_t s = 0;
+    for (uint32_t i = b; i < e; i++) s += hst[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        uint32_t t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += t;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (uint32_t i = b; i < e; i++) {
+        uint32_t v = hst[i];
+        hst[i] = run;
+        run += v;
+    }
+}
+
+// Scatter: a tile of 2048 keys is split into 8 warp slices of 256; each warp
+// counts its digits, a per-digit scan over the warps gives every warp its own
+// running offsets, then each warp places its keys in order (match_any gives the
+// rank among equal digits inside a 32-key step).
+__global__ void __launch_bounds__(256) k_sort_scatter(const uint2* src0, const uint2* src1, uint2* dst0,
+                                                      uint2* dst1, const Ctrl* c, const uint32_t* hist,
+                                                      int shift, int G, const int* status) {
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[TILE_WARPS][256];
+    if (*status) return;
+    const int list = blockIdx.y;
+    const uint2* src = list ? src1 : src0;
+    uint2* dst = list ? dst1 : dst0;
+    const uint32_t k = list ? c->cnt_min : c->cnt_max;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t beg, end;
+    list_range(k, G, beg, end);
+    run[threadIdx.x] = hist[(size_t)list * 256 * G + (size_t)threadIdx.x * G + blockIdx.x];
+    const uint32_t lt = lanemask_lt();
+    for (uint32_t t0 = beg; t0 < end; t0 += SORT_TILE) {
+        for (int d = 0; d < TILE_WARPS; d++) wcnt[d][threadIdx.x] = 0;
+        __syncthreads();
+        uint2 e[SORT_TILE / 256];
+        uint32_t dg[SORT_TILE / 256];
+        const uint32_t ws = t0 + warp * (SORT_TILE / TILE_WARPS);
+#pragma unroll
+        for (int r = 0; r < SORT_TILE / 256; r++) {
+            uint32_t p = ws + r * 32 + lane;
+            bool ok = p < end;
+            e[r] = ok ? src[p] : make_uint2(0, 0);
+            dg[r] = ok ? ((e[r].x >> shift) & 0xFFu) : 256u + lane;
+            uint32_t peers = __match_any_sync(FULL, dg[r]);
+            if (ok && (peers & lt) == 0) wcnt[warp][dg[r]] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        {   // per digit: exclusive over warps, then advance the CTA running offset
+            uint32_t s = run[threadIdx.x];
+#pragma unroll
+            for (int w = 0; w < TILE_WARPS; w++) {
+                uint32_t v = wcnt[w][threadIdx.x];
+                wcnt[w][threadIdx.x] = s;
+                s += v;
+            }
+            run[threadIdx.x] = s;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < SORT_TILE / 256; r++) {
+            uint32_t p = ws + r * 32 + lane;
+            bool ok = p < end;
+            uint32_t peers = __match_any_sync(FULL, dg[r]);
+            if (ok) {
+                uint32_t base = wcnt[warp][dg[r]];
+                dst[base + __popc(peers & lt)] = e[r];
+            }
+            __syncwarp();
+            if (ok && (peers & lt) == 0) wcnt[warp][dg[r]] += __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+}
+
+// ============================================================ dense ranks
+//
+// After sorting, entries of one list are ordered by key; the bin q(v) is
+// monotone in v, so entries of a bin are contiguous.  delta = 1 + number of
+// distinct keys before it in its bin: an inclusive segmented count of
+// "new value" flags with segments at bin changes.  Carried as (h, c): h = a
+// segment starts in the range, c = count since the last segment start.
+
+struct SegCnt {
+    uint32_t h, c;
+};
+__device__ __forceinline__ SegCnt seg_op(SegCnt x, SegCnt y) {
+    return SegCnt{x.h | y.h, y.h ? y.c : x.c + y.c};
+}
+
+__device__ __forceinline__ SegCnt rank_elem(const uint2* s, uint32_t i, int list, float r) {
+    uint32_t kk = s[i].x;
+    if (i == 0) return SegCnt{1, 1};
+    uint32_t kp = s[i - 1].x;
+    float v = key_float(list ? ~kk : kk), vp = key_float(list ? ~kp : kp);
+    bool seg = quantize(v, r) != quantize(vp, r);
+    return SegCnt{seg ? 1u : 0u, (seg || kk != kp) ? 1u : 0u};
+}
+
+// pass 1: aggregate per tile of RANK_TILE entries
+__global__ void __launch_bounds__(256) k_rank_tiles(const uint2* s0, const uint2* s1, const Ctrl* c,
+                                                    uint2* agg, uint32_t agg_stride, int G,
+                                                    const int* status) {
+    __shared__ SegCnt sh[256];
+    if (*status) return;
+    const int list = blockIdx.y;
+    const uint2* s = list ? s1 : s0;
+    const uint32_t k = list ? c->cnt_min : c->cnt_max;
+    const float r = c->r_f;
+    const uint32_t ntiles = (uint32_t)cdiv(k, RANK_TILE);
+    for (uint32_t t = blockIdx.x; t < ntiles; t += G) {
+        SegCnt acc{0, 0};
+        const uint32_t b = t * RANK_TILE + threadIdx.x * (RANK_TILE / 256);
+#pragma unroll 4
+        for (int j = 0; j < RANK_TILE / 256; j++)
+            if (b + j < k) acc = seg_op(acc, rank_elem(s, b + j, list, r));
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            SegCnt tot{0, 0};
+            for (int j = 0; j < 256; j++) tot = seg_op(tot, sh[j]);
+            agg[(size_t)list * agg_stride + t] = make_uint2(tot.h, tot.c);
+        }
+        __syncthreads();
+    }
+}
+
+// pass 2: exclusive scan of tile aggregates (one CTA per list, sequential chunks)
+__global__ void __launch_bounds__(256) k_rank_scan(uint2* agg, uint32_t agg_stride, const Ctrl* c,
+                                                   const int* status) {
+    __shared__ SegCnt sh[256];
+    if (*status) return;
+    const int list = blockIdx.x;
+    const uint32_t k = list ? c->cnt_min : c->cnt_max;
+    const uint32_t ntiles = (uint32_t)cdiv(k, RANK_TILE);
+    uint2* a = agg + (size_t)list * agg_stride;
+    const uint32_t per = (ntiles + 255) / 256;
+    const uint32_t b = threadIdx.x * per, e = min(ntiles, b + per);
+    SegCnt acc{0, 0};
+    for (uint32_t i = b; i < e; i++) acc = seg_op(acc, SegCnt{a[i].x, a[i].y});
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        SegCnt run{0, 0};
+        for (int j = 0; j < 256; j++) {
+            SegCnt v = sh[j];
+            sh[j] = run;
+            run = seg_op(run, v);
+        }
+    }
+    __syncthreads();
+    SegCnt run = sh[threadIdx.x];
+    for (uint32_t i = b; i < e; i++) {
+        SegCnt v{a[i].x, a[i].y};
+        a[i] = make_uint2(run.h, run.c);
+        run = seg_op(run, v);
+    }
+}
+
+// pass 3: per tile, scan with the carried prefix and scatter delta[pos]
+__global__ void __launch_bounds__(256) k_rank_scatter(const uint2* s0, const uint2* s1, const Ctrl* c,
+                                                      const uint2* agg, uint32_t agg_stride,
+                                                      int32_t* delta, int G, const int* status) {
+    __shared__ SegCnt sh[256];
+    if (*status) return;
+    const int list = blockIdx.y;
+    const uint2* s = list ? s1 : s0;
+    const uint32_t k = list ? c->cnt_min : c->cnt_max;
+    const float r = c->r_f;
+    const uint32_t ntiles = (uint32_t)cdiv(k, RANK_TILE);
+    for (uint32_t t = blockIdx.x; t < ntiles; t += G) {
+        SegCnt acc{0, 0};
+        const uint32_t b = t * RANK_TILE + threadIdx.x * (RANK_TILE / 256);
+        SegCnt el[RANK_TILE / 256];
+#pragma unroll
+        for (int j = 0; j < RANK_TILE / 256; j++) {
+            el[j] = (b + j < k) ? rank_elem(s, b + j, list, r) : SegCnt{0, 0};
+            acc = seg_op(acc, el[j]);
+        }
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint2 pre = agg[(size_t)list * agg_stride + t];
+            SegCnt run{pre.x, pre.y};
+            for (int j = 0; j < 256; j++) {
+                SegCnt v = sh[j];
+                sh[j] = run;
+                run = seg_op(run, v);
+            }
+        }
+        __syncthreads();
+        SegCnt run = sh[threadIdx.x];
+#pragma unroll
+        for (int j = 0; j < RANK_TILE / 256; j++) {
+            if (b + j < k) {
+                run = seg_op(run, el[j]);
+                delta[s[b + j].y] = (int32_t)run.c;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ================================================================ finalize
+
+__device__ void zero_bytes(uint8_t* out, uint64_t from, uint64_t to) {
+    for (uint64_t i = from; i < to; i++) out[i] = 0;
+}
+
+template <class T>
+__device__ __forceinline__ void put(uint8_t* h, int off, T v) {
+    *reinterpret_cast<T*>(h + off) = v;
+}
+
+// Header, zero padding between sections, adaptive RBF parameters and the
+// stream size.  Section IV-B(3) picks sigma in [0.5, 1] and k in {3, 5, 7} from
+// the data's neighbour variation; here V = sum |d| / (pairs * max(1, qmax -
+// qmin)) over the integer codes (exact, order independent).
+__global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k_over,
+                           float rbf_sigma_over, const int* status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (*status) {
+        *out_size = 0;
+        return;
+    }
+    const Geo g = c->g;
+    const bool topo = !(c->flags & FLAG_NO_TOPO);
+    const uint64_t k = topo ? c->k_total : 0;
+    Layout lo;
+    make_layout(g.n, g.nb, topo, c->pay_words, k, topo ? c->rank_words : 0, lo);
+    // padding
+    zero_bytes(out, lo.s1 + 4 * cdiv(g.nb, 32), lo.s2);
+    zero_bytes(out, lo.s2 + g.nb, lo.s4);
+    zero_bytes(out, lo.s4 + 4ull * g.nb, lo.s6);
+    zero_bytes(out, lo.s6 + (topo ? 4 * cdiv(g.n, 16) : 0), lo.s5);
+    if (topo) {
+        uint64_t nbd = cdiv(k, L);
+        zero_bytes(out, lo.s5_end, lo.s7);
+        zero_bytes(out, lo.r1 + 4 * cdiv(nbd, 32), lo.r2);
+        zero_bytes(out, lo.r2 + nbd, lo.r4);
+        zero_bytes(out, lo.r4 + 4 * nbd, lo.r5);
+    }
+    // RBF parameters
+    const float r = c->r_f;
+    int64_t qmin = quantize(c->vmin, r), qmax = quantize(c->vmax, r);
+    int64_t span = qmax - qmin;
+    if (span < 1) span = 1;
+    uint64_t pairs = (uint64_t)g.n - g.nb;
+    double V = pairs ? __ddiv_rn((double)c->sum_abs, __dmul_rn((double)pairs, (double)span)) : 0.0;
+    float sigma = rbf_sigma_over > 0.0f
+                      ? rbf_sigma_over
+                      : __double2float_rn(__dadd_rn(0.5, __dmul_rn(0.5, __dsub_rn(1.0, fmin(1.0, __ddiv_rn(V, 0.05))))));
+    int32_t kk = rbf_k_over > 0 ? rbf_k_over : (V < 0.002 ? 7 : (V < 0.02 ? 5 : 3));
+    double s = (double)sigma;
+    float gw[9];
+    for (int d2 = 1; d2 <= 9; d2++)
+        gw[d2 - 1] = __double2float_rn(exp_neg(__ddiv_rn((double)d2, __dmul_rn(__dmul_rn(2.0, s), s))));
+    // header
+    uint8_t* h = out;
+    for (int i = 0; i < (int)HDR; i += 4) put<uint32_t>(h, i, 0u);
+    put<uint32_t>(h, 0, MAGIC);
+    put<uint32_t>(h, 4, VERSION);
+    put<uint32_t>(h, 8, (uint32_t)g.ndim);
+    put<uint32_t>(h, 12, L);
+    put<uint64_t>(h, 16, g.nx);
+    put<uint64_t>(h, 24, g.ny);
+    put<uint64_t>(h, 32, g.nz);
+    put<uint32_t>(h, 40, c->flags & FLAG_NO_TOPO);
+    put<uint32_t>(h, 44, (uint32_t)c->rel);
+    put<double>(h, 48, c->eb);
+    put<double>(h, 56, c->eps);
+    put<float>(h, 64, c->w_f);
+    put<float>(h, 68, c->r_f);
+    put<float>(h, 72, c->h_f);
+    put<uint32_t>(h, 76, (uint32_t)c->const_field);
+    put<float>(h, 80, c->vmin);
+    put<float>(h, 84, c->vmax);
+    put<uint32_t>(h, 88, (uint32_t)kk);
+    put<float>(h, 92, sigma);
+    put<uint32_t>(h, 96, (uint32_t)c->rs_sweeps);
+    put<uint64_t>(h, 104, g.n);
+    put<uint64_t>(h, 112, g.nb);
+    put<uint64_t>(h, 120, topo ? c->cnt_min : 0ull);
+    put<uint64_t>(h, 128, topo ? c->cnt_max : 0ull);
+    put<uint64_t>(h, 136, topo ? c->k_sad : 0ull);
+    put<uint64_t>(h, 144, c->sum_abs);
+    put<uint64_t>(h, 152, lo.s1);
+    put<uint64_t>(h, 160, lo.s2);
+    put<uint64_t>(h, 168, lo.s4);
+    put<uint64_t>(h, 176, lo.s6);
+    put<uint64_t>(h, 184, lo.s5);
+    put<uint64_t>(h, 192, topo ? lo.s7 : lo.end);
+    put<uint64_t>(h, 200, lo.end);
+    put<uint64_t>(h, 208, c->pay_words);
+    put<uint32_t>(h, 216, topo ? (uint32_t)c->rank_words : 0u);
+    for (int i = 0; i < 9; i++) put<float>(h, 220 + 4 * i, gw[i]);
+    *out_size = lo.end;
+}
+
+// saddle count for the header (labels already written)
+__global__ void k_count_saddles(const uint32_t* labels, Ctrl* c, const int* status) {
+    if (*status) return;
+    const uint32_t nwords = (c->g.n + 15) / 16;
+    unsigned long long s = 0;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x) {
+        uint32_t w = labels[i];
+        s += __popc(((w >> 1) & 0x55555555u) & ~w & 0x55555555u);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(&c->k_sad, s);
+}
+
+// ============================================================ host launchers
+
+void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bool topo, int sms,
+                     cudaStream_t st) {
+    uint32_t nchunks = (g.n + 511) / 512;
+    uint32_t blocks = hmin<uint32_t>((nchunks + 7) / 8, (uint32_t)sms * 8);
+    if (blocks == 0) blocks = 1;
+    if (topo) k_range_cd<true, false, true><<<blocks, 256, 0, st>>>(a, g, c, labels, nullptr);
+    else k_range_cd<false, false, true><<<blocks, 256, 0, st>>>(a, g, c, labels, nullptr);
+}
+
+void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsigned long long* counts,
+                            int sms, cudaStream_t st) {
+    uint32_t nchunks = (g.n + 511) / 512;
+    uint32_t blocks = hmin<uint32_t>((nchunks + 7) / 8, (uint32_t)sms * 8);
+    if (blocks == 0) blocks = 1;
+    if (counts) {
+        k_range_cd<true, true, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, counts);
+        k_count_regular<<<1, 1, 0, st>>>(g.n, counts);
+    } else {
+        k_range_cd<true, false, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, nullptr);
+    }
+}
+
+// Section III-B error classes between two packed label maps.
+__global__ void k_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsigned long long* out) {
+    __shared__ unsigned long long sh[12];
+    if (threadIdx.x < 12) sh[threadIdx.x] = 0;
+    __syncthreads();
+    const uint64_t nwords = (n + 15) / 16;
+    unsigned long long loc[12];
+    for (int i = 0; i < 12; i++) loc[i] = 0;
+    for (uint64_t w = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; w < nwords;
+         w += (uint64_t)gridDim.x * blockDim.x) {
+        uint32_t x = a[w], y = b[w];
+        uint32_t diff = x ^ y;
+        while (diff) {
+            int bit = (__ffs(diff) - 1) & ~1;
+            diff &= ~(3u << bit);
+            int ta = (x >> bit) & 3, tb = (y >> bit) & 3;
+            if (tb == LAB_R) loc[0 * 4 + ta]++;
+            else if (ta == LAB_R) loc[1 * 4 + tb]++;
+            else loc[2 * 4 + ta]++;
+        }
+    }
+    for (int i = 0; i < 12; i++)
+        if (loc[i]) atomicAdd(&sh[i], loc[i]);
+    __syncthreads();
+    if (threadIdx.x < 12 && sh[threadIdx.x]) atomicAdd(&out[threadIdx.x], sh[threadIdx.x]);
+}
+
+void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsigned long long* out12, int sms,
+                        cudaStream_t st) {
+    uint64_t nwords = (n + 15) / 16;
+    uint32_t blocks = (uint32_t)hmin<uint64_t>((nwords + 255) / 256, (uint64_t)sms * 4);
+    if (blocks == 0) blocks = 1;
+    k_topo_errors<<<blocks, 256, 0, st>>>(a, b, n, out12);
+}
+
+void launch_qparams(Ctrl* c, int* status, cudaStream_t st) { k_qparams<<<1, 32, 0, st>>>(c, status); }
+
+void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, Desc* desc, uint8_t* out,
+                         const Layout& lo, uint2* listM, uint2* listm, bool topo, uint32_t nb, int sms,
+                         int* status, cudaStream_t st) {
+    EncOut o{reinterpret_cast<uint32_t*>(out + lo.s1), out + lo.s2,
+             reinterpret_cast<int32_t*>(out + lo.s4), reinterpret_cast<uint32_t*>(out + lo.s5)};
+    uint32_t ntiles = (nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    uint32_t grid = hmin<uint32_t>(ntiles, (uint32_t)sms * 6);
+    if (grid == 0) grid = 1;
+    if (topo) k_encode_field<true><<<grid, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
+    else k_encode_field<false><<<grid, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
+}
+
+void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint32_t* hist,
+                  uint2* agg, uint32_t agg_stride, int32_t* delta, int G, int* status, cudaStream_t st) {
+    dim3 grid(G, 2);
+    uint2 *a0 = listM, *a1 = listm, *b0 = tmpM, *b1 = tmpm;
+    for (int pass = 0; pass < 4; pass++) {
+        int shift = 8 * pass;
+        k_sort_hist<<<grid, 256, 0, st>>>(a0, a1, c, hist, shift, G, status);
+        k_sort_scan<<<2, 1024, 0, st>>>(hist, G, status);
+        k_sort_scatter<<<grid, 256, 0, st>>>(a0, a1, b0, b1, c, hist, shift, G, status);
+        uint2* t0 = a0; a0 = b0; b0 = t0;
+        uint2* t1 = a1; a1 = b1; b1 = t1;
+    }
+    // after 4 passes the sorted data is back in listM / listm
+    k_rank_tiles<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, G, status);
+    k_rank_scan<<<2, 256, 0, st>>>(agg, agg_stride, c, status);
+    k_rank_scatter<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, delta, G, status);
+}
+
+void launch_encode_ranks(const int32_t* delta, Ctrl* c, Desc* desc, uint8_t* out, uint32_t max_tiles,
+                         int sms, int* status, cudaStream_t st) {
+    uint32_t grid = hmin<uint32_t>(max_tiles, (uint32_t)sms * 6);
+    if (grid == 0) grid = 1;
+    k_encode_ranks<<<grid, 256, 0, st>>>(delta, c, desc, out, status);
+}
+
+void launch_count_saddles(const uint32_t* labels, Ctrl* c, uint32_t n, int sms, int* status,
+                          cudaStream_t st) {
+    uint32_t nwords = (n + 15) / 16;
+    uint32_t blocks = hmin<uint32_t>((nwords + 255) / 256, (uint32_t)sms * 4);
+    if (blocks == 0) blocks = 1;
+    k_count_saddles<<<blocks, 256, 0, st>>>(labels, c, status);
+}
+
+void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, float rbf_sigma,
+                     int* status, cudaStream_t st) {
+    k_finalize<<<1, 32, 0, st>>>(c, out, out_size, rbf_k, rbf_sigma, status);
+}
+
+}  // namespace tsz

@@ -1,0 +1,57 @@
+// tsz_internal.h -- declarations shared by the kernel files and the C-ABI layer.
+#pragma once
+
+#include "tsz_common.cuh"
+
+namespace tsz {
+
+constexpr int SORT_TILE = 2048;   // keys per sort step of one CTA
+constexpr int RANK_TILE = 2048;   // entries per dense-rank tile
+
+// ---- workspace carving (all offsets 256-byte aligned)
+struct CompressWs {
+    uint64_t ctrl, desc, rdesc, listM, listm, tmpM, tmpm, hist, agg, delta, end;
+    uint32_t list_cap, ntiles, rank_tiles, agg_stride;
+    int G;
+};
+struct DecompressWs {
+    uint64_t ctrl, desc, rdesc, cp_idx, delta, newv, sad, sadv, end;
+    uint32_t ntiles, rank_tiles, sad_cap;
+};
+CompressWs compress_ws(uint64_t n);
+DecompressWs decompress_ws(uint64_t n);
+
+// ---- compression launchers (tsz_compress.cu)
+void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bool topo, int sms,
+                     cudaStream_t st);
+void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsigned long long* counts,
+                            int sms, cudaStream_t st);
+void launch_qparams(Ctrl* c, int* status, cudaStream_t st);
+void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, Desc* desc, uint8_t* out,
+                         const Layout& lo, uint2* listM, uint2* listm, bool topo, uint32_t nb, int sms,
+                         int* status, cudaStream_t st);
+void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint32_t* hist,
+                  uint2* agg, uint32_t agg_stride, int32_t* delta, int G, int* status, cudaStream_t st);
+void launch_encode_ranks(const int32_t* delta, Ctrl* c, Desc* desc, uint8_t* out, uint32_t max_tiles,
+                         int sms, int* status, cudaStream_t st);
+void launch_count_saddles(const uint32_t* labels, Ctrl* c, uint32_t n, int sms, int* status,
+                          cudaStream_t st);
+void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, float rbf_sigma,
+                     int* status, cudaStream_t st);
+
+// ---- decompression launchers (tsz_decompress.cu)
+void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c, int* status,
+                         cudaStream_t st);
+void launch_decode_field(const uint8_t* in, Ctrl* c, Desc* desc, float* out, uint32_t* cp_idx,
+                         uint32_t ntiles, int sms, int* status, cudaStream_t st);
+void launch_decode_ranks(const uint8_t* in, Ctrl* c, Desc* desc, int32_t* delta, uint32_t max_tiles,
+                         int sms, int* status, cudaStream_t st);
+cudaError_t launch_fixup(const uint8_t* in, Ctrl* c, float* out, const uint32_t* cp_idx,
+                         const int32_t* delta, float* newv, uint32_t* sad, float* sadv, uint32_t sad_cap,
+                         int sms, int* status, cudaStream_t st);
+
+// ---- analysis
+void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsigned long long* out12,
+                        int sms, cudaStream_t st);
+
+}  // namespace tsz

@@ -1,0 +1,93 @@
+"""The C-ABI library builds, loads, exports every symbol include/toposzp.h
+declares, and its host-only functions behave (no GPU needed: none of these
+calls reaches a CUDA API)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_17552_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "toposzp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(toposzp_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_exports(lib):
+    names = declared_symbols()
+    assert set(names) == set(_lib.EXPORTS)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_status_strings_and_defaults(lib):
+    for code in range(9):
+        s = lib.toposzp_status_string(code)
+        assert s and s != b"unknown status"
+    p = _lib.Params()
+    lib.toposzp_default_params(ctypes.byref(p))
+    assert (p.flags, p.rs_sweeps, p.rbf_k, p.rbf_sigma) == (0, 1, 0, 0.0)
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (1800, 3600), (1, 1), (1, 37), (7, 9, 11), (3, 1, 5)])
+def test_bounds_cover_the_oracle_stream(lib, shape):
+    nd = len(shape)
+    dims = _lib.dims3(nd, tuple(reversed(shape)))
+    bound = lib.toposzp_compress_bound(nd, dims)
+    assert bound >= 256
+    if np.prod(shape) <= 4096:
+        rng = np.random.default_rng(0)
+        a = rng.normal(size=shape).astype(np.float32)
+        assert len(oracle.compress(a, 1e-4, rel=True)) <= bound
+    assert lib.toposzp_compress_workspace_size(nd, dims) > 0
+    assert lib.toposzp_decompress_workspace_size(nd, dims) > 0
+
+
+def test_invalid_arguments_rejected_on_host(lib):
+    dims = _lib.dims3(2, (8, 8))
+    p = _lib.Params()
+    lib.toposzp_default_params(ctypes.byref(p))
+    fake = ctypes.c_void_p(256)   # never dereferenced: checks fail first
+    assert lib.toposzp_compress(None, 2, dims, 1, 1e-3, ctypes.byref(p), fake, 1 << 20, fake, fake,
+                                1 << 20, fake, None) == _lib.INVALID_ARG
+    assert lib.toposzp_compress(fake, 4, dims, 1, 1e-3, ctypes.byref(p), fake, 1 << 20, fake, fake,
+                                1 << 20, fake, None) == _lib.INVALID_ARG
+    assert lib.toposzp_compress(fake, 2, dims, 1, -1.0, ctypes.byref(p), fake, 1 << 20, fake, fake,
+                                1 << 20, fake, None) == _lib.INVALID_ARG
+    assert lib.toposzp_compress(fake, 2, dims, 1, 1e-3, ctypes.byref(p), fake, 10, fake, fake,
+                                1 << 20, fake, None) == _lib.BUFFER_TOO_SMALL
+    assert lib.toposzp_compress(fake, 2, dims, 1, 1e-3, ctypes.byref(p), fake, 1 << 20, fake, fake,
+                                16, fake, None) == _lib.BUFFER_TOO_SMALL
+    big = _lib.dims3(3, (2048, 2048, 1024))
+    assert lib.toposzp_compress(fake, 3, big, 1, 1e-3, ctypes.byref(p), fake, 1 << 20, fake, fake,
+                                1 << 20, fake, None) == _lib.UNSUPPORTED
+    p.rbf_k = 4
+    assert lib.toposzp_compress(fake, 2, dims, 1, 1e-3, ctypes.byref(p), fake, 1 << 20, fake, fake,
+                                1 << 20, fake, None) == _lib.INVALID_ARG
+    assert lib.toposzp_decompress(fake, 100, fake, 0, fake, 1 << 20, fake, None) == _lib.INVALID_ARG
+
+
+def test_inspect_reads_oracle_header(lib):
+    a = np.random.default_rng(1).normal(size=(6, 10, 12)).astype(np.float32)
+    buf = oracle.compress(a, 1e-3, rel=True)
+    info = _lib.Info()
+    cbuf = ctypes.create_string_buffer(buf[:256], 256)
+    assert lib.toposzp_inspect(cbuf, 256, ctypes.byref(info)) == 0
+    h = oracle.header(buf)
+    assert info.ndim == 3 and list(info.dims) == [12, 10, 6] and info.n == a.size
+    assert info.total_size == len(buf) and info.k_min == h["k_min"] and info.k_max == h["k_max"]
+    bad = ctypes.create_string_buffer(b"XXXX" + buf[4:256], 256)
+    assert lib.toposzp_inspect(bad, 256, ctypes.byref(info)) == _lib.CORRUPT_STREAM

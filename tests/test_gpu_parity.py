@@ -1,0 +1,179 @@
+"""CUDA path against the CPU oracle, element by element.
+
+Bit-exact on everything: the compressed stream (every header field, section
+and padding byte), the decompressed float32 values, and the critical-point
+labels.  Inputs are seeded synthetic fields; sizes span several 2048-point
+tiles with ragged tails, degenerate shapes, and the full workload sizes.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2602_17552_gb300 import _lib, codec, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def section_report(a: bytes, b: bytes) -> str:
+    """Name the first differing byte by stream section (for failure messages)."""
+    n = min(len(a), len(b))
+    diff = next((i for i in range(n) if a[i] != b[i]), n)
+    h = oracle.header(b) if len(b) >= 256 else {}
+    names = ["off_s1", "off_s2", "off_s4", "off_s6", "off_s5", "off_s7", "total"]
+    where = "header"
+    for k in names:
+        if k in h and diff >= h[k]:
+            where = k
+    return f"len gpu {len(a)} oracle {len(b)}; first diff at byte {diff} ({where})"
+
+
+def gpu_roundtrip(a: np.ndarray, eb: float, rel: bool, **kw):
+    f = torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    buf = codec.compress(f, eb, "rel" if rel else "abs", **kw)
+    out = codec.decompress(buf, a.shape)
+    return buf.cpu().numpy().tobytes(), out.cpu().numpy()
+
+
+def assert_parity(a, eb, rel=True, **kw):
+    okw = dict(no_topo=kw.get("no_topo", False), rs_sweeps=kw.get("rs_sweeps", 1),
+               rbf_k=kw.get("rbf_k", 0), rbf_sigma=kw.get("rbf_sigma", 0.0))
+    gbuf, gout = gpu_roundtrip(a, eb, rel, **okw)
+    obuf = oracle.compress(a, eb, rel=rel, **okw)
+    assert gbuf == obuf, section_report(gbuf, obuf)
+    oout = oracle.decompress(obuf, a.shape)
+    assert np.array_equal(gout.view(np.uint32), oout.view(np.uint32)), \
+        f"{np.count_nonzero(gout.view(np.uint32) != oout.view(np.uint32))} decoded values differ"
+    return obuf, oout
+
+
+SMALL = [
+    ("bumps256_abs", lambda: synth.gaussian_bumps_2d().numpy(), None),
+    ("climate_300x517", lambda: synth.climate_2d(300, 517, seed=2).numpy(), None),
+    ("turb_24", lambda: synth.turbulence_3d(24, seed=3).numpy(), None),
+    ("mixed3d_45x37x29", lambda: synth.grf((29, 37, 45), -11 / 3, 4).numpy(), None),
+    ("adv2d_133x71", lambda: synth.adversarial_small(1, (133, 71)).numpy(), None),
+    ("adv3d_17x9x13", lambda: synth.adversarial_small(2, (17, 9, 13)).numpy(), None),
+]
+
+
+@pytest.mark.parametrize("name,make,_", SMALL, ids=[s[0] for s in SMALL])
+@pytest.mark.parametrize("eb", [1e-2, 1e-3, 1e-4])
+def test_parity_small(name, make, _, eb):
+    a = make()
+    assert_parity(a, eb, rel=True)
+
+
+def test_parity_config1_abs_bound():
+    """256x256 bumps, absolute bound 1e-3 of the value range."""
+    a = synth.gaussian_bumps_2d().numpy()
+    eb = 1e-3 * float(a.max() - a.min())
+    buf, out = assert_parity(a, eb, rel=False)
+    la, lo = oracle.critical_points(a), oracle.critical_points(out)
+    e = oracle.topo_errors(la, lo)
+    assert e[1].sum() == 0 and e[2].sum() == 0
+
+
+@pytest.mark.parametrize("shape", [(1, 1), (1, 37), (37, 1), (2, 2), (3, 3), (1, 1, 40), (5, 1, 7),
+                                   (3, 3, 3), (1, 33), (4, 8, 1), (2, 1025)])
+def test_parity_degenerate_shapes(shape):
+    rng = np.random.default_rng(sum(shape))
+    a = rng.integers(-4, 5, size=shape).astype(np.float32) * np.float32(0.25)
+    assert_parity(a, 1e-2, rel=True)
+    assert_parity(a, 0.3, rel=False)
+
+
+def test_parity_constant_and_tiny_range():
+    assert_parity(np.full((37, 41), -2.5, np.float32), 1e-3, rel=True)
+    assert_parity(np.zeros((9, 10, 11), np.float32), 1e-3, rel=True)
+    a = np.full((64, 70), 1.0, np.float32)
+    a[10, 10] = np.float32(1.001)
+    assert_parity(a, 0.01, rel=True)
+    # a one-ulp range makes eps ~ 6e-8: too small for M = 1 on both sides
+    a[10, 10] = np.nextafter(np.float32(1), np.float32(2))
+    with pytest.raises(oracle.OracleError) as eo:
+        oracle.compress(a, 0.5, rel=True)
+    with pytest.raises(_lib.TopoSZpError) as eg:
+        codec.compress(torch.from_numpy(a).cuda(), 0.5, "rel")
+    assert eo.value.status == eg.value.status == _lib.EB_TOO_SMALL
+
+
+def test_parity_negative_zero_and_denormals():
+    rng = np.random.default_rng(3)
+    a = rng.choice(np.array([-0.0, 0.0, 1e-40, -1e-40, 1e-38, -2e-38], np.float32), size=(50, 60))
+    assert_parity(a.astype(np.float32), 0.25, rel=True)
+
+
+@pytest.mark.parametrize("opts", [dict(no_topo=True), dict(rbf_k=3, rbf_sigma=1.0), dict(rbf_k=5),
+                                  dict(rbf_k=7, rbf_sigma=0.6), dict(rs_sweeps=3)])
+def test_parity_params(opts):
+    a = synth.climate_2d(120, 250, seed=9).numpy()
+    assert_parity(a, 1e-2, rel=True, **opts)
+    b = synth.turbulence_3d(20, seed=5).numpy()
+    assert_parity(b, 1e-3, rel=True, **opts)
+
+
+def test_deterministic_across_calls():
+    a = torch.from_numpy(synth.turbulence_3d(32, seed=8).numpy()).cuda()
+    outs = [codec.compress(a, 1e-3, "rel").cpu().numpy().tobytes() for _ in range(3)]
+    assert outs[0] == outs[1] == outs[2]
+
+
+@pytest.mark.parametrize("shape", [(256, 256), (90, 333), (12, 40, 41), (1, 77)])
+def test_critical_points_and_topo_errors(shape):
+    rng = np.random.default_rng(7)
+    a = rng.integers(0, 5, size=shape).astype(np.float32)
+    f = torch.from_numpy(a).cuda()
+    words, cnt = codec.critical_points(f)
+    lab = codec.unpack_labels(words, a.size).cpu().numpy().reshape(shape)
+    want = oracle.critical_points(a)
+    assert np.array_equal(lab, want)
+    assert cnt.cpu().tolist() == [int((want == t).sum()) for t in range(4)]
+    b = a + rng.integers(0, 2, size=shape).astype(np.float32)
+    wb, _ = codec.critical_points(torch.from_numpy(b).cuda())
+    e = codec.topo_errors(words, wb, a.size).cpu().numpy()
+    assert np.array_equal(e, oracle.topo_errors(want, oracle.critical_points(b)).astype(np.int64))
+
+
+def test_device_errors_reported():
+    a = synth.gaussian_bumps_2d(40, 50, count=5, seed=2).numpy()
+    bad = a.copy()
+    bad[3, 4] = np.inf
+    with pytest.raises(_lib.TopoSZpError) as ei:
+        codec.compress(torch.from_numpy(bad).cuda(), 1e-3, "rel")
+    assert ei.value.status == _lib.NONFINITE
+    big = (a * 1e6).astype(np.float32)
+    with pytest.raises(_lib.TopoSZpError) as ei:
+        codec.compress(torch.from_numpy(big).cuda(), 1e-3 * 2 ** -20, "abs")
+    assert ei.value.status == _lib.EB_TOO_SMALL
+    buf = codec.compress(torch.from_numpy(a).cuda(), 1e-3, "rel")
+    for corrupt in (buf[:200].clone(), torch.cat([buf[:100], buf[100:].flip(0)])):
+        with pytest.raises(_lib.TopoSZpError) as ei:
+            codec.decompress(corrupt, a.shape)
+        assert ei.value.status == _lib.CORRUPT_STREAM
+    with pytest.raises(_lib.TopoSZpError):
+        codec.decompress(buf, (a.shape[0] + 1, a.shape[1]))
+    # a damaged payload must never read outside the buffer: widths inflated to 32
+    h = oracle.header(buf.cpu().numpy().tobytes())
+    dmg = buf.clone()
+    dmg[h["off_s2"]:h["off_s2"] + 16] = 32
+    with pytest.raises(_lib.TopoSZpError) as ei:
+        codec.decompress(dmg, a.shape)
+    assert ei.value.status == _lib.CORRUPT_STREAM
+
+
+def test_parity_config2_full():
+    """1800 x 3600 climate-like field, relative bounds 1e-2, 1e-3, 1e-4."""
+    a = synth.climate_2d(1800, 3600, seed=2, device="cuda").cpu().numpy()
+    for eb in (1e-2, 1e-3, 1e-4):
+        buf, out = assert_parity(a, eb, rel=True)
+        dev = np.abs(a.astype(np.float64) - out).max()
+        assert dev <= 2 * oracle.header(buf)["eps"]
+
+
+@pytest.mark.slow
+def test_parity_config3_full():
+    """512^3 turbulence-like log-normal field, relative bounds 1e-3 and 1e-5."""
+    a = synth.turbulence_3d(512, seed=3, device="cuda").cpu().numpy()
+    for eb in (1e-3, 1e-5):
+        assert_parity(a, eb, rel=True)
