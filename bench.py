@@ -45,6 +45,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256"])
     ap.add_argument("--eb", type=float, default=1e-3)
+    ap.add_argument("--side", type=int, default=512, help="edge of the 3D turbulence field")
     ap.add_argument("--no-topo", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU-baseline work")
@@ -52,10 +53,10 @@ def parse_args():
     return ap.parse_args()
 
 
-def workload_spec(name, eb):
+def workload_spec(name, eb, side=512):
     from paper_2602_17552_gb300 import synth
     if name == "turb512":
-        return synth.turb_512(eb)
+        return synth.turb_512(eb, n=side)
     if name == "climate":
         return synth.climate_1800x3600(eb)
     return synth.bumps_256()
@@ -177,7 +178,7 @@ def run_reference(args):
     ws, rank, local = dist_setup(args)
     if rank != 0:
         return
-    spec = workload_spec(args.workload, args.eb)
+    spec = workload_spec(args.workload, args.eb, args.side)
     field = spec.make("cuda" if torch.cuda.is_available() else "cpu").cpu()
     eb_abs = args.eb * float(field.max() - field.min()) if spec.eb_mode != "rel" else args.eb
     per_step = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
@@ -214,7 +215,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    spec = workload_spec(args.workload, args.eb)
+    spec = workload_spec(args.workload, args.eb, args.side)
     from dataclasses import replace
     spec = replace(spec, seed=spec.seed + 1000 * rank)
     field = spec.make(dev)
@@ -233,10 +234,7 @@ def run_ours(args):
     rec = torch.empty_like(field)
     stream = torch.cuda.current_stream(dev)
 
-    def step(events=None):
-        if events is not None:
-            arr = (ctypes.c_void_p * 9)(*[e.cuda_event for e in events])
-            L.toposzp_set_stage_events(arr, 9)
+    def step():
         codec.compress_async(field, eb, mode, params=params, out=out, ws=cws, size=size, status=st_c)
         codec.decompress_async(out, field.shape, out=rec, ws=dws, status=st_d)
 
@@ -248,8 +246,12 @@ def run_ours(args):
     info = codec.inspect(out)
     csize = int(size.item())
 
-    # ---- timed region
+    # ---- timed region.  torch creates CUDA events lazily: record each stage
+    # event once so its handle exists before the library records it again.
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(9)] for _ in range(args.steps)]
+    for es in ev:
+        for e in es:
+            e.record(stream)
     outer = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if pg:
@@ -259,7 +261,8 @@ def run_ours(args):
         outer[0].record(stream)
         for s in range(args.steps):
             arr = (ctypes.c_void_p * 9)(*[e.cuda_event for e in ev[s]])
-            L.toposzp_set_stage_events(arr, 9)
+            if L.toposzp_set_stage_events(arr, 9) != 0:
+                raise RuntimeError("toposzp_set_stage_events rejected the event handles")
             codec.compress_async(field, eb, mode, params=params, out=out, ws=cws, size=size, status=st_c)
             mids[s].record(stream)
             codec.decompress_async(out, field.shape, out=rec, ws=dws, status=st_d)
