@@ -14,7 +14,7 @@ namespace tsz {
 static uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
 constexpr uint64_t CTRL_BYTES = 4096;
-constexpr int SORT_G = 1024;   // CTAs per list in the rank sort (fixed: sizes the workspace)
+constexpr int SORT_G = 256;    // CTAs per list in the rank sort (fixed: sizes the workspace)
 
 static_assert(sizeof(Ctrl) <= CTRL_BYTES, "control block too large");
 
@@ -74,8 +74,12 @@ DecompressWs decompress_ws(uint64_t n) {
     w.sad_cap = (uint32_t)n;
     uint64_t o = 0;
     w.ctrl = o; o = a256(o + CTRL_BYTES);
-    w.desc = o; o = a256(o + 16ull * (w.ntiles + 1));
     w.rdesc = o; o = a256(o + 16ull * (w.rank_tiles + 1));
+    w.flags = o; o = a256(o + 4ull * (w.ntiles + 1));
+    w.tile_w = o; o = a256(o + 4ull * (w.ntiles + 1));
+    w.tile_c = o; o = a256(o + 4ull * (w.ntiles + 1));
+    w.pay_pre = o; o = a256(o + 8ull * (w.ntiles + 1));
+    w.cp_pre = o; o = a256(o + 4ull * (w.ntiles + 1));
     w.cp_idx = o; o = a256(o + 4ull * (n + 2));
     w.delta = o; o = a256(o + 4ull * (n + 2));
     w.newv = o; o = a256(o + 4ull * (n + 2));
@@ -255,19 +259,23 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
     Ctrl* c = reinterpret_cast<Ctrl*>(ws + w.ctrl);
     const int sms = sm_count();
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
-    cudaMemsetAsync(ws, 0, w.cp_idx, st);   // control block and look-back descriptors
+    cudaMemsetAsync(ws, 0, w.tile_w, st);   // control block, rank look-back descriptors, stage flags
     launch_parse_header(src, in_size, n_out, c, status, st);
-    stage(5, st);
-    launch_decode_field(src, c, reinterpret_cast<Desc*>(ws + w.desc), out,
-                        reinterpret_cast<uint32_t*>(ws + w.cp_idx), w.ntiles, sms, status, st);
-    stage(6, st);
+    launch_dec_offsets(src, c, reinterpret_cast<uint32_t*>(ws + w.tile_w), reinterpret_cast<uint32_t*>(ws + w.tile_c),
+                       reinterpret_cast<unsigned long long*>(ws + w.pay_pre), reinterpret_cast<uint32_t*>(ws + w.cp_pre),
+                       w.ntiles, sms, status, st);
     launch_decode_ranks(src, c, reinterpret_cast<Desc*>(ws + w.rdesc),
                         reinterpret_cast<int32_t*>(ws + w.delta), w.rank_tiles, sms, status, st);
+    stage(5, st);
+    launch_decode_fused(src, c, out, reinterpret_cast<unsigned long long*>(ws + w.pay_pre),
+                        reinterpret_cast<uint32_t*>(ws + w.cp_pre), reinterpret_cast<int32_t*>(ws + w.delta),
+                        reinterpret_cast<uint32_t*>(ws + w.cp_idx), reinterpret_cast<float*>(ws + w.newv),
+                        reinterpret_cast<uint32_t*>(ws + w.flags), reinterpret_cast<uint32_t*>(ws + w.sad),
+                        w.sad_cap, sms, status, st);
+    stage(6, st);
     stage(7, st);
-    cudaError_t e = launch_fixup(src, c, out, reinterpret_cast<uint32_t*>(ws + w.cp_idx),
-                                 reinterpret_cast<int32_t*>(ws + w.delta), reinterpret_cast<float*>(ws + w.newv),
-                                 reinterpret_cast<uint32_t*>(ws + w.sad), reinterpret_cast<float*>(ws + w.sadv),
-                                 w.sad_cap, sms, status, st);
+    cudaError_t e = launch_saddle_rounds(src, c, out, reinterpret_cast<uint32_t*>(ws + w.sad),
+                                         reinterpret_cast<float*>(ws + w.sadv), w.sad_cap, sms, status, st);
     if (e != cudaSuccess) return TOPOSZP_ERR_CUDA;
     stage(8, st);
     return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;

@@ -96,6 +96,8 @@ struct Ctrl {
     // decode-side bookkeeping
     unsigned long long stat_restored, stat_skipped, stat_saddle;
     unsigned int sad_cnt[8];
+    unsigned int front[4];    // per-stage frontiers of the fused decoder
+    unsigned int tile_fused, pad5[3];
     Layout lo;
     float g_rbf[9];
 };

@@ -101,6 +101,144 @@ __global__ void __launch_bounds__(256) k_range_cd(const float* __restrict__ a, c
     }
 }
 
+// ------------------------------------------------- range + CD, vector path
+//
+// For nx % 4 == 0 (rows start on 16-byte boundaries): lane l of a warp owns
+// the quad of points [4q, 4q+4) of a 128-point chunk, so the field, the rows
+// above/below and the planes before/after are single float4 loads, and the x
+// neighbours of a quad come from the adjacent lanes by shuffle.  Points in rows
+// with all y/z neighbours present take a branch-free comparison path; boundary
+// rows fall back to the general rule.  Coordinates advance by the grid stride
+// without divisions.
+
+// Section IV-A(1) at a point whose y (and z) pairs exist: per axis, H = both
+// neighbours higher, L = both lower; m = all H, M = all L, s = every axis H or
+// L with at least one of each.  `xl`/`xr` false: that x neighbour is absent.
+__device__ __forceinline__ uint32_t cd_fast(float v, float l, float r, bool xl, bool xr, float ym, float yp,
+                                            float zm, float zp, bool three) {
+    const bool hl = !xl || l > v, hr = !xr || r > v, ll = !xl || l < v, lr = !xr || r < v;
+    const bool Hx = hl && hr, Lx = ll && lr;
+    const bool Hy = ym > v && yp > v, Ly = ym < v && yp < v;
+    const bool Hz = !three || (zm > v && zp > v), Lz = !three || (zm < v && zp < v);
+    const bool m = Hx && Hy && Hz, M = Lx && Ly && Lz;
+    const bool s = xl && xr && (Hx || Lx) && (Hy || Ly) && (Hz || Lz) && !m && !M;
+    return (uint32_t)(m | M) | ((uint32_t)(s | M) << 1);
+}
+
+template <bool TOPO, bool COUNTS, bool STATS>
+__global__ void __launch_bounds__(256) k_range_cd_vec(const float* __restrict__ a, const Geo g, Ctrl* c,
+                                                      uint32_t* __restrict__ labels,
+                                                      unsigned long long* counts) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = (g.n + 127) / 128;
+    const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    const bool three = g.ndim == 3;
+    // coordinates of this lane's first quad, and the grid stride in (x, y, z) digits
+    uint32_t x, y, z;
+    {
+        const uint64_t i0 = (uint64_t)warp0 * 128 + 4u * lane;
+        coords(g, i0 < g.n ? (uint32_t)i0 : 0u, x, y, z);
+    }
+    const uint64_t S = (uint64_t)nwarps * 128;
+    const uint32_t sx = (uint32_t)(S % g.nx);
+    const uint64_t sr = S / g.nx;
+    const uint32_t sy = (uint32_t)(sr % g.ny);
+    const uint32_t sz = (uint32_t)(sr / g.ny);
+    float vmin = __int_as_float(0x7F800000), vmax = __int_as_float(0xFF800000);
+    bool bad = false;
+    unsigned long long cm = 0, cs = 0, cM = 0;
+    GlobalVal val{a};
+    for (uint32_t ch = warp0; ch < nchunks; ch += nwarps) {
+        const uint32_t i0 = ch * 128u + 4u * lane;
+        const bool active = i0 < g.n;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (active) v = __ldg(reinterpret_cast<const float4*>(a + i0));
+        if (STATS && active) {
+            vmin = fminf(fminf(vmin, v.x), fminf(v.y, fminf(v.z, v.w)));
+            vmax = fmaxf(fmaxf(vmax, v.x), fmaxf(v.y, fmaxf(v.z, v.w)));
+            bad |= !(fabsf(v.x) <= 3.402823466e38f) || !(fabsf(v.y) <= 3.402823466e38f) ||
+                   !(fabsf(v.z) <= 3.402823466e38f) || !(fabsf(v.w) <= 3.402823466e38f);
+        }
+        if (TOPO) {
+            float left = __shfl_up_sync(FULL, v.w, 1);
+            float right = __shfl_down_sync(FULL, v.x, 1);
+            const bool xl = x > 0, xr = x + 4 < g.nx;
+            if (active && lane == 0 && xl) left = __ldg(a + i0 - 1);
+            if (active && lane == 31 && xr) right = __ldg(a + i0 + 4);
+            uint32_t bits = 0;
+            if (active) {
+                const bool inner = y > 0 && y + 1 < g.ny && (!three || (z > 0 && z + 1 < g.nz));
+                if (inner) {
+                    const float4 ym = __ldg(reinterpret_cast<const float4*>(a + i0 - g.nx));
+                    const float4 yp = __ldg(reinterpret_cast<const float4*>(a + i0 + g.nx));
+                    float4 zm = ym, zp = yp;
+                    if (three) {
+                        zm = __ldg(reinterpret_cast<const float4*>(a + i0 - g.nxy));
+                        zp = __ldg(reinterpret_cast<const float4*>(a + i0 + g.nxy));
+                    }
+                    bits = cd_fast(v.x, left, v.y, xl, true, ym.x, yp.x, zm.x, zp.x, three) |
+                           cd_fast(v.y, v.x, v.z, true, true, ym.y, yp.y, zm.y, zp.y, three) << 2 |
+                           cd_fast(v.z, v.y, v.w, true, true, ym.z, yp.z, zm.z, zp.z, three) << 4 |
+                           cd_fast(v.w, v.z, right, true, xr, ym.w, yp.w, zm.w, zp.w, three) << 6;
+                } else {
+                    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                    for (int j = 0; j < 4; j++)
+                        bits |= (uint32_t)classify(val, g, i0 + j, x + j, y, z, vv[j]) << (2 * j);
+                }
+            }
+            // four lanes make one 16-point label word
+            const uint32_t b1 = __shfl_down_sync(FULL, bits, 1);
+            const uint32_t b2 = __shfl_down_sync(FULL, bits, 2);
+            const uint32_t b3 = __shfl_down_sync(FULL, bits, 3);
+            if (active && (lane & 3) == 0) {
+                const uint32_t word = bits | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                if (labels) labels[i0 >> 4] = word;
+                if (COUNTS) {
+                    const uint32_t lo = word & 0x55555555u, hi = (word >> 1) & 0x55555555u;
+                    cm += __popc(lo & ~hi);
+                    cs += __popc(hi & ~lo);
+                    cM += __popc(lo & hi);
+                }
+            }
+        }
+        // advance by the grid stride
+        x += sx;
+        uint32_t cy = 0;
+        if (x >= g.nx) { x -= g.nx; cy = 1; }
+        y += sy + cy;
+        uint32_t cz = 0;
+        if (y >= g.ny) { y -= g.ny; cz = 1; }
+        z += sz + cz;
+    }
+    if (STATS) {
+        uint32_t kmax = vmax >= vmin ? ord_key(vmax) : 0u;
+        uint32_t kmin = vmax >= vmin ? ~ord_key(vmin) : 0u;
+        kmax = __reduce_max_sync(FULL, kmax);
+        kmin = __reduce_max_sync(FULL, kmin);
+        const bool anybad = __any_sync(FULL, bad);
+        if (lane == 0) {
+            if (kmax) atomicMax(&c->max_key, kmax);
+            if (kmin) atomicMax(&c->min_inv, kmin);
+            if (anybad) atomicExch(&c->nonfinite, 1u);
+        }
+    }
+    if (COUNTS) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            cm += __shfl_xor_sync(FULL, cm, o);
+            cs += __shfl_xor_sync(FULL, cs, o);
+            cM += __shfl_xor_sync(FULL, cM, o);
+        }
+        if (lane == 0) {
+            if (cm) atomicAdd(&counts[1], cm);
+            if (cs) atomicAdd(&counts[2], cs);
+            if (cM) atomicAdd(&counts[3], cM);
+        }
+    }
+}
+
 // counts[0] = n - (m + s + M)
 __global__ void k_count_regular(uint32_t n, unsigned long long* counts) {
     counts[0] = (unsigned long long)n - counts[1] - counts[2] - counts[3];
@@ -488,6 +626,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int G, const
     const uint32_t per = (total + 1023) / 1024;
     const uint32_t b = threadIdx.x * per, e = min(total, b + per);
     uint32_t s = 0;
+#pragma unroll 16
     for (uint32_t i = b; i < e; i++) s += hst[i];
     part[threadIdx.x] = s;
     __syncthreads();
@@ -498,6 +637,7 @@ __global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int G, const
         __syncthreads();
     }
     uint32_t run = part[threadIdx.x] - s;
+#pragma unroll 16
     for (uint32_t i = b; i < e; i++) {
         uint32_t v = hst[i];
         hst[i] = run;
@@ -808,8 +948,18 @@ __global__ void k_count_saddles(const uint32_t* labels, Ctrl* c, const int* stat
 
 // ============================================================ host launchers
 
+static bool vec_ok(const float* a, const Geo& g) {
+    return g.nx % 4 == 0 && (reinterpret_cast<uintptr_t>(a) & 15u) == 0;
+}
+
 void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bool topo, int sms,
                      cudaStream_t st) {
+    if (vec_ok(a, g)) {
+        uint32_t blocks = hmin<uint32_t>((g.n / 128 + 7) / 8 + 1, (uint32_t)sms * 8);
+        if (topo) k_range_cd_vec<true, false, true><<<blocks, 256, 0, st>>>(a, g, c, labels, nullptr);
+        else k_range_cd_vec<false, false, true><<<blocks, 256, 0, st>>>(a, g, c, labels, nullptr);
+        return;
+    }
     uint32_t nchunks = (g.n + 511) / 512;
     uint32_t blocks = hmin<uint32_t>((nchunks + 7) / 8, (uint32_t)sms * 8);
     if (blocks == 0) blocks = 1;
@@ -819,6 +969,16 @@ void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bo
 
 void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsigned long long* counts,
                             int sms, cudaStream_t st) {
+    if (vec_ok(a, g)) {
+        uint32_t blocks = hmin<uint32_t>((g.n / 128 + 7) / 8 + 1, (uint32_t)sms * 8);
+        if (counts) {
+            k_range_cd_vec<true, true, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, counts);
+            k_count_regular<<<1, 1, 0, st>>>(g.n, counts);
+        } else {
+            k_range_cd_vec<true, false, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, nullptr);
+        }
+        return;
+    }
     uint32_t nchunks = (g.n + 511) / 512;
     uint32_t blocks = hmin<uint32_t>((nchunks + 7) / 8, (uint32_t)sms * 8);
     if (blocks == 0) blocks = 1;

@@ -2,15 +2,16 @@
 //
 //   k_parse_header   one thread: validate the stream header against the call
 //                    and the buffer size, fill the control block
-//   k_decode_field   BE^, LZ^ + B^, QZ^: unpack sign/magnitude planes with warp
-//                    shuffles, inverse Lorenzo by a warp prefix sum, dequantise;
-//                    a look-back over (payload words, extremum count) gives each
-//                    tile its payload offset and each extremum its position in
-//                    the delta sequence (MD^)
-//   k_decode_ranks   the same inverse codec on the rank stream
-//   k_fixup          cooperative kernel: CP^ + RP^ extrema stencils (evaluate
-//                    on the QZ^ snapshot, then apply), collect lost saddles,
-//                    then RS^ colour rounds (evaluate, grid sync, apply)
+//   k_dec_tile_*     offset pre-pass: per 2048-point tile, payload words and
+//                    extremum counts -> exclusive prefixes (MD^ bookkeeping)
+//   k_decode_ranks   the inverse codec on the rank stream (delta sequence)
+//   k_decode_fused   persistent wavefront over tiles: BE^, LZ^ + B^, QZ^ (planes
+//                    unpacked with warp shuffles, inverse Lorenzo by a warp
+//                    prefix sum), then CP^ + RP^ extrema stencils evaluated on
+//                    the QZ^ snapshot and applied, then the lost saddles
+//                    collected -- each stage trailing the previous one by the
+//                    neighbour reach, so the field stays in L2 in between
+//   k_saddle_rounds  cooperative RS^ colour rounds (evaluate, grid sync, write)
 // Every read of the stream is bounds-checked against the validated header; a
 // violation sets CORRUPT_STREAM and skips the access.
 #include <cooperative_groups.h>
@@ -109,126 +110,6 @@ __device__ __forceinline__ int32_t decode_block(const uint32_t* pay, unsigned lo
     return (int32_t)((uint32_t)first + d);
 }
 
-template <bool TOPO>
-__device__ __forceinline__ void decode_field_body(const uint8_t* __restrict__ in, Ctrl* c, Desc* desc,
-                                                  float* __restrict__ out, uint32_t* cp_idx, int* status) {
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_w[TILE_WARPS], s_cp[TILE_WARPS];
-    __shared__ unsigned long long s_pre_w, s_pre_cp;
-    const Geo g = c->g;
-    const Layout lo = c->lo;
-    const float w_f = c->w_f;
-    const unsigned long long pay_words = c->pay_words, k = c->k_total;
-    const uint8_t* widths = in + lo.s2;
-    const int32_t* firsts = reinterpret_cast<const int32_t*>(in + lo.s4);
-    const uint32_t* pay = reinterpret_cast<const uint32_t*>(in + lo.s5);
-    const uint32_t* labels = reinterpret_cast<const uint32_t*>(in + lo.s6);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
-    const uint32_t lt = lanemask_lt();
-    bool corrupt = false;
-    while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_dec, 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t blk0 = tile * TILE_BLOCKS + warp * BPW;
-        uint32_t my_w = 0;
-        int32_t my_first = 0;
-        if (lane < BPW && blk0 + lane < g.nb) {
-            my_w = widths[blk0 + lane];
-            my_first = firsts[blk0 + lane];
-            if (my_w > 32) {
-                corrupt = true;
-                my_w = 0;
-            }
-        }
-        uint32_t ww = (lane < BPW && my_w) ? 1u + my_w : 0u;
-        ww = __reduce_add_sync(FULL, ww);
-        uint32_t mmask[BPW];
-        uint32_t wcp = 0;
-#pragma unroll
-        for (int j = 0; j < BPW; j++) {
-            mmask[j] = 0;
-            if (TOPO) {
-                const uint32_t b = blk0 + j;
-                if (b < g.nb) {
-                    const uint32_t i = b * 32u + lane;
-                    const int lab = i < g.n ? label_at(labels, i) : 0;
-                    mmask[j] = __ballot_sync(FULL, lab & 1);   // m = 01, M = 11
-                    wcp += __popc(mmask[j]);
-                }
-            }
-        }
-        if (lane == 0) {
-            s_w[warp] = ww;
-            s_cp[warp] = wcp;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t vw = lane < TILE_WARPS ? s_w[lane] : 0, vc = lane < TILE_WARPS ? s_cp[lane] : 0;
-            uint32_t iw = vw, ic = vc;
-#pragma unroll
-            for (int o = 1; o < TILE_WARPS; o <<= 1) {
-                uint32_t t0 = __shfl_up_sync(FULL, iw, o), t1 = __shfl_up_sync(FULL, ic, o);
-                if (lane >= o) { iw += t0; ic += t1; }
-            }
-            uint32_t tw = __shfl_sync(FULL, iw, TILE_WARPS - 1), tc = __shfl_sync(FULL, ic, TILE_WARPS - 1);
-            unsigned long long pw, pc;
-            lookback(desc, tile, tw, tc, pw, pc, status);
-            if (lane < TILE_WARPS) {
-                s_w[lane] = iw - vw;
-                s_cp[lane] = ic - vc;
-            }
-            if (lane == 0) {
-                s_pre_w = pw;
-                s_pre_cp = pc;
-                if (tile == ntiles - 1 && (pw + tw != pay_words || (TOPO && pc + tc != k)))
-                    set_status(status, ST_CORRUPT);
-            }
-        }
-        __syncthreads();
-        unsigned long long woff = s_pre_w + s_w[warp];
-        unsigned long long cpoff = s_pre_cp + s_cp[warp];
-#pragma unroll
-        for (int j = 0; j < BPW; j++) {
-            const uint32_t b = blk0 + j;
-            if (b >= g.nb) break;
-            const uint32_t w = __shfl_sync(FULL, my_w, j);
-            const int32_t first = __shfl_sync(FULL, my_first, j);
-            int32_t q = first;
-            if (w) {
-                if (woff + 1 + w <= pay_words) q = decode_block(pay, woff, w, first, lane);
-                else corrupt = true;
-                woff += 1 + w;
-            }
-            const uint32_t i = b * 32u + lane;
-            if (i < g.n) out[i] = dequantize(q, w_f);
-            if (TOPO) {
-                const uint32_t mm = mmask[j];
-                if ((mm >> lane) & 1u) {
-                    unsigned long long pos = cpoff + __popc(mm & lt);
-                    if (pos < k) cp_idx[pos] = i;
-                    else corrupt = true;
-                }
-                cpoff += __popc(mm);
-            }
-        }
-        __syncthreads();
-    }
-    if (corrupt) set_status(status, ST_CORRUPT);
-}
-
-// The stream's flags decide at run time whether labels are read (the host does
-// not read the header, so one launch serves both kinds of stream).
-__global__ void __launch_bounds__(256) k_decode_field(const uint8_t* __restrict__ in, Ctrl* c, Desc* desc,
-                                                      float* __restrict__ out, uint32_t* cp_idx,
-                                                      int* status) {
-    if (*status) return;
-    if (c->flags & FLAG_NO_TOPO) decode_field_body<false>(in, c, desc, out, cp_idx, status);
-    else decode_field_body<true>(in, c, desc, out, cp_idx, status);
-}
-
 __global__ void __launch_bounds__(256) k_decode_ranks(const uint8_t* __restrict__ in, Ctrl* c, Desc* desc,
                                                       int32_t* __restrict__ delta, int* status) {
     __shared__ uint32_t s_tile;
@@ -318,7 +199,7 @@ __device__ __forceinline__ bool step_ulps(float x, long long kk, float& res) {
     return true;
 }
 
-struct OverrideVal {
+struct OverrideVal {   // the field with point p set to v
     const float* F;
     uint32_t p;
     float v;
@@ -329,7 +210,9 @@ __device__ __forceinline__ int colour_of(const Geo& g, uint32_t x, uint32_t y, u
     return g.ndim == 2 ? (int)((x + 2u * y) % 5u) : (int)((x + 2u * y + 3u * z) % 7u);
 }
 
-// RS^ candidate: returns true and the refined value when accepted.
+// RS^ candidate: returns true and the refined value when accepted.  Runs only
+// inside the cooperative rounds kernel, whose grid syncs order every write of
+// the previous colour before these (L1-cached) reads.
 __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const Geo& g, const Ctrl* c,
                                  uint32_t p, uint32_t x, uint32_t y, uint32_t z, float& vout) {
     const float Fp = F[p];
@@ -388,29 +271,251 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
     return true;
 }
 
-__global__ void __launch_bounds__(256) k_fixup(const uint8_t* __restrict__ in, Ctrl* c, float* out,
-                                               const uint32_t* cp_idx, const int32_t* delta, float* newv,
-                                               uint32_t* sad, float* sadv, uint32_t sad_cap, int* status) {
-    cg::grid_group grid = cg::this_grid();
-    // uniform across the grid: neither word is written by this kernel
-    if (*status || (c->flags & FLAG_NO_TOPO)) return;
+// ---------------------------------------------------------- offset pre-pass
+//
+// Per decode tile (64 blocks): payload words from the widths and the number of
+// extrema (m/M labels) -> exclusive prefixes.  With every tile's offsets known
+// up front the fused decoder needs no look-back.
+
+__global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict__ in, Ctrl* c,
+                                                       uint32_t* tile_w, uint32_t* tile_c, int* status) {
+    if (*status) return;
     const Geo g = c->g;
-    const uint32_t* labels = reinterpret_cast<const uint32_t*>(in + c->lo.s6);
-    const uint64_t k = c->k_total;
-    const float h_f = c->h_f;
-    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const Layout lo = c->lo;
+    const bool topo = !(c->flags & FLAG_NO_TOPO);
+    const uint8_t* widths = in + lo.s2;
+    const uint32_t* labels = reinterpret_cast<const uint32_t*>(in + lo.s6);
+    const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    const uint32_t nwords = (g.n + 15) / 16;
     const int lane = threadIdx.x & 31;
+    bool corrupt = false;
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += (gridDim.x * blockDim.x) >> 5) {
+        uint32_t words = 0, cps = 0;
+        for (int j = 0; j < TILE_BLOCKS / 32; j++) {
+            const uint32_t b = t * TILE_BLOCKS + j * 32 + lane;
+            if (b < g.nb) {
+                uint32_t w = __ldg(widths + b);
+                if (w > 32) { corrupt = true; w = 0; }
+                words += w ? 1u + w : 0u;
+            }
+        }
+        if (topo) {
+            for (int j = 0; j < TILE_BLOCKS * 2 / 32; j++) {
+                const uint32_t wi = t * TILE_BLOCKS * 2 + j * 32 + lane;
+                if (wi < nwords) cps += __popc(__ldg(labels + wi) & 0x55555555u);   // m = 01, M = 11
+            }
+        }
+        words = __reduce_add_sync(FULL, words);
+        cps = __reduce_add_sync(FULL, cps);
+        if (lane == 0) {
+            tile_w[t] = words;
+            tile_c[t] = cps;
+        }
+    }
+    if (corrupt) set_status(status, ST_CORRUPT);
+}
+
+// exclusive scans of the tile sums (one CTA); totals must match the header
+__global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t* tile_w, const uint32_t* tile_c,
+                                                        unsigned long long* pay_pre, uint32_t* cp_pre, int* status) {
+    __shared__ unsigned long long sw[1024];
+    __shared__ unsigned long long sc[1024];
+    if (*status) return;
+    const uint32_t ntiles = (c->g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    const uint32_t per = (ntiles + 1023) / 1024;
+    const uint32_t b = threadIdx.x * per, e = hmin<uint32_t>(ntiles, b + per);
+    unsigned long long aw = 0, ac = 0;
+    for (uint32_t i = b; i < e; i++) {
+        aw += tile_w[i];
+        ac += tile_c[i];
+    }
+    sw[threadIdx.x] = aw;
+    sc[threadIdx.x] = ac;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned long long tw = threadIdx.x >= o ? sw[threadIdx.x - o] : 0;
+        unsigned long long tc = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
+        __syncthreads();
+        sw[threadIdx.x] += tw;
+        sc[threadIdx.x] += tc;
+        __syncthreads();
+    }
+    unsigned long long rw = sw[threadIdx.x] - aw, rc = sc[threadIdx.x] - ac;
+    for (uint32_t i = b; i < e; i++) {
+        pay_pre[i] = rw;
+        cp_pre[i] = (uint32_t)rc;
+        rw += tile_w[i];
+        rc += tile_c[i];
+    }
+    if (threadIdx.x == 1023) {
+        pay_pre[ntiles] = sw[1023];
+        cp_pre[ntiles] = (uint32_t)sc[1023];
+        const bool topo = !(c->flags & FLAG_NO_TOPO);
+        if (sw[1023] != c->pay_words || (topo && sc[1023] != c->k_total)) set_status(status, ST_CORRUPT);
+    }
+}
+
+// ------------------------------------------------------- fused wavefront decode
+//
+// One persistent kernel over linear tiles of 2048 points.  The CTA that takes
+// tile t runs
+//   S1(t)       decode: BE^, LZ^ + B^, QZ^ -> out = D0; positions of extrema
+//   S2(t - H)   CP^ + RP^ evaluation of that tile's extrema on the D0 snapshot
+//   S3(t - 2H)  apply the accepted stencil values
+//   S4(t - 3H)  collect the tile's saddles that are still lost
+// where H tiles cover the farthest face neighbour (one plane in 3D, one row in
+// 2D).  Stage k of tile s starts only when stage k-1 is complete for every tile
+// up to s + H (a per-stage frontier over per-tile flags), so S2 always reads
+// unmodified D0 (Jacobi, as in the oracle) and S4 reads finished extrema, while
+// the working window of about 3H tiles stays in L2: the field reaches HBM once.
+// Waits only ever point at lower tile indices held by running CTAs (tiles are
+// handed out in order), and every wait is bounded.
+
+struct CgVal {   // L2-coherent reads of a field other CTAs write during the kernel
+    const float* F;
+    __device__ __forceinline__ float operator()(uint32_t j) const { return __ldcg(F + j); }
+};
+
+// Warp 0 waits until stage `k` is complete for every tile below `need`.
+__device__ __forceinline__ void wait_front(Ctrl* c, const uint32_t* flags, int k, uint32_t need,
+                                           uint32_t ntiles, int* status) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        volatile unsigned int* fr = &c->front[k];
+        uint32_t spins = 0;
+        while (true) {
+            uint32_t f = *fr;
+            if (f >= need) break;
+            const uint32_t j = f + lane;
+            const uint32_t v = j < ntiles ? *(volatile const uint32_t*)(flags + j) : 0u;
+            const uint32_t done = __ballot_sync(FULL, (v >> k) & 1u);
+            const uint32_t run = done == FULL ? 32u : (uint32_t)(__ffs(~done) - 1);
+            if (run) {
+                if (lane == 0) atomicMax((unsigned int*)&c->front[k], f + run);
+                continue;
+            }
+            if (++spins > SPIN_LIMIT) {
+                if (lane == 0) set_status(status, ST_TIMEOUT);
+                break;
+            }
+            __nanosleep(spins < 32 ? 64 : 256);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void mark_done(uint32_t* flags, int k, uint32_t tile) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicOr(flags + tile, 1u << k);
+    }
+}
+
+struct FusedArgs {
+    const uint8_t* in;
+    Ctrl* c;
+    float* out;
+    const unsigned long long* pay_pre;
+    const uint32_t* cp_pre;
+    const int32_t* delta;
+    uint32_t* cp_idx;
+    float* newv;
+    uint32_t* flags;
+    uint32_t* sad;
+    uint32_t sad_cap;
+    int* status;
+};
+
+template <bool TOPO>
+__device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo, uint32_t t, uint32_t* s_w,
+                             uint32_t* s_cp, bool& corrupt) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint8_t* widths = A.in + lo.s2;
+    const int32_t* firsts = reinterpret_cast<const int32_t*>(A.in + lo.s4);
+    const uint32_t* pay = reinterpret_cast<const uint32_t*>(A.in + lo.s5);
+    const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
+    const unsigned long long pay_words = A.c->pay_words, k = A.c->k_total;
+    const float w_f = A.c->w_f;
+    const uint32_t blk0 = t * TILE_BLOCKS + warp * BPW;
+    uint32_t my_w = 0;
+    int32_t my_first = 0;
+    if (lane < BPW && blk0 + lane < g.nb) {
+        my_w = __ldg(widths + blk0 + lane);
+        my_first = __ldg(firsts + blk0 + lane);
+        if (my_w > 32) my_w = 0;
+    }
+    const uint32_t ww = __reduce_add_sync(FULL, (lane < BPW && my_w) ? 1u + my_w : 0u);
+    uint32_t mmask[BPW];
+    uint32_t wcp = 0;
+#pragma unroll
+    for (int j = 0; j < BPW; j++) {
+        mmask[j] = 0;
+        if (TOPO) {
+            const uint32_t b = blk0 + j;
+            if (b < g.nb) {
+                const uint32_t i = b * 32u + lane;
+                const int lab = i < g.n ? label_at(labels, i) : 0;
+                mmask[j] = __ballot_sync(FULL, lab & 1);
+                wcp += __popc(mmask[j]);
+            }
+        }
+    }
+    if (lane == 0) {
+        s_w[warp] = ww;
+        s_cp[warp] = wcp;
+    }
+    __syncthreads();
+    unsigned long long woff = A.pay_pre[t], cpoff = A.cp_pre[t];
+    for (int w = 0; w < warp; w++) {
+        woff += s_w[w];
+        cpoff += s_cp[w];
+    }
     const uint32_t lt = lanemask_lt();
-    GlobalVal val{out};
-    // ---- CP^ + RP^: evaluate every extremum on the QZ^ snapshot (Jacobi)
-    unsigned long long restored = 0, skipped = 0;
-    for (uint64_t pos = tid; pos < k; pos += nth) {
-        const uint32_t p = cp_idx[pos];
-        const int lab = label_at(labels, p);
+#pragma unroll
+    for (int j = 0; j < BPW; j++) {
+        const uint32_t b = blk0 + j;
+        if (b >= g.nb) break;
+        const uint32_t w = __shfl_sync(FULL, my_w, j);
+        const int32_t first = __shfl_sync(FULL, my_first, j);
+        int32_t q = first;
+        if (w) {
+            if (woff + 1 + w <= pay_words) q = decode_block(pay, woff, w, first, lane);
+            else corrupt = true;
+            woff += 1 + w;
+        }
+        const uint32_t i = b * 32u + lane;
+        if (i < g.n) A.out[i] = dequantize(q, w_f);
+        if (TOPO) {
+            const uint32_t mm = mmask[j];
+            if ((mm >> lane) & 1u) {
+                const unsigned long long pos = cpoff + __popc(mm & lt);
+                if (pos < k) A.cp_idx[pos] = i;
+                else corrupt = true;
+            }
+            cpoff += __popc(mm);
+        }
+    }
+}
+
+// CP^ + RP^ on one tile's extrema, reading the D0 snapshot (Jacobi).
+__device__ void stage_extrema(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t s,
+                              unsigned long long& restored, unsigned long long& skipped) {
+    const uint32_t P0 = A.cp_pre[s], P1 = A.cp_pre[s + 1];
+    const float h_f = A.c->h_f;
+    CgVal val{A.out};
+    for (uint32_t pos = P0 + threadIdx.x; pos < P1; pos += blockDim.x) {
+        const uint32_t p = __ldcg(A.cp_idx + pos);
         float nv = __int_as_float(0x7FC00000);
+        if (p >= g.n) {   // only a damaged stream gets here (its checks already failed)
+            A.newv[pos] = nv;
+            continue;
+        }
+        const int lab = label_at(labels, p);
         uint32_t x, y, z;
         coords(g, p, x, y, z);
-        const float v0 = out[p];
+        const float v0 = val(p);
         if (classify(val, g, p, x, y, z, v0) != lab) {
             const uint32_t st[3] = {1u, g.nx, g.nxy};
             const uint32_t cc[3] = {x, y, z}, dd[3] = {g.nx, g.ny, g.nz};
@@ -418,18 +523,18 @@ __global__ void __launch_bounds__(256) k_fixup(const uint8_t* __restrict__ in, C
             bool have = false;
             for (int ax = 0; ax < g.ndim; ax++) {
                 if (cc[ax] > 0) {
-                    const float u = out[p - st[ax]];
+                    const float u = val(p - st[ax]);
                     if (!have || (lab == LAB_MAX ? u > ext : u < ext)) ext = u;
                     have = true;
                 }
                 if (cc[ax] + 1 < dd[ax]) {
-                    const float u = out[p + st[ax]];
+                    const float u = val(p + st[ax]);
                     if (!have || (lab == LAB_MAX ? u > ext : u < ext)) ext = u;
                     have = true;
                 }
             }
             float v;
-            const long long dl = delta[pos];
+            const long long dl = __ldg(A.delta + pos);
             if (have && step_ulps(ext, lab == LAB_MAX ? dl : -dl, v) && fabsf(__fsub_rn(v, v0)) <= h_f) {
                 nv = v;
                 restored++;
@@ -437,52 +542,132 @@ __global__ void __launch_bounds__(256) k_fixup(const uint8_t* __restrict__ in, C
                 skipped++;
             }
         }
-        newv[pos] = nv;
+        A.newv[pos] = nv;
     }
-    grid.sync();
-    for (uint64_t pos = tid; pos < k; pos += nth) {
-        const float v = newv[pos];
-        if (!isnan(v)) out[cp_idx[pos]] = v;
+}
+
+__device__ void stage_apply(const FusedArgs& A, const Geo& g, uint32_t s) {
+    const uint32_t P0 = A.cp_pre[s], P1 = A.cp_pre[s + 1];
+    for (uint32_t pos = P0 + threadIdx.x; pos < P1; pos += blockDim.x) {
+        const float v = __ldcg(A.newv + pos);
+        const uint32_t p = __ldcg(A.cp_idx + pos);
+        if (!isnan(v) && p < g.n) A.out[p] = v;
     }
-    grid.sync();
-    // ---- collect saddles that are still lost (a fixed saddle never breaks again)
+}
+
+// Saddles of tile s that the extrema stage left lost go to the candidate list.
+__device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t s) {
     const uint32_t nwords = (g.n + 15) / 16;
-    for (uint32_t wi0 = tid - lane; wi0 < nwords; wi0 += nth) {
-        const uint32_t wi = wi0 + lane;
-        const uint32_t word = wi < nwords ? labels[wi] : 0u;
-        uint32_t smask = ((word >> 1) & ~word) & 0x55555555u;   // code 10
-        uint32_t lost = 0;
-        while (smask) {
-            const int bit = __ffs(smask) - 1;
-            smask &= smask - 1;
-            const uint32_t p = wi * 16u + (uint32_t)(bit >> 1);
-            uint32_t x, y, z;
-            coords(g, p, x, y, z);
-            if (classify(val, g, p, x, y, z, out[p]) != LAB_SAD) lost |= 1u << (bit >> 1);
-        }
-        const uint32_t cnt = __popc(lost);
-        uint32_t incl = cnt;
+    if (threadIdx.x >= TILE_BLOCKS * 2) return;   // 128 label words per tile: warps 0..3
+    const int lane = threadIdx.x & 31;
+    const uint32_t wi = s * TILE_BLOCKS * 2 + threadIdx.x;
+    const uint32_t word = wi < nwords ? __ldg(labels + wi) : 0u;
+    uint32_t smask = ((word >> 1) & ~word) & 0x55555555u;   // code 10
+    uint32_t lost = 0;
+    CgVal val{A.out};
+    while (smask) {
+        const int bit = __ffs(smask) - 1;
+        smask &= smask - 1;
+        const uint32_t p = wi * 16u + (uint32_t)(bit >> 1);
+        if (p >= g.n) break;   // padding bits of a damaged stream
+        uint32_t x, y, z;
+        coords(g, p, x, y, z);
+        if (classify(val, g, p, x, y, z, val(p)) != LAB_SAD) lost |= 1u << (bit >> 1);
+    }
+    const uint32_t cnt = __popc(lost);
+    uint32_t incl = cnt;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(FULL, incl, o);
-            if (lane >= o) incl += t;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t tt = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += tt;
+    }
+    const uint32_t tot = __shfl_sync(FULL, incl, 31);
+    uint32_t base = 0;
+    if (lane == 31 && tot) base = atomicAdd(&A.c->sad_cnt[0], tot);
+    base = __shfl_sync(FULL, base, 31);
+    uint32_t slot = base + incl - cnt;
+    while (lost) {
+        const int b = __ffs(lost) - 1;
+        lost &= lost - 1;
+        if (slot < A.sad_cap) A.sad[slot] = wi * 16u + (uint32_t)b;
+        slot++;
+    }
+}
+
+template <bool TOPO>
+__device__ void fused_body(const FusedArgs& A) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint32_t s_w[TILE_WARPS], s_cp[TILE_WARPS];
+    Ctrl* c = A.c;
+    const Geo g = c->g;
+    const Layout lo = c->lo;
+    const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
+    const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    const uint32_t reach = g.ndim == 3 ? g.nxy : g.nx;
+    const uint32_t H = TOPO ? (uint32_t)hmin<uint64_t>(ntiles, reach / (TILE_BLOCKS * L) + 2) : 0u;
+    const uint32_t total = ntiles + 3 * H;
+    bool corrupt = false;
+    unsigned long long restored = 0, skipped = 0;
+    while (true) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_fused, 1u);
+        __syncthreads();
+        const uint32_t t = s_tile;
+        __syncthreads();
+        if (t >= total) break;
+        if (t < ntiles) {
+            stage_decode<TOPO>(A, g, lo, t, s_w, s_cp, corrupt);
+            mark_done(A.flags, 1, t);
         }
-        const uint32_t tot = __shfl_sync(FULL, incl, 31);
-        uint32_t base = 0;
-        if (lane == 31 && tot) base = atomicAdd(&c->sad_cnt[0], tot);
-        base = __shfl_sync(FULL, base, 31);
-        uint32_t slot = base + incl - cnt;
-        while (lost) {
-            const int b = __ffs(lost) - 1;
-            lost &= lost - 1;
-            if (slot < sad_cap) sad[slot] = wi * 16u + (uint32_t)b;
-            slot++;
+        if (TOPO) {
+            const long long s2 = (long long)t - H, s3 = (long long)t - 2 * H, s4 = (long long)t - 3 * H;
+            if (s2 >= 0 && s2 < ntiles) {
+                wait_front(c, A.flags, 1, (uint32_t)hmin<long long>(s2 + H, ntiles - 1) + 1, ntiles, A.status);
+                stage_extrema(A, g, labels, (uint32_t)s2, restored, skipped);
+                mark_done(A.flags, 2, (uint32_t)s2);
+            }
+            if (s3 >= 0 && s3 < ntiles) {
+                wait_front(c, A.flags, 2, (uint32_t)hmin<long long>(s3 + H, ntiles - 1) + 1, ntiles, A.status);
+                stage_apply(A, g, (uint32_t)s3);
+                mark_done(A.flags, 3, (uint32_t)s3);
+            }
+            if (s4 >= 0 && s4 < ntiles) {
+                wait_front(c, A.flags, 3, (uint32_t)hmin<long long>(s4 + H, ntiles - 1) + 1, ntiles, A.status);
+                stage_saddles(A, g, labels, (uint32_t)s4);
+                __syncthreads();
+            }
         }
     }
-    (void)lt;
-    grid.sync();
-    // ---- RS^: colour rounds, two phases each
-    const uint32_t ns = min(c->sad_cnt[0], sad_cap);
+    if (corrupt) set_status(A.status, ST_CORRUPT);
+    if (TOPO) {
+        for (int o = 16; o > 0; o >>= 1) {
+            restored += __shfl_xor_sync(FULL, restored, o);
+            skipped += __shfl_xor_sync(FULL, skipped, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (restored) atomicAdd(&c->stat_restored, restored);
+            if (skipped) atomicAdd(&c->stat_skipped, skipped);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_decode_fused(FusedArgs A) {
+    if (*A.status) return;
+    if (A.c->flags & FLAG_NO_TOPO) fused_body<false>(A);
+    else fused_body<true>(A);
+}
+
+// RS^ colour rounds over the lost-saddle list (cooperative: the grid syncs
+// between the evaluation and the write of every colour).
+__global__ void __launch_bounds__(256) k_saddle_rounds(const uint8_t* __restrict__ in, Ctrl* c, float* out,
+                                                       const uint32_t* sad, float* sadv, uint32_t sad_cap,
+                                                       int* status) {
+    cg::grid_group grid = cg::this_grid();
+    // uniform across the grid: neither word is written by this kernel
+    if (*status || (c->flags & FLAG_NO_TOPO)) return;
+    const Geo g = c->g;
+    const uint32_t* labels = reinterpret_cast<const uint32_t*>(in + c->lo.s6);
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
+    const uint32_t ns = hmin<uint32_t>(c->sad_cnt[0], sad_cap);
     const int ncol = g.ndim == 2 ? 5 : 7;
     unsigned long long fixed = 0;
     for (int sw = 0; sw < c->rs_sweeps; sw++) {
@@ -510,30 +695,14 @@ __global__ void __launch_bounds__(256) k_fixup(const uint8_t* __restrict__ in, C
             grid.sync();
         }
     }
-    for (int o = 16; o > 0; o >>= 1) {
-        restored += __shfl_xor_sync(FULL, restored, o);
-        skipped += __shfl_xor_sync(FULL, skipped, o);
-        fixed += __shfl_xor_sync(FULL, fixed, o);
-    }
-    if (lane == 0) {
-        if (restored) atomicAdd(&c->stat_restored, restored);
-        if (skipped) atomicAdd(&c->stat_skipped, skipped);
-        if (fixed) atomicAdd(&c->stat_saddle, fixed);
-    }
+    for (int o = 16; o > 0; o >>= 1) fixed += __shfl_xor_sync(FULL, fixed, o);
+    if ((threadIdx.x & 31) == 0 && fixed) atomicAdd(&c->stat_saddle, fixed);
 }
-
 // ------------------------------------------------------------ host launchers
 
 void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c, int* status,
                          cudaStream_t st) {
     k_parse_header<<<1, 32, 0, st>>>(in, in_size, n_out, c, status);
-}
-
-void launch_decode_field(const uint8_t* in, Ctrl* c, Desc* desc, float* out, uint32_t* cp_idx,
-                         uint32_t ntiles, int sms, int* status, cudaStream_t st) {
-    uint32_t grid = hmin<uint32_t>(ntiles, (uint32_t)sms * 6);
-    if (grid == 0) grid = 1;
-    k_decode_field<<<grid, 256, 0, st>>>(in, c, desc, out, cp_idx, status);
 }
 
 void launch_decode_ranks(const uint8_t* in, Ctrl* c, Desc* desc, int32_t* delta, uint32_t max_tiles,
@@ -543,23 +712,43 @@ void launch_decode_ranks(const uint8_t* in, Ctrl* c, Desc* desc, int32_t* delta,
     k_decode_ranks<<<grid, 256, 0, st>>>(in, c, desc, delta, status);
 }
 
-int fixup_grid(int sms) {
+void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* tile_c,
+                        unsigned long long* pay_pre, uint32_t* cp_pre, uint32_t ntiles, int sms, int* status,
+                        cudaStream_t st) {
+    uint32_t blocks = hmin<uint32_t>((ntiles + 7) / 8, (uint32_t)sms * 8);
+    if (blocks == 0) blocks = 1;
+    k_dec_tile_sums<<<blocks, 256, 0, st>>>(in, c, tile_w, tile_c, status);
+    k_dec_tile_scan<<<1, 1024, 0, st>>>(c, tile_w, tile_c, pay_pre, cp_pre, status);
+}
+
+void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
+                         const uint32_t* cp_pre, const int32_t* delta, uint32_t* cp_idx, float* newv,
+                         uint32_t* flags, uint32_t* sad, uint32_t sad_cap, int sms, int* status,
+                         cudaStream_t st) {
     static int per_sm = -1;
     if (per_sm < 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_fixup, 256, 0) != cudaSuccess || b < 1)
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_decode_fused, 256, 0) != cudaSuccess || b < 1)
+            b = 1;
+        per_sm = b;
+    }
+    FusedArgs A{in, c, out, pay_pre, cp_pre, delta, cp_idx, newv, flags, sad, sad_cap, status};
+    // persistent: never more CTAs than can be resident at once (waits point at
+    // tiles held by running CTAs)
+    k_decode_fused<<<per_sm * sms, 256, 0, st>>>(A);
+}
+
+cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, float* sadv,
+                                 uint32_t sad_cap, int sms, int* status, cudaStream_t st) {
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_saddle_rounds, 256, 0) != cudaSuccess || b < 1)
             b = 1;
         per_sm = b < 4 ? b : 4;
     }
-    return per_sm * sms;
+    void* args[] = {(void*)&in, (void*)&c, (void*)&out, (void*)&sad, (void*)&sadv, (void*)&sad_cap,
+                    (void*)&status};
+    return cudaLaunchCooperativeKernel((const void*)k_saddle_rounds, dim3(per_sm * sms), dim3(256), args, 0, st);
 }
-
-cudaError_t launch_fixup(const uint8_t* in, Ctrl* c, float* out, const uint32_t* cp_idx,
-                         const int32_t* delta, float* newv, uint32_t* sad, float* sadv, uint32_t sad_cap,
-                         int sms, int* status, cudaStream_t st) {
-    void* args[] = {(void*)&in, (void*)&c, (void*)&out, (void*)&cp_idx, (void*)&delta,
-                    (void*)&newv, (void*)&sad, (void*)&sadv, (void*)&sad_cap, (void*)&status};
-    return cudaLaunchCooperativeKernel((const void*)k_fixup, dim3(fixup_grid(sms)), dim3(256), args, 0, st);
-}
-
 }  // namespace tsz

@@ -15,7 +15,7 @@ struct CompressWs {
     int G;
 };
 struct DecompressWs {
-    uint64_t ctrl, desc, rdesc, cp_idx, delta, newv, sad, sadv, end;
+    uint64_t ctrl, rdesc, flags, tile_w, tile_c, pay_pre, cp_pre, cp_idx, delta, newv, sad, sadv, end;
     uint32_t ntiles, rank_tiles, sad_cap;
 };
 CompressWs compress_ws(uint64_t n);
@@ -42,13 +42,17 @@ void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, f
 // ---- decompression launchers (tsz_decompress.cu)
 void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c, int* status,
                          cudaStream_t st);
-void launch_decode_field(const uint8_t* in, Ctrl* c, Desc* desc, float* out, uint32_t* cp_idx,
-                         uint32_t ntiles, int sms, int* status, cudaStream_t st);
+void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* tile_c,
+                        unsigned long long* pay_pre, uint32_t* cp_pre, uint32_t ntiles, int sms, int* status,
+                        cudaStream_t st);
 void launch_decode_ranks(const uint8_t* in, Ctrl* c, Desc* desc, int32_t* delta, uint32_t max_tiles,
                          int sms, int* status, cudaStream_t st);
-cudaError_t launch_fixup(const uint8_t* in, Ctrl* c, float* out, const uint32_t* cp_idx,
-                         const int32_t* delta, float* newv, uint32_t* sad, float* sadv, uint32_t sad_cap,
-                         int sms, int* status, cudaStream_t st);
+void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
+                         const uint32_t* cp_pre, const int32_t* delta, uint32_t* cp_idx, float* newv,
+                         uint32_t* flags, uint32_t* sad, uint32_t sad_cap, int sms, int* status,
+                         cudaStream_t st);
+cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, float* sadv,
+                                 uint32_t sad_cap, int sms, int* status, cudaStream_t st);
 
 // ---- analysis
 void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsigned long long* out12,

@@ -75,7 +75,10 @@ def test_parity_config1_abs_bound():
 
 
 @pytest.mark.parametrize("shape", [(1, 1), (1, 37), (37, 1), (2, 2), (3, 3), (1, 1, 40), (5, 1, 7),
-                                   (3, 3, 3), (1, 33), (4, 8, 1), (2, 1025)])
+                                   (3, 3, 3), (1, 33), (4, 8, 1), (2, 1025),
+                                   # nx % 4 == 0: the vectorised CD path and its boundary rows
+                                   (1, 4), (2, 8), (3, 4, 4), (5, 3, 12), (9, 16), (4, 1, 8), (2, 2, 4),
+                                   (1, 1, 128), (3, 260)])
 def test_parity_degenerate_shapes(shape):
     rng = np.random.default_rng(sum(shape))
     a = rng.integers(-4, 5, size=shape).astype(np.float32) * np.float32(0.25)
@@ -119,7 +122,8 @@ def test_deterministic_across_calls():
     assert outs[0] == outs[1] == outs[2]
 
 
-@pytest.mark.parametrize("shape", [(256, 256), (90, 333), (12, 40, 41), (1, 77)])
+@pytest.mark.parametrize("shape", [(256, 256), (90, 333), (12, 40, 41), (1, 77), (33, 44), (6, 7, 12),
+                                   (1, 16), (3, 1, 20), (70, 5, 36)])
 def test_critical_points_and_topo_errors(shape):
     rng = np.random.default_rng(7)
     a = rng.integers(0, 5, size=shape).astype(np.float32)
