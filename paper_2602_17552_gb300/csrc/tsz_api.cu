@@ -271,10 +271,12 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
                         reinterpret_cast<uint32_t*>(ws + w.cp_pre), reinterpret_cast<int32_t*>(ws + w.delta),
                         reinterpret_cast<uint32_t*>(ws + w.cp_idx), reinterpret_cast<float*>(ws + w.newv),
                         reinterpret_cast<uint32_t*>(ws + w.flags), reinterpret_cast<uint32_t*>(ws + w.sad),
-                        w.sad_cap, sms, status, st);
+                        w.sad_cap, w.ntiles, 64u, sms, status, st);
     stage(6, st);
     stage(7, st);
+    // the stencil values are consumed by now: their buffer holds the colour buckets
     cudaError_t e = launch_saddle_rounds(src, c, out, reinterpret_cast<uint32_t*>(ws + w.sad),
+                                         reinterpret_cast<uint32_t*>(ws + w.newv),
                                          reinterpret_cast<float*>(ws + w.sadv), w.sad_cap, sms, status, st);
     if (e != cudaSuccess) return TOPOSZP_ERR_CUDA;
     stage(8, st);

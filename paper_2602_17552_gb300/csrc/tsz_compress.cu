@@ -304,177 +304,174 @@ struct EncOut {
     uint32_t* pay;
 };
 
-// Field encoder.  TOPO also reads the labels, counts the extrema of each tile
-// (carried through the same look-back as the payload size, giving each
-// extremum its position in the delta sequence) and appends (key, position)
-// pairs to the maxima / minima lists.
+// Field encoder, one 2048-point tile per CTA (tiles handed out in order by an
+// atomic counter, so the look-back only waits on CTAs that already run).
+// Phase 1 quantises, forms the Lorenzo residuals and widths, and packs every
+// non-constant block's sign and magnitude planes into shared memory; only then
+// does warp 0 run the look-back, after which the tile's payload is one
+// contiguous, coalesced copy.  TOPO also reads the labels, counts the tile's
+// extrema (carried through the same look-back, giving each extremum its
+// position in the delta sequence) and appends (key, position) pairs to the
+// maxima / minima lists.
+constexpr int WARP_PAY = BPW * 33;   // worst-case payload words of one warp's blocks
+
 template <bool TOPO>
 __global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ a,
                                                       const uint32_t* __restrict__ labels, Ctrl* c,
                                                       Desc* desc, EncOut o, uint2* listM, uint2* listm,
                                                       int* status) {
+    __shared__ uint32_t s_pay[TILE_WARPS * WARP_PAY];
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_w[TILE_WARPS], s_cp[TILE_WARPS], s_M[TILE_WARPS], s_m[TILE_WARPS];
     __shared__ unsigned long long s_pre_w, s_pre_cp;
-    __shared__ uint32_t s_baseM, s_basem;
     __shared__ uint32_t s_cbits[2];
+    __shared__ unsigned long long s_sum;
     if (*status) return;
     const Geo g = c->g;
     const float r = c->r_f;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
     const uint32_t ncw = (g.nb + 31) / 32;
-    unsigned long long sum_abs = 0;
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(&c->tile_enc, 1u);
+        s_sum = 0;
+    }
     if (threadIdx.x < 2) s_cbits[threadIdx.x] = 0;
-    while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_enc, 1u);
-        __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t blk0 = tile * TILE_BLOCKS + warp * BPW;
-        int32_t dreg[BPW];
-        float areg[BPW];
-        uint32_t labbits = 0;   // 2 bits per block j for this lane
-        uint32_t my_w = 0;
-        int32_t my_first = 0;
-        uint32_t wwords = 0, wcp = 0, wM = 0, wm = 0;
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    if (tile >= ntiles) return;
+    const uint32_t blk0 = tile * TILE_BLOCKS + warp * BPW;
+    uint32_t* wpay = s_pay + warp * WARP_PAY;
+    float areg[BPW];
+    uint32_t labbits = 0;   // 2 bits per block j for this lane
+    uint32_t my_w = 0;
+    int32_t my_first = 0;
+    uint32_t wwords = 0, wM = 0, wm = 0, sum_abs = 0;
+    // issue all loads of the warp's blocks first
 #pragma unroll
-        for (int j = 0; j < BPW; j++) {
-            const uint32_t b = blk0 + j;
-            dreg[j] = 0;
-            areg[j] = 0.0f;
-            if (b < g.nb) {
-                const uint32_t i = b * 32u + lane;
-                const uint32_t nvalid = min(32u, g.n - b * 32u);
-                float v = (lane < nvalid) ? __ldg(a + i) : 0.0f;
-                int32_t q = quantize(v, r);
-                int32_t qlast = __shfl_sync(FULL, q, nvalid - 1);
-                if (lane >= nvalid) q = qlast;
-                int32_t prev = __shfl_up_sync(FULL, q, 1);
-                int32_t d = lane ? q - prev : 0;
-                uint32_t m = (uint32_t)(d < 0 ? -d : d);
-                uint32_t mx = __reduce_max_sync(FULL, m);
-                uint32_t w = 32u - __clz(mx);
-                int32_t first = __shfl_sync(FULL, q, 0);
-                uint32_t sm = __reduce_add_sync(FULL, m);
-                if (lane == 0) sum_abs += sm;
-                if (lane == j) {
-                    my_w = w;
-                    my_first = first;
-                }
-                dreg[j] = d;
-                areg[j] = v;
-                wwords += w ? 1u + w : 0u;
-                if (TOPO) {
-                    int lab = (lane < nvalid) ? label_at(labels, i) : 0;
-                    labbits |= (uint32_t)lab << (2 * j);
-                    uint32_t bM = __ballot_sync(FULL, lab == LAB_MAX);
-                    uint32_t bm = __ballot_sync(FULL, lab == LAB_MIN);
-                    wM += __popc(bM);
-                    wm += __popc(bm);
-                }
-            }
+    for (int j = 0; j < BPW; j++) {
+        const uint32_t i = (blk0 + j) * 32u + lane;
+        areg[j] = (blk0 + j < g.nb && i < g.n) ? __ldg(a + i) : 0.0f;
+        if (TOPO) labbits |= (uint32_t)((blk0 + j < g.nb && i < g.n) ? label_at(labels, i) : 0) << (2 * j);
+    }
+#pragma unroll
+    for (int j = 0; j < BPW; j++) {
+        const uint32_t b = blk0 + j;
+        if (b >= g.nb) break;
+        const uint32_t nvalid = min(32u, g.n - b * 32u);
+        int32_t q = quantize(areg[j], r);
+        const int32_t qlast = __shfl_sync(FULL, q, nvalid - 1);
+        if (lane >= nvalid) q = qlast;
+        const int32_t prev = __shfl_up_sync(FULL, q, 1);
+        const int32_t d = lane ? q - prev : 0;
+        const uint32_t m = (uint32_t)(d < 0 ? -d : d);
+        const uint32_t w = 32u - __clz(__reduce_max_sync(FULL, m));
+        const int32_t first = __shfl_sync(FULL, q, 0);
+        sum_abs += __reduce_add_sync(FULL, m);
+        if (lane == j) {
+            my_w = w;
+            my_first = first;
         }
-        wcp = wM + wm;
+        if (w) {
+            uint32_t word = __ballot_sync(FULL, d < 0);
+            for (uint32_t p = 0; p < w; p++) {
+                const uint32_t bp = __ballot_sync(FULL, (m >> p) & 1u);
+                if (lane == p + 1) word = bp;
+            }
+            if (lane <= w) wpay[wwords + lane] = word;
+            wwords += 1 + w;
+        }
+        if (TOPO) {
+            const int lab = (labbits >> (2 * j)) & 3;
+            wM += __popc(__ballot_sync(FULL, lab == LAB_MAX));
+            wm += __popc(__ballot_sync(FULL, lab == LAB_MIN));
+        }
+    }
+    if (lane == 0) {
+        s_w[warp] = wwords;
+        s_cp[warp] = wM + wm;
+        s_M[warp] = wM;
+        s_m[warp] = wm;
+        if (sum_abs) atomicAdd(&s_sum, (unsigned long long)sum_abs);
+    }
+    {   // constant-block bits of this warp's 8 blocks
+        const uint32_t cb = __ballot_sync(FULL, lane < BPW && blk0 + lane < g.nb && my_w == 0) & 0xFFu;
+        if (lane == 0 && cb) atomicOr(&s_cbits[warp >> 2], cb << ((warp & 3) * 8));
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t vw = lane < TILE_WARPS ? s_w[lane] : 0, vc = lane < TILE_WARPS ? s_cp[lane] : 0;
+        const uint32_t vM = lane < TILE_WARPS ? s_M[lane] : 0, vm = lane < TILE_WARPS ? s_m[lane] : 0;
+        uint32_t iw = vw, ic = vc, iM = vM, im = vm;
+#pragma unroll
+        for (int of = 1; of < TILE_WARPS; of <<= 1) {
+            const uint32_t t0 = __shfl_up_sync(FULL, iw, of), t1 = __shfl_up_sync(FULL, ic, of);
+            const uint32_t t2 = __shfl_up_sync(FULL, iM, of), t3 = __shfl_up_sync(FULL, im, of);
+            if (lane >= of) { iw += t0; ic += t1; iM += t2; im += t3; }
+        }
+        const uint32_t tw = __shfl_sync(FULL, iw, TILE_WARPS - 1), tc = __shfl_sync(FULL, ic, TILE_WARPS - 1);
+        const uint32_t tM = __shfl_sync(FULL, iM, TILE_WARPS - 1), tm = __shfl_sync(FULL, im, TILE_WARPS - 1);
+        uint32_t bM = 0, bm = 0;
+        if (TOPO && lane == 0) {
+            if (tM) bM = atomicAdd(&c->cnt_max, tM);
+            if (tm) bm = atomicAdd(&c->cnt_min, tm);
+        }
+        unsigned long long pw, pc;
+        lookback(desc, tile, tw, tc, pw, pc, status);
+        bM = __shfl_sync(FULL, bM, 0);
+        bm = __shfl_sync(FULL, bm, 0);
+        if (lane < TILE_WARPS) {   // exclusive offsets per warp
+            s_w[lane] = iw - vw;
+            s_cp[lane] = ic - vc;
+            s_M[lane] = bM + iM - vM;
+            s_m[lane] = bm + im - vm;
+        }
         if (lane == 0) {
-            s_w[warp] = wwords;
-            s_cp[warp] = wcp;
-            s_M[warp] = wM;
-            s_m[warp] = wm;
+            s_pre_w = pw;
+            s_pre_cp = pc;
+            if (tile == ntiles - 1) {
+                c->pay_words = pw + tw;
+                c->k_total = pc + tc;
+            }
+            if (s_sum) atomicAdd(&c->sum_abs, s_sum);
         }
-        // constant-block bits of this warp's 8 blocks
-        {
-            uint32_t cb = __ballot_sync(FULL, lane < BPW && blk0 + lane < g.nb && my_w == 0) & 0xFFu;
-            if (lane == 0 && cb) atomicOr(&s_cbits[warp >> 2], cb << ((warp & 3) * 8));
-        }
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t vw = lane < TILE_WARPS ? s_w[lane] : 0, vc = lane < TILE_WARPS ? s_cp[lane] : 0;
-            uint32_t vM = lane < TILE_WARPS ? s_M[lane] : 0, vm = lane < TILE_WARPS ? s_m[lane] : 0;
-            // inclusive scans over the 8 warps
-            uint32_t iw = vw, ic = vc, iM = vM, im = vm;
-#pragma unroll
-            for (int o = 1; o < TILE_WARPS; o <<= 1) {
-                uint32_t t0 = __shfl_up_sync(FULL, iw, o), t1 = __shfl_up_sync(FULL, ic, o);
-                uint32_t t2 = __shfl_up_sync(FULL, iM, o), t3 = __shfl_up_sync(FULL, im, o);
-                if (lane >= o) { iw += t0; ic += t1; iM += t2; im += t3; }
-            }
-            uint32_t tw = __shfl_sync(FULL, iw, TILE_WARPS - 1), tc = __shfl_sync(FULL, ic, TILE_WARPS - 1);
-            uint32_t tM = __shfl_sync(FULL, iM, TILE_WARPS - 1), tm = __shfl_sync(FULL, im, TILE_WARPS - 1);
-            unsigned long long pw, pc;
-            lookback(desc, tile, tw, tc, pw, pc, status);
-            uint32_t bM = 0, bm = 0;
-            if (TOPO && lane == 0) {
-                if (tM) bM = atomicAdd(&c->cnt_max, tM);
-                if (tm) bm = atomicAdd(&c->cnt_min, tm);
-            }
-            bM = __shfl_sync(FULL, bM, 0);
-            bm = __shfl_sync(FULL, bm, 0);
-            if (lane < TILE_WARPS) {   // exclusive offsets per warp
-                s_w[lane] = iw - vw;
-                s_cp[lane] = ic - vc;
-                s_M[lane] = bM + iM - vM;
-                s_m[lane] = bm + im - vm;
-            }
-            if (lane == 0) {
-                s_pre_w = pw;
-                s_pre_cp = pc;
-                if (tile == ntiles - 1) {
-                    c->pay_words = pw + tw;
-                    c->k_total = pc + tc;
-                }
-            }
-        }
-        __syncthreads();
-        // ---- phase 2: write this warp's blocks
-        unsigned long long woff = s_pre_w + s_w[warp];
+    }
+    __syncthreads();
+    // ---- phase 2: coalesced copy of the packed planes, metadata, extremum lists
+    {
+        uint32_t* dst = o.pay + s_pre_w + s_w[warp];
+        for (uint32_t k = lane; k < wwords; k += 32) dst[k] = wpay[k];
+    }
+    if (lane < BPW && blk0 + lane < g.nb) {
+        o.width[blk0 + lane] = (uint8_t)my_w;
+        o.first[blk0 + lane] = my_first;
+    }
+    if (threadIdx.x < 2) {
+        const uint32_t wi = tile * 2 + threadIdx.x;
+        if (wi < ncw) o.cbits[wi] = s_cbits[threadIdx.x];
+    }
+    if (TOPO) {
         unsigned long long cpoff = s_pre_cp + s_cp[warp];
         uint32_t offM = s_M[warp], offm = s_m[warp];
         const uint32_t lt = lanemask_lt();
 #pragma unroll
         for (int j = 0; j < BPW; j++) {
-            const uint32_t b = blk0 + j;
-            if (b >= g.nb) break;
-            const uint32_t w = __shfl_sync(FULL, my_w, j);
-            const int32_t d = dreg[j];
-            if (w) {
-                const uint32_t m = (uint32_t)(d < 0 ? -d : d);
-                uint32_t word = __ballot_sync(FULL, d < 0);
-                for (uint32_t p = 0; p < w; p++) {
-                    uint32_t bp = __ballot_sync(FULL, (m >> p) & 1u);
-                    if (lane == p + 1) word = bp;
-                }
-                if (lane <= w) o.pay[woff + lane] = word;
-                woff += 1 + w;
+            if (blk0 + j >= g.nb) break;
+            const int lab = (labbits >> (2 * j)) & 3;
+            const uint32_t bM = __ballot_sync(FULL, lab == LAB_MAX);
+            const uint32_t bm = __ballot_sync(FULL, lab == LAB_MIN);
+            const uint32_t bb = bM | bm;
+            if (lab == LAB_MAX || lab == LAB_MIN) {
+                const uint32_t pos = (uint32_t)(cpoff + __popc(bb & lt));
+                const uint32_t key = ord_key(areg[j]);
+                if (lab == LAB_MAX) listM[offM + __popc(bM & lt)] = make_uint2(key, pos);
+                else listm[offm + __popc(bm & lt)] = make_uint2(~key, pos);
             }
-            if (TOPO) {
-                const int lab = (labbits >> (2 * j)) & 3;
-                const uint32_t bM = __ballot_sync(FULL, lab == LAB_MAX);
-                const uint32_t bm = __ballot_sync(FULL, lab == LAB_MIN);
-                const uint32_t bb = bM | bm;
-                if (lab == LAB_MAX || lab == LAB_MIN) {
-                    uint32_t pos = (uint32_t)(cpoff + __popc(bb & lt));
-                    uint32_t key = ord_key(areg[j]);
-                    if (lab == LAB_MAX) listM[offM + __popc(bM & lt)] = make_uint2(key, pos);
-                    else listm[offm + __popc(bm & lt)] = make_uint2(~key, pos);
-                }
-                cpoff += __popc(bb);
-                offM += __popc(bM);
-                offm += __popc(bm);
-            }
-        }
-        if (lane < BPW && blk0 + lane < g.nb) {
-            o.width[blk0 + lane] = (uint8_t)my_w;
-            o.first[blk0 + lane] = my_first;
-        }
-        __syncthreads();
-        if (threadIdx.x < 2) {
-            uint32_t wi = tile * 2 + threadIdx.x;
-            if (wi < ncw) o.cbits[wi] = s_cbits[threadIdx.x];
-            s_cbits[threadIdx.x] = 0;
+            cpoff += __popc(bb);
+            offM += __popc(bM);
+            offm += __popc(bm);
         }
     }
-    if (lane == 0 && sum_abs) atomicAdd(&c->sum_abs, sum_abs);
 }
 
 // Rank-sequence encoder: the same codec on the delta sequence (Section IV-A:
@@ -1032,11 +1029,9 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, Desc* 
                          int* status, cudaStream_t st) {
     EncOut o{reinterpret_cast<uint32_t*>(out + lo.s1), out + lo.s2,
              reinterpret_cast<int32_t*>(out + lo.s4), reinterpret_cast<uint32_t*>(out + lo.s5)};
-    uint32_t ntiles = (nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
-    uint32_t grid = hmin<uint32_t>(ntiles, (uint32_t)sms * 6);
-    if (grid == 0) grid = 1;
-    if (topo) k_encode_field<true><<<grid, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
-    else k_encode_field<false><<<grid, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
+    const uint32_t ntiles = (nb + TILE_BLOCKS - 1) / TILE_BLOCKS;   // one tile per CTA
+    if (topo) k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
+    else k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
 }
 
 void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint32_t* hist,

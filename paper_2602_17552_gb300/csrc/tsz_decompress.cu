@@ -210,40 +210,111 @@ __device__ __forceinline__ int colour_of(const Geo& g, uint32_t x, uint32_t y, u
     return g.ndim == 2 ? (int)((x + 2u * y) % 5u) : (int)((x + 2u * y + 3u * z) % 7u);
 }
 
+// Offsets of the RBF neighbourhood N_r(p) \ {p} in the fixed (z, y, x)
+// ascending order, with their squared length; built per CTA in shared memory.
+struct RbfTable {
+    int n;                 // number of offsets
+    float den_full;        // sum of the weights in table order (all in the domain)
+    int dx[122], dy[122], dz[122], d2[122];
+    int lin[122];          // linear offset dx + dy nx + dz nx ny
+};
+
+__device__ void build_rbf_table(RbfTable& T, const Geo& g, const Ctrl* c) {
+    if (threadIdx.x == 0) {
+        const int r = c->rbf_k / 2, rz = g.ndim == 3 ? r : 0;
+        int m = 0;
+        float den = 0.0f;
+        for (int dz = -rz; dz <= rz; dz++)
+            for (int dy = -r; dy <= r; dy++)
+                for (int dx = -r; dx <= r; dx++) {
+                    const int d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 == 0 || d2 > r * r) continue;
+                    T.dx[m] = dx;
+                    T.dy[m] = dy;
+                    T.dz[m] = dz;
+                    T.d2[m] = d2;
+                    T.lin[m] = dx + dy * (int)g.nx + dz * (int)g.nxy;
+                    den = __fadd_rn(den, c->g_rbf[d2 - 1]);
+                    m++;
+                }
+        T.n = m;
+        T.den_full = den;
+    }
+    __syncthreads();
+}
+
+// Relation of a neighbour value u to p once p moves by a step smaller than
+// half the smallest nonzero gap: distinct neighbours keep their side, ties go
+// to the side opposite the move (up: tie -> lower).
+__device__ __forceinline__ bool higher_after(float u, float fp, bool up) { return u > fp || (u == fp && !up); }
+__device__ __forceinline__ bool lower_after(float u, float fp, bool up) { return u < fp || (u == fp && up); }
+
 // RS^ candidate: returns true and the refined value when accepted.  Runs only
 // inside the cooperative rounds kernel, whose grid syncs order every write of
 // the previous colour before these (L1-cached) reads.
 __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const Geo& g, const Ctrl* c,
-                                 uint32_t p, uint32_t x, uint32_t y, uint32_t z, float& vout) {
-    const float Fp = F[p];
-    GlobalVal val{F};
+                                 const RbfTable& T, uint32_t p, uint32_t x, uint32_t y, uint32_t z, float& vout) {
     // a saddle label is only valid at interior points; anything else is a bad stream
     if (x == 0 || x + 1 >= g.nx || y == 0 || y + 1 >= g.ny || (g.ndim == 3 && (z == 0 || z + 1 >= g.nz)))
         return false;
-    if (classify(val, g, p, x, y, z, Fp) == LAB_SAD) return false;   // not lost (any more)
+    const float Fp = F[p];
     const uint32_t st[3] = {1u, g.nx, g.nxy};
-    float gmin = __int_as_float(0x7F800000);
+    float nb[6];
     for (int ax = 0; ax < g.ndim; ax++) {
-        float g1 = fabsf(__fsub_rn(F[p - st[ax]], Fp)), g2 = fabsf(__fsub_rn(F[p + st[ax]], Fp));
-        if (g1 > 0.0f && g1 < gmin) gmin = g1;
-        if (g2 > 0.0f && g2 < gmin) gmin = g2;
+        nb[2 * ax] = F[p - st[ax]];
+        nb[2 * ax + 1] = F[p + st[ax]];
+    }
+    // current type: s means the saddle is not lost (any more)
+    {
+        int ph = 0, pl = 0, px = 0;
+        for (int ax = 0; ax < g.ndim; ax++) {
+            const float a = nb[2 * ax], b = nb[2 * ax + 1];
+            if (a > Fp && b > Fp) ph++;
+            else if (a < Fp && b < Fp) pl++;
+            else px++;
+        }
+        if (px == 0 && ph > 0 && pl > 0) return false;
+    }
+    float gmin = __int_as_float(0x7F800000);
+    for (int i = 0; i < 2 * g.ndim; i++) {
+        const float gi = fabsf(__fsub_rn(nb[i], Fp));
+        if (gi > 0.0f && gi < gmin) gmin = gi;
     }
     if (isinf(gmin)) return false;
+    // Exact shortcut: |v - Fp| <= gmin / 2 keeps every distinct neighbour on its
+    // side, so p's type with v depends only on the direction of the move; if
+    // neither direction gives a saddle, check (a) below rejects every v.
+    bool feasible[2];
+    for (int up = 0; up < 2; up++) {
+        int ph = 0, pl = 0, px = 0;
+        for (int ax = 0; ax < g.ndim; ax++) {
+            const float a = nb[2 * ax], b = nb[2 * ax + 1];
+            if (higher_after(a, Fp, up) && higher_after(b, Fp, up)) ph++;
+            else if (lower_after(a, Fp, up) && lower_after(b, Fp, up)) pl++;
+            else px++;
+        }
+        feasible[up] = px == 0 && ph > 0 && pl > 0;
+    }
+    if (!feasible[0] && !feasible[1]) return false;
     // normalised Gaussian kernel over N_r(p) \ {p}, fixed (z, y, x) order
-    const int r = c->rbf_k / 2, rz = g.ndim == 3 ? r : 0;
-    float num = 0.0f, den = 0.0f;
-    for (int dz = -rz; dz <= rz; dz++)
-        for (int dy = -r; dy <= r; dy++)
-            for (int dx = -r; dx <= r; dx++) {
-                const int d2 = dx * dx + dy * dy + dz * dz;
-                if (d2 == 0 || d2 > r * r) continue;
-                const long long xx = (long long)x + dx, yy = (long long)y + dy, zz = (long long)z + dz;
-                if (xx < 0 || yy < 0 || zz < 0 || xx >= g.nx || yy >= g.ny || zz >= g.nz) continue;
-                const float gw = c->g_rbf[d2 - 1];
-                const float fv = F[(uint32_t)xx + g.nx * ((uint32_t)yy + g.ny * (uint32_t)zz)];
-                num = __fadd_rn(num, __fmul_rn(gw, fv));
-                den = __fadd_rn(den, gw);
-            }
+    const int r = c->rbf_k / 2;
+    const bool inside = x >= (uint32_t)r && x + r < g.nx && y >= (uint32_t)r && y + r < g.ny &&
+                        (g.ndim == 2 || (z >= (uint32_t)r && z + r < g.nz));
+    float num = 0.0f, den;
+    if (inside) {
+#pragma unroll 8
+        for (int e = 0; e < T.n; e++) num = __fadd_rn(num, __fmul_rn(c->g_rbf[T.d2[e] - 1], F[(int)p + T.lin[e]]));
+        den = T.den_full;
+    } else {
+        den = 0.0f;
+        for (int e = 0; e < T.n; e++) {
+            const long long xx = (long long)x + T.dx[e], yy = (long long)y + T.dy[e], zz = (long long)z + T.dz[e];
+            if (xx < 0 || yy < 0 || zz < 0 || xx >= g.nx || yy >= g.ny || zz >= g.nz) continue;
+            const float gw = c->g_rbf[T.d2[e] - 1];
+            num = __fadd_rn(num, __fmul_rn(gw, F[(int)p + T.lin[e]]));
+            den = __fadd_rn(den, gw);
+        }
+    }
     const float u = __fdiv_rn(num, den);
     const float capv = fminf(__fmul_rn(0.1f, c->h_f), __fmul_rn(0.5f, gmin));
     float stp = __fsub_rn(u, Fp);
@@ -251,9 +322,10 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
     if (stp < -capv) stp = -capv;
     const float v = __fadd_rn(Fp, stp);
     if (v == Fp) return false;
+    GlobalVal val{F};
     OverrideVal nv{F, p, v};
-    if (classify(nv, g, p, x, y, z, v) != LAB_SAD) return false;
-    for (int ax = 0; ax < g.ndim; ax++) {
+    if (classify(nv, g, p, x, y, z, v) != LAB_SAD) return false;   // (a)
+    for (int ax = 0; ax < g.ndim; ax++) {                          // (b)
         for (int sg = -1; sg <= 1; sg += 2) {
             const uint32_t q = sg < 0 ? p - st[ax] : p + st[ax];
             uint32_t qx = x, qy = y, qz = z;
@@ -266,7 +338,7 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
             if (tn != to && tn != label_at(labels, q)) return false;
         }
     }
-    if (!(fabsf(__fsub_rn(v, Fp)) <= c->h_f)) return false;
+    if (!(fabsf(__fsub_rn(v, Fp)) <= c->h_f)) return false;       // (c)
     vout = v;
     return true;
 }
@@ -413,6 +485,14 @@ __device__ __forceinline__ void mark_done(uint32_t* flags, int k, uint32_t tile)
     }
 }
 
+// Tiles between a point and its farthest face neighbour (+1 for the tile
+// boundary, +1 spare), capped at the tile count.
+__host__ __device__ inline uint32_t fused_reach(const Geo& g, uint32_t ntiles) {
+    const uint32_t reach = g.ndim == 3 ? g.nxy : g.nx;
+    const uint32_t h = reach / (TILE_BLOCKS * L) + 2;
+    return h < ntiles ? h : ntiles;
+}
+
 struct FusedArgs {
     const uint8_t* in;
     Ctrl* c;
@@ -429,15 +509,21 @@ struct FusedArgs {
 };
 
 template <bool TOPO>
-__device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo, uint32_t t, uint32_t* s_w,
-                             uint32_t* s_cp, bool& corrupt) {
+__device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo, uint32_t t, uint32_t* s_pay,
+                             uint32_t* s_w, uint32_t* s_cp, bool& corrupt) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint8_t* widths = A.in + lo.s2;
     const int32_t* firsts = reinterpret_cast<const int32_t*>(A.in + lo.s4);
     const uint32_t* pay = reinterpret_cast<const uint32_t*>(A.in + lo.s5);
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
-    const unsigned long long pay_words = A.c->pay_words, k = A.c->k_total;
+    const unsigned long long k = A.c->k_total;
     const float w_f = A.c->w_f;
+    // the tile's payload is one contiguous word range: stage it with coalesced loads
+    const unsigned long long P0 = A.pay_pre[t], P1 = A.pay_pre[t + 1];
+    uint32_t len = 0;
+    if (P1 >= P0 && P1 - P0 <= (unsigned long long)TILE_BLOCKS * 33 && P1 <= A.c->pay_words) len = (uint32_t)(P1 - P0);
+    else corrupt = true;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_pay[i] = __ldg(pay + P0 + i);
     const uint32_t blk0 = t * TILE_BLOCKS + warp * BPW;
     uint32_t my_w = 0;
     int32_t my_first = 0;
@@ -467,7 +553,8 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
         s_cp[warp] = wcp;
     }
     __syncthreads();
-    unsigned long long woff = A.pay_pre[t], cpoff = A.cp_pre[t];
+    uint32_t woff = 0;
+    unsigned long long cpoff = A.cp_pre[t];
     for (int w = 0; w < warp; w++) {
         woff += s_w[w];
         cpoff += s_cp[w];
@@ -481,7 +568,7 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
         const int32_t first = __shfl_sync(FULL, my_first, j);
         int32_t q = first;
         if (w) {
-            if (woff + 1 + w <= pay_words) q = decode_block(pay, woff, w, first, lane);
+            if (woff + 1 + w <= len) q = decode_block(s_pay, woff, w, first, lane);
             else corrupt = true;
             woff += 1 + w;
         }
@@ -596,6 +683,7 @@ __device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* 
 
 template <bool TOPO>
 __device__ void fused_body(const FusedArgs& A) {
+    __shared__ uint32_t s_pay[TILE_BLOCKS * 33];
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_w[TILE_WARPS], s_cp[TILE_WARPS];
     Ctrl* c = A.c;
@@ -603,39 +691,37 @@ __device__ void fused_body(const FusedArgs& A) {
     const Layout lo = c->lo;
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
     const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
-    const uint32_t reach = g.ndim == 3 ? g.nxy : g.nx;
-    const uint32_t H = TOPO ? (uint32_t)hmin<uint64_t>(ntiles, reach / (TILE_BLOCKS * L) + 2) : 0u;
+    const uint32_t H = TOPO ? fused_reach(g, ntiles) : 0u;
     const uint32_t total = ntiles + 3 * H;
     bool corrupt = false;
     unsigned long long restored = 0, skipped = 0;
     while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_fused, 1u);
-        __syncthreads();
-        const uint32_t t = s_tile;
-        __syncthreads();
-        if (t >= total) break;
-        if (t < ntiles) {
-            stage_decode<TOPO>(A, g, lo, t, s_w, s_cp, corrupt);
-            mark_done(A.flags, 1, t);
+    if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_fused, 1u);
+    __syncthreads();
+    const uint32_t t = s_tile;
+    __syncthreads();
+    if (t >= total) break;
+    if (t < ntiles) {
+        stage_decode<TOPO>(A, g, lo, t, s_pay, s_w, s_cp, corrupt);
+        mark_done(A.flags, 1, t);
+    }
+    if (TOPO) {
+        const long long s2 = (long long)t - H, s3 = (long long)t - 2 * H, s4 = (long long)t - 3 * H;
+        if (s2 >= 0 && s2 < ntiles) {
+            wait_front(c, A.flags, 1, (uint32_t)hmin<long long>(s2 + H, ntiles - 1) + 1, ntiles, A.status);
+            stage_extrema(A, g, labels, (uint32_t)s2, restored, skipped);
+            mark_done(A.flags, 2, (uint32_t)s2);
         }
-        if (TOPO) {
-            const long long s2 = (long long)t - H, s3 = (long long)t - 2 * H, s4 = (long long)t - 3 * H;
-            if (s2 >= 0 && s2 < ntiles) {
-                wait_front(c, A.flags, 1, (uint32_t)hmin<long long>(s2 + H, ntiles - 1) + 1, ntiles, A.status);
-                stage_extrema(A, g, labels, (uint32_t)s2, restored, skipped);
-                mark_done(A.flags, 2, (uint32_t)s2);
-            }
-            if (s3 >= 0 && s3 < ntiles) {
-                wait_front(c, A.flags, 2, (uint32_t)hmin<long long>(s3 + H, ntiles - 1) + 1, ntiles, A.status);
-                stage_apply(A, g, (uint32_t)s3);
-                mark_done(A.flags, 3, (uint32_t)s3);
-            }
-            if (s4 >= 0 && s4 < ntiles) {
-                wait_front(c, A.flags, 3, (uint32_t)hmin<long long>(s4 + H, ntiles - 1) + 1, ntiles, A.status);
-                stage_saddles(A, g, labels, (uint32_t)s4);
-                __syncthreads();
-            }
+        if (s3 >= 0 && s3 < ntiles) {
+            wait_front(c, A.flags, 2, (uint32_t)hmin<long long>(s3 + H, ntiles - 1) + 1, ntiles, A.status);
+            stage_apply(A, g, (uint32_t)s3);
+            mark_done(A.flags, 3, (uint32_t)s3);
         }
+        if (s4 >= 0 && s4 < ntiles) {
+            wait_front(c, A.flags, 3, (uint32_t)hmin<long long>(s4 + H, ntiles - 1) + 1, ntiles, A.status);
+            stage_saddles(A, g, labels, (uint32_t)s4);
+        }
+    }
     }
     if (corrupt) set_status(A.status, ST_CORRUPT);
     if (TOPO) {
@@ -657,10 +743,13 @@ __global__ void __launch_bounds__(256) k_decode_fused(FusedArgs A) {
 }
 
 // RS^ colour rounds over the lost-saddle list (cooperative: the grid syncs
-// between the evaluation and the write of every colour).
+// between the evaluation and the write of every colour).  The list is first
+// bucketed by colour so that each round touches only its own candidates.
 __global__ void __launch_bounds__(256) k_saddle_rounds(const uint8_t* __restrict__ in, Ctrl* c, float* out,
-                                                       const uint32_t* sad, float* sadv, uint32_t sad_cap,
-                                                       int* status) {
+                                                       const uint32_t* sad, uint32_t* sadb, float* sadv,
+                                                       uint32_t sad_cap, int* status) {
+    __shared__ RbfTable T;
+    __shared__ uint32_t s_cnt[8], s_base[8];
     cg::grid_group grid = cg::this_grid();
     // uniform across the grid: neither word is written by this kernel
     if (*status || (c->flags & FLAG_NO_TOPO)) return;
@@ -669,26 +758,58 @@ __global__ void __launch_bounds__(256) k_saddle_rounds(const uint8_t* __restrict
     const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x, nth = gridDim.x * blockDim.x;
     const uint32_t ns = hmin<uint32_t>(c->sad_cnt[0], sad_cap);
     const int ncol = g.ndim == 2 ? 5 : 7;
+    build_rbf_table(T, g, c);
+    // bucket by colour
+    if (threadIdx.x < 8) s_cnt[threadIdx.x] = 0;
+    __syncthreads();
+    for (uint32_t j = tid; j < ns; j += nth) {
+        uint32_t x, y, z;
+        coords(g, sad[j], x, y, z);
+        atomicAdd(&s_cnt[colour_of(g, x, y, z)], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 8 && s_cnt[threadIdx.x]) atomicAdd(&c->sad_col[threadIdx.x], s_cnt[threadIdx.x]);
+    grid.sync();
+    uint32_t base[8], cnt[8];
+    {
+        uint32_t b = 0;
+        for (int k = 0; k < 8; k++) {
+            base[k] = b;
+            cnt[k] = *(volatile unsigned int*)&c->sad_col[k];
+            b += cnt[k];
+        }
+    }
+    // each block reserves one range per colour, then fills it through shared memory
+    if (threadIdx.x < 8) {
+        s_base[threadIdx.x] = s_cnt[threadIdx.x] ? atomicAdd(&c->sad_fill[threadIdx.x], s_cnt[threadIdx.x]) : 0u;
+        s_cnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j < ns; j += nth) {
+        const uint32_t p = sad[j];
+        uint32_t x, y, z;
+        coords(g, p, x, y, z);
+        const int col = colour_of(g, x, y, z);
+        const uint32_t slot = s_base[col] + atomicAdd(&s_cnt[col], 1u);
+        sadb[base[col] + slot] = p;
+    }
+    grid.sync();
     unsigned long long fixed = 0;
     for (int sw = 0; sw < c->rs_sweeps; sw++) {
         for (int col = 0; col < ncol; col++) {
-            for (uint32_t j = tid; j < ns; j += nth) {
-                const uint32_t p = sad[j];
+            const uint32_t b0 = base[col], nc = cnt[col];
+            for (uint32_t j = tid; j < nc; j += nth) {
+                const uint32_t p = sadb[b0 + j];
                 uint32_t x, y, z;
                 coords(g, p, x, y, z);
-                if (colour_of(g, x, y, z) != col) continue;
                 float v;
-                sadv[j] = saddle_candidate(out, labels, g, c, p, x, y, z, v) ? v : __int_as_float(0x7FC00000);
+                sadv[b0 + j] = saddle_candidate(out, labels, g, c, T, p, x, y, z, v) ? v : __int_as_float(0x7FC00000);
             }
             grid.sync();
-            for (uint32_t j = tid; j < ns; j += nth) {
-                const uint32_t p = sad[j];
-                uint32_t x, y, z;
-                coords(g, p, x, y, z);
-                if (colour_of(g, x, y, z) != col) continue;
-                const float v = sadv[j];
+            for (uint32_t j = tid; j < nc; j += nth) {
+                const float v = sadv[b0 + j];
                 if (!isnan(v)) {
-                    out[p] = v;
+                    out[sadb[b0 + j]] = v;
                     fixed++;
                 }
             }
@@ -723,23 +844,19 @@ void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* 
 
 void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
                          const uint32_t* cp_pre, const int32_t* delta, uint32_t* cp_idx, float* newv,
-                         uint32_t* flags, uint32_t* sad, uint32_t sad_cap, int sms, int* status,
-                         cudaStream_t st) {
-    static int per_sm = -1;
-    if (per_sm < 0) {
-        int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_decode_fused, 256, 0) != cudaSuccess || b < 1)
-            b = 1;
-        per_sm = b;
-    }
+                         uint32_t* flags, uint32_t* sad, uint32_t sad_cap, uint32_t ntiles_dec, uint32_t h_bound,
+                         int sms, int* status, cudaStream_t st) {
     FusedArgs A{in, c, out, pay_pre, cp_pre, delta, cp_idx, newv, flags, sad, sad_cap, status};
-    // persistent: never more CTAs than can be resident at once (waits point at
-    // tiles held by running CTAs)
-    k_decode_fused<<<per_sm * sms, 256, 0, st>>>(A);
+    // About one virtual tile per CTA (ntiles decode tiles plus 3H trailing stage
+    // slots; H is known only on the device, so CTAs keep taking virtual tiles
+    // until all are done).  Waits only point at lower tiles, taken by CTAs that
+    // started earlier, so any residency makes progress.
+    const uint32_t grid = ntiles_dec + 3 * hmin<uint32_t>(ntiles_dec, h_bound);
+    k_decode_fused<<<grid, 256, 0, st>>>(A);
 }
 
-cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, float* sadv,
-                                 uint32_t sad_cap, int sms, int* status, cudaStream_t st) {
+cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, uint32_t* sadb,
+                                 float* sadv, uint32_t sad_cap, int sms, int* status, cudaStream_t st) {
     static int per_sm = -1;
     if (per_sm < 0) {
         int b = 0;
@@ -747,8 +864,8 @@ cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const u
             b = 1;
         per_sm = b < 4 ? b : 4;
     }
-    void* args[] = {(void*)&in, (void*)&c, (void*)&out, (void*)&sad, (void*)&sadv, (void*)&sad_cap,
-                    (void*)&status};
+    void* args[] = {(void*)&in, (void*)&c, (void*)&out, (void*)&sad, (void*)&sadb, (void*)&sadv,
+                    (void*)&sad_cap, (void*)&status};
     return cudaLaunchCooperativeKernel((const void*)k_saddle_rounds, dim3(per_sm * sms), dim3(256), args, 0, st);
 }
 }  // namespace tsz

@@ -49,10 +49,10 @@ void launch_decode_ranks(const uint8_t* in, Ctrl* c, Desc* desc, int32_t* delta,
                          int sms, int* status, cudaStream_t st);
 void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
                          const uint32_t* cp_pre, const int32_t* delta, uint32_t* cp_idx, float* newv,
-                         uint32_t* flags, uint32_t* sad, uint32_t sad_cap, int sms, int* status,
-                         cudaStream_t st);
-cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, float* sadv,
-                                 uint32_t sad_cap, int sms, int* status, cudaStream_t st);
+                         uint32_t* flags, uint32_t* sad, uint32_t sad_cap, uint32_t ntiles_dec, uint32_t h_bound,
+                         int sms, int* status, cudaStream_t st);
+cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, uint32_t* sadb,
+                                 float* sadv, uint32_t sad_cap, int sms, int* status, cudaStream_t st);
 
 // ---- analysis
 void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsigned long long* out12,
