@@ -40,6 +40,7 @@ static bool make_geo(int ndim, const uint64_t dims[3], Geo& g) {
     g.nxy = (uint32_t)nxy;
     g.n = (uint32_t)(nxy * nz);
     g.nb = (uint32_t)cdiv(g.n, L);
+    geo_divs(g);
     return true;
 }
 

@@ -38,13 +38,46 @@ template <class T>
 __host__ __device__ inline T hmin(T a, T b) { return a < b ? a : b; }
 __host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 
+// Division by a run-time invariant d by multiply-high and shifts (the
+// round-up method of Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994): exact for every 32-bit dividend.
+struct FastDiv {
+    uint32_t d, m, s1, s2;
+};
+
+__host__ __device__ inline FastDiv make_fastdiv(uint32_t d) {
+    FastDiv f;
+    f.d = d;
+    uint32_t l = 0;
+    while (l < 32 && (1ull << l) < d) l++;                 // l = ceil(log2 d)
+    f.m = (uint32_t)(((1ull << 32) * ((1ull << l) - d)) / d + 1);
+    f.s1 = l < 1 ? l : 1;
+    f.s2 = l > 0 ? l - 1 : 0;
+    return f;
+}
+
+__host__ __device__ inline uint32_t fdiv(uint32_t n, const FastDiv& f) {
+#ifdef __CUDA_ARCH__
+    const uint32_t t = __umulhi(f.m, n);
+#else
+    const uint32_t t = (uint32_t)(((uint64_t)f.m * n) >> 32);
+#endif
+    return (t + ((n - t) >> f.s1)) >> f.s2;
+}
+
 struct Geo {
     int ndim;
     uint32_t nx, ny, nz;   // nz = 1 in 2D
     uint32_t n;            // nx * ny * nz < 2^31
     uint32_t nxy;
     uint32_t nb;           // blocks of L
+    FastDiv fx, fy;        // division by nx and by ny
 };
+
+__host__ __device__ inline void geo_divs(Geo& g) {
+    g.fx = make_fastdiv(g.nx);
+    g.fy = make_fastdiv(g.ny);
+}
 
 // Stream layout of Section IV-A as placed in this format: header, (1) const
 // bitmap, (2) widths, (4) first values, (6) labels, (3)+(5) planes, (7) ranks.
@@ -201,10 +234,35 @@ struct GlobalVal {
 
 __device__ __forceinline__ void coords(const Geo& g, uint32_t i, uint32_t& x, uint32_t& y,
                                        uint32_t& z) {
-    x = i % g.nx;
-    uint32_t t = i / g.nx;
-    y = t % g.ny;
-    z = t / g.ny;
+    const uint32_t t = fdiv(i, g.fx);
+    x = i - t * g.nx;
+    z = fdiv(t, g.fy);
+    y = t - z * g.ny;
+}
+
+// classify() for a point known to have both neighbours on every axis: the same
+// rule as a straight-line sequence of comparisons.
+template <class Val>
+__device__ __forceinline__ int classify_interior(const Val& val, const Geo& g, uint32_t i, float v) {
+    const float xm = val(i - 1), xp = val(i + 1), ym = val(i - g.nx), yp = val(i + g.nx);
+    const bool three = g.ndim == 3;
+    const float zm = three ? val(i - g.nxy) : xm, zp = three ? val(i + g.nxy) : xp;
+    const bool Hx = xm > v && xp > v, Lx = xm < v && xp < v;
+    const bool Hy = ym > v && yp > v, Ly = ym < v && yp < v;
+    const bool Hz = !three || (zm > v && zp > v), Lz = !three || (zm < v && zp < v);
+    const bool m = Hx && Hy && Hz, M = Lx && Ly && Lz;
+    const bool s = (Hx || Lx) && (Hy || Ly) && (Hz || Lz) && !m && !M;
+    return (int)((uint32_t)(m | M) | ((uint32_t)(s | M) << 1));
+}
+
+__device__ __forceinline__ bool is_interior(const Geo& g, uint32_t x, uint32_t y, uint32_t z) {
+    return x > 0 && x + 1 < g.nx && y > 0 && y + 1 < g.ny && (g.ndim == 2 || (z > 0 && z + 1 < g.nz));
+}
+
+template <class Val>
+__device__ __forceinline__ int classify_any(const Val& val, const Geo& g, uint32_t i, uint32_t x, uint32_t y,
+                                            uint32_t z, float v) {
+    return is_interior(g, x, y, z) ? classify_interior(val, g, i, v) : classify(val, g, i, x, y, z, v);
 }
 
 // ----------------------------------------------------- decoupled look-back

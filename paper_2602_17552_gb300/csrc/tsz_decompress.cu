@@ -75,6 +75,7 @@ __global__ void k_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_o
     g.n = (uint32_t)n_out;
     g.nxy = (uint32_t)(nx * ny);
     g.nb = (uint32_t)nb;
+    geo_divs(g);
     c->g = g;
     c->flags = flags;
     c->w_f = w_f;
@@ -324,7 +325,7 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
     if (v == Fp) return false;
     GlobalVal val{F};
     OverrideVal nv{F, p, v};
-    if (classify(nv, g, p, x, y, z, v) != LAB_SAD) return false;   // (a)
+    if (classify_interior(nv, g, p, v) != LAB_SAD) return false;   // (a): p is interior
     for (int ax = 0; ax < g.ndim; ax++) {                          // (b)
         for (int sg = -1; sg <= 1; sg += 2) {
             const uint32_t q = sg < 0 ? p - st[ax] : p + st[ax];
@@ -333,8 +334,8 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
             else if (ax == 1) qy = sg < 0 ? y - 1 : y + 1;
             else qz = sg < 0 ? z - 1 : z + 1;
             const float fq = F[q];
-            const int tn = classify(nv, g, q, qx, qy, qz, fq);
-            const int to = classify(val, g, q, qx, qy, qz, fq);
+            const int tn = classify_any(nv, g, q, qx, qy, qz, fq);
+            const int to = classify_any(val, g, q, qx, qy, qz, fq);
             if (tn != to && tn != label_at(labels, q)) return false;
         }
     }
@@ -456,7 +457,11 @@ __device__ __forceinline__ void wait_front(Ctrl* c, const uint32_t* flags, int k
         volatile unsigned int* fr = &c->front[k];
         uint32_t spins = 0;
         while (true) {
-            uint32_t f = *fr;
+            // one read, broadcast: every branch below must be warp-uniform,
+            // since the loop body uses full-warp ballots
+            uint32_t f = 0;
+            if (lane == 0) f = *fr;
+            f = __shfl_sync(FULL, f, 0);
             if (f >= need) break;
             const uint32_t j = f + lane;
             const uint32_t v = j < ntiles ? *(volatile const uint32_t*)(flags + j) : 0u;
@@ -470,14 +475,17 @@ __device__ __forceinline__ void wait_front(Ctrl* c, const uint32_t* flags, int k
                 if (lane == 0) set_status(status, ST_TIMEOUT);
                 break;
             }
-            __nanosleep(spins < 32 ? 64 : 256);
+            __nanosleep(spins < 64 ? 32 : 256);
         }
         __threadfence();
     }
     __syncthreads();
 }
 
-__device__ __forceinline__ void mark_done(uint32_t* flags, int k, uint32_t tile) {
+// Publish stage k of `tile` (waiters advance the frontier, 32 tiles per poll).
+__device__ __forceinline__ void mark_done(Ctrl* c, uint32_t* flags, int k, uint32_t tile, uint32_t ntiles) {
+    (void)c;
+    (void)ntiles;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -586,12 +594,14 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
     }
 }
 
-// CP^ + RP^ on one tile's extrema, reading the D0 snapshot (Jacobi).
+// CP^ + RP^ on one tile's extrema, reading the D0 snapshot (Jacobi).  Each
+// neighbour is loaded once and serves both the lost test and the extreme
+// neighbour value.
 __device__ void stage_extrema(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t s,
                               unsigned long long& restored, unsigned long long& skipped) {
     const uint32_t P0 = A.cp_pre[s], P1 = A.cp_pre[s + 1];
     const float h_f = A.c->h_f;
-    CgVal val{A.out};
+    const uint32_t st[3] = {1u, g.nx, g.nxy};
     for (uint32_t pos = P0 + threadIdx.x; pos < P1; pos += blockDim.x) {
         const uint32_t p = __ldcg(A.cp_idx + pos);
         float nv = __int_as_float(0x7FC00000);
@@ -600,29 +610,43 @@ __device__ void stage_extrema(const FusedArgs& A, const Geo& g, const uint32_t* 
             continue;
         }
         const int lab = label_at(labels, p);
+        const long long dl = __ldg(A.delta + pos);
         uint32_t x, y, z;
         coords(g, p, x, y, z);
-        const float v0 = val(p);
-        if (classify(val, g, p, x, y, z, v0) != lab) {
-            const uint32_t st[3] = {1u, g.nx, g.nxy};
-            const uint32_t cc[3] = {x, y, z}, dd[3] = {g.nx, g.ny, g.nz};
+        const uint32_t cc[3] = {x, y, z}, dd[3] = {g.nx, g.ny, g.nz};
+        const float v0 = __ldcg(A.out + p);
+        // neighbours in (x-, x+, y-, y+, z-, z+) order; absent ones flagged
+        float u[6];
+        bool have[6];
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            const bool on = ax < g.ndim;
+            have[2 * ax] = on && cc[ax] > 0;
+            have[2 * ax + 1] = on && cc[ax] + 1 < dd[ax];
+            u[2 * ax] = have[2 * ax] ? __ldcg(A.out + p - st[ax]) : 0.0f;
+            u[2 * ax + 1] = have[2 * ax + 1] ? __ldcg(A.out + p + st[ax]) : 0.0f;
+        }
+        // type of p in D0: for a labelled extremum only m / M matter (no FT)
+        int nn = 0, nhi = 0, nlo = 0;
+#pragma unroll
+        for (int e = 0; e < 6; e++) {
+            if (!have[e]) continue;
+            nn++;
+            nhi += u[e] > v0;
+            nlo += u[e] < v0;
+        }
+        const bool kept = nn > 0 && (lab == LAB_MIN ? nhi == nn : nlo == nn);
+        if (!kept) {
             float ext = 0.0f;
-            bool have = false;
-            for (int ax = 0; ax < g.ndim; ax++) {
-                if (cc[ax] > 0) {
-                    const float u = val(p - st[ax]);
-                    if (!have || (lab == LAB_MAX ? u > ext : u < ext)) ext = u;
-                    have = true;
-                }
-                if (cc[ax] + 1 < dd[ax]) {
-                    const float u = val(p + st[ax]);
-                    if (!have || (lab == LAB_MAX ? u > ext : u < ext)) ext = u;
-                    have = true;
-                }
+            bool any = false;
+#pragma unroll
+            for (int e = 0; e < 6; e++) {
+                if (!have[e]) continue;
+                if (!any || (lab == LAB_MAX ? u[e] > ext : u[e] < ext)) ext = u[e];
+                any = true;
             }
             float v;
-            const long long dl = __ldg(A.delta + pos);
-            if (have && step_ulps(ext, lab == LAB_MAX ? dl : -dl, v) && fabsf(__fsub_rn(v, v0)) <= h_f) {
+            if (any && step_ulps(ext, lab == LAB_MAX ? dl : -dl, v) && fabsf(__fsub_rn(v, v0)) <= h_f) {
                 nv = v;
                 restored++;
             } else {
@@ -659,7 +683,7 @@ __device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* 
         if (p >= g.n) break;   // padding bits of a damaged stream
         uint32_t x, y, z;
         coords(g, p, x, y, z);
-        if (classify(val, g, p, x, y, z, val(p)) != LAB_SAD) lost |= 1u << (bit >> 1);
+        if (classify_any(val, g, p, x, y, z, val(p)) != LAB_SAD) lost |= 1u << (bit >> 1);
     }
     const uint32_t cnt = __popc(lost);
     uint32_t incl = cnt;
@@ -703,19 +727,19 @@ __device__ void fused_body(const FusedArgs& A) {
     if (t >= total) break;
     if (t < ntiles) {
         stage_decode<TOPO>(A, g, lo, t, s_pay, s_w, s_cp, corrupt);
-        mark_done(A.flags, 1, t);
+        mark_done(c, A.flags, 1, t, ntiles);
     }
     if (TOPO) {
         const long long s2 = (long long)t - H, s3 = (long long)t - 2 * H, s4 = (long long)t - 3 * H;
         if (s2 >= 0 && s2 < ntiles) {
             wait_front(c, A.flags, 1, (uint32_t)hmin<long long>(s2 + H, ntiles - 1) + 1, ntiles, A.status);
             stage_extrema(A, g, labels, (uint32_t)s2, restored, skipped);
-            mark_done(A.flags, 2, (uint32_t)s2);
+            mark_done(c, A.flags, 2, (uint32_t)s2, ntiles);
         }
         if (s3 >= 0 && s3 < ntiles) {
             wait_front(c, A.flags, 2, (uint32_t)hmin<long long>(s3 + H, ntiles - 1) + 1, ntiles, A.status);
             stage_apply(A, g, (uint32_t)s3);
-            mark_done(A.flags, 3, (uint32_t)s3);
+            mark_done(c, A.flags, 3, (uint32_t)s3, ntiles);
         }
         if (s4 >= 0 && s4 < ntiles) {
             wait_front(c, A.flags, 3, (uint32_t)hmin<long long>(s4 + H, ntiles - 1) + 1, ntiles, A.status);
@@ -736,7 +760,7 @@ __device__ void fused_body(const FusedArgs& A) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_decode_fused(FusedArgs A) {
+__global__ void __launch_bounds__(256, 6) k_decode_fused(FusedArgs A) {
     if (*A.status) return;
     if (A.c->flags & FLAG_NO_TOPO) fused_body<false>(A);
     else fused_body<true>(A);
