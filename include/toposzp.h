@@ -140,6 +140,32 @@ toposzp_status toposzp_critical_points(const float* field, int ndim, const uint6
 toposzp_status toposzp_topo_errors(const uint32_t* labels_orig, const uint32_t* labels_dec,
                                    uint64_t n, uint64_t* out12, toposzp_stream stream);
 
+/* Compress without any workspace from the caller.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory --
+ * e.g. an in-situ hook inside a simulation whose device memory is entirely
+ * owned by the simulation's own pool allocator, or a caller running while a
+ * CUDA graph is being captured, where a cudaMalloc would break the capture.
+ * Same arguments, results and stream semantics as toposzp_compress, minus the
+ * workspace: the library uses a static device array of its own instead.
+ *   - Fields of at most toposzp_noalloc_max_points() points (262,144: e.g.
+ *     512 x 512, or a 1 MiB float32 field); larger ones return
+ *     TOPOSZP_ERR_UNSUPPORTED before any work is queued.
+ *   - The array (about 5.4 MB) is part of the library's image: every GPU that
+ *     loads the library holds it until the process exits.
+ *   - No cudaMalloc, cudaFree or other allocating call is made.  The first
+ *     call on each device looks up the array's device address (with that
+ *     device current); make that first call before any stream capture.
+ *   - Every call, on any stream, shares the one array per device and clears
+ *     the parts that must start at zero; calls whose GPU work overlaps in time
+ *     race on it, so serialise them (one stream, or events). */
+toposzp_status toposzp_compress_noalloc(const float* field, int ndim, const uint64_t dims[3],
+                                        toposzp_eb_mode mode, double eb, const toposzp_params* params,
+                                        void* out, uint64_t out_capacity, uint64_t* out_size,
+                                        int32_t* status, toposzp_stream stream);
+
+/* Host.  Largest field (points) toposzp_compress_noalloc accepts. */
+uint64_t toposzp_noalloc_max_points(void);
+
 /* Host.  Profiling hook (no counterpart in the paper).  After a call with
  * count > 0, every toposzp_compress records events[0..4] (cudaEvent_t handles
  * owned by the caller) on its stream: before the range + CD kernel, after it,

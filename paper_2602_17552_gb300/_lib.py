@@ -42,7 +42,7 @@ class Info(ctypes.Structure):
 EXPORTS = ("toposzp_default_params", "toposzp_status_string", "toposzp_compress_bound",
            "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size", "toposzp_compress",
            "toposzp_inspect", "toposzp_decompress", "toposzp_critical_points", "toposzp_topo_errors",
-           "toposzp_set_stage_events")
+           "toposzp_set_stage_events", "toposzp_compress_noalloc", "toposzp_noalloc_max_points")
 
 _lib = None
 
@@ -78,6 +78,11 @@ def load() -> ctypes.CDLL:
     L.toposzp_topo_errors.restype = c_int
     L.toposzp_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), c_int]
     L.toposzp_set_stage_events.restype = c_int
+    L.toposzp_compress_noalloc.argtypes = [vp, c_int, dims_t, c_int, ctypes.c_double, ctypes.POINTER(Params),
+                                           vp, u64, vp, i32p, vp]
+    L.toposzp_compress_noalloc.restype = c_int
+    L.toposzp_noalloc_max_points.argtypes = []
+    L.toposzp_noalloc_max_points.restype = u64
     _lib = L
     return L
 

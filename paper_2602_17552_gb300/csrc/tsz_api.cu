@@ -5,13 +5,14 @@
 // device data; every data-dependent size is consumed on the device.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "../../include/toposzp.h"
 #include "tsz_internal.h"
 
 namespace tsz {
 
-static uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
+constexpr uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
 constexpr uint64_t CTRL_BYTES = 4096;
 constexpr int SORT_G = 256;    // CTAs per list in the rank sort (fixed: sizes the workspace)
@@ -44,8 +45,8 @@ static bool make_geo(int ndim, const uint64_t dims[3], Geo& g) {
     return true;
 }
 
-CompressWs compress_ws(uint64_t n) {
-    CompressWs w;
+constexpr CompressWs compress_ws_c(uint64_t n) {
+    CompressWs w{};
     const uint64_t nb = cdiv(n, L);
     w.G = SORT_G;
     w.list_cap = (uint32_t)(cdiv(n, 2) + 1);
@@ -66,6 +67,8 @@ CompressWs compress_ws(uint64_t n) {
     w.end = o;
     return w;
 }
+
+CompressWs compress_ws(uint64_t n) { return compress_ws_c(n); }
 
 DecompressWs decompress_ws(uint64_t n) {
     DecompressWs w;
@@ -104,6 +107,36 @@ static cudaEvent_t g_stage_ev[9];
 static bool g_stage_on = false;
 static void stage(int i, cudaStream_t st) {
     if (g_stage_on) cudaEventRecord(g_stage_ev[i], st);
+}
+
+// ------------------------------------------------ allocation-free compress
+//
+// Scratch for toposzp_compress_noalloc: a file-scope device array sized for
+// the largest field that entry point accepts.  Every GPU that loads this
+// library holds it until the process exits.  Host code never uses the array's
+// name as an address: the device address is looked up once per device.
+constexpr uint64_t NOALLOC_MAX_POINTS = 1ull << 18;
+constexpr uint64_t NOALLOC_WS_BYTES = compress_ws_c(NOALLOC_MAX_POINTS).end;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_WS_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static void* g_noalloc_addr[NOALLOC_MAX_DEVICES];
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (set-up on the
+// first call per device, with that device current).
+static toposzp_status noalloc_scratch(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return TOPOSZP_ERR_CUDA;
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return TOPOSZP_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return TOPOSZP_ERR_CUDA;
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return TOPOSZP_OK;
 }
 
 }  // namespace tsz
@@ -219,6 +252,22 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     stage(4, st);
     return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;
 }
+
+toposzp_status toposzp_compress_noalloc(const float* field, int ndim, const uint64_t dims[3],
+                                        toposzp_eb_mode mode, double eb, const toposzp_params* params,
+                                        void* out, uint64_t out_capacity, uint64_t* out_size,
+                                        int32_t* status, toposzp_stream stream) {
+    Geo g;
+    if (!dims || !make_geo(ndim, dims, g)) return TOPOSZP_ERR_INVALID_ARG;
+    if (g.n > NOALLOC_MAX_POINTS) return TOPOSZP_ERR_UNSUPPORTED;   // larger than the static scratch
+    void* scratch = nullptr;
+    const toposzp_status st = noalloc_scratch(&scratch);
+    if (st != TOPOSZP_OK) return st;
+    return toposzp_compress(field, ndim, dims, mode, eb, params, out, out_capacity, out_size, scratch,
+                            NOALLOC_WS_BYTES, status, stream);
+}
+
+uint64_t toposzp_noalloc_max_points(void) { return NOALLOC_MAX_POINTS; }
 
 toposzp_status toposzp_inspect(const void* header_host, uint64_t header_bytes, toposzp_info* info) {
     if (!header_host || !info || header_bytes < HDR) return TOPOSZP_ERR_INVALID_ARG;

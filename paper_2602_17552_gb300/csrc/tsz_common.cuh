@@ -33,7 +33,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 // sleeps up to 256 ns), sets ST_TIMEOUT and lets the kernel finish.
 constexpr uint32_t SPIN_LIMIT = 1u << 22;
 
-__host__ __device__ inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+__host__ __device__ constexpr inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 template <class T>
 __host__ __device__ inline T hmin(T a, T b) { return a < b ? a : b; }
 __host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
