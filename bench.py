@@ -43,7 +43,12 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256"])
+    ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256", "batch", "serve"])
+    ap.add_argument("--fields", type=int, default=96, help="batch workload: number of fields")
+    ap.add_argument("--branches", type=int, default=0, help="batch workload: graph branches (0 = tuned)")
+    ap.add_argument("--requests", type=int, default=400, help="serve workload: number of requests")
+    ap.add_argument("--max-mb", type=float, default=256.0, help="serve workload: largest request (MB)")
+    ap.add_argument("--rate", type=float, default=0.0, help="serve workload: arrivals/s (0 = saturate)")
     ap.add_argument("--eb", type=float, default=1e-3)
     ap.add_argument("--side", type=int, default=512, help="edge of the 3D turbulence field")
     ap.add_argument("--no-topo", action="store_true")
@@ -378,10 +383,95 @@ def oracle_free_header(buf):
             "off_s5": u64(184), "off_s7": u64(192), "total": u64(200), "pay_words": u64(208)}
 
 
+def run_batch(args):
+    """Mixed batch: all fields through one CUDA-graph launch (compress, then
+    decompress) vs the same fields as per-field plain launches; aggregate GB/s."""
+    import torch
+    from paper_2602_17552_gb300 import batch, codec, synth
+    specs = synth.mixed_batch(count=args.fields)
+    fields = [s.make("cuda") for s in specs]
+    ebs = [s.eb for s in specs]
+    nbytes = sum(f.numel() * 4 for f in fields)
+    branches = args.branches or tuned_branches()
+    plan = batch.BatchPlan.create(fields, ebs, "rel", branches=branches).capture()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(max(3, args.warmup)):
+        plan.compress()
+        plan.decompress()
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(args.steps):
+        plan.compress()
+        plan.decompress()
+    ev[1].record()
+    torch.cuda.synchronize()
+    plan.check()
+    t_batch = ev[0].elapsed_time(ev[1]) / args.steps
+    # plain: one field after another on one stream, the same kernels
+    single = batch.BatchPlan.create(fields, ebs, "rel", branches=1)
+    for _ in range(max(3, args.warmup)):
+        single.run_eager("compress")
+        single.run_eager("decompress")
+    torch.cuda.synchronize()
+    ev[0].record()
+    for _ in range(args.steps):
+        single.run_eager("compress")
+        single.run_eager("decompress")
+    ev[2].record()
+    torch.cuda.synchronize()
+    t_plain = ev[0].elapsed_time(ev[2]) / args.steps
+    print(json.dumps({
+        "metric": "batched compress+decompress throughput (uncompressed bytes / round-trip time)",
+        "value": round(nbytes / (t_batch * 1e-3) / 1e9, 2), "unit": "GB/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(t_batch, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{len(fields)} mixed 2D/3D GRF fields ({nbytes / 1e9:.2f} GB), relative eb "
+                               "from {1e-2,1e-3,1e-4}, one CUDA graph launch per direction",
+                   "branches": branches},
+        "plain_per_field": {"value": round(nbytes / (t_plain * 1e-3) / 1e9, 2), "ms_per_step": round(t_plain, 3)},
+        "speedup_vs_plain": round(t_plain / t_batch, 3)}), flush=True)
+
+
+def tuned_branches():
+    try:
+        from paper_2602_17552_gb300 import autotune
+        return autotune.load().get("batch_branches", 8)
+    except Exception:
+        return 8
+
+
+def run_serve(args):
+    """Request stream served with continuous batching vs one request at a time."""
+    import torch
+    from paper_2602_17552_gb300 import serve, synth
+    rate = args.rate or 1e5
+    reqs = synth.request_stream(count=args.requests, rate_hz=rate, seed=7,
+                                max_bytes=int(args.max_mb * (1 << 20)))
+    srv = serve.Server(slots=8)
+    srv.run(reqs[: min(8, len(reqs))])          # warm-up
+    jobs = [serve.Job(r, r.spec.shape()) for r in reqs]
+    srv.produce(jobs)                            # inputs resident before the clock starts
+    served, _ = srv.run(reqs, produced=jobs)
+    serial, _ = srv.run(reqs, serial=True, produced=jobs)
+    a, b = served.summary(), serial.summary()
+    print(json.dumps({
+        "metric": "served throughput (aggregate uncompressed GB/s) and latency",
+        "value": round(a["aggregate_gbs"], 2), "unit": "GB/s", "n_gpus": 1, "steps": len(reqs), "warmup": 8,
+        "ms_per_step": round(1e3 * a["wall_s"] / len(reqs), 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{len(reqs)} compress/decompress requests, Poisson {rate:g}/s, 64 KB - "
+                               f"{args.max_mb:g} MB log-uniform, 2D/3D, rel eb 1e-5..1e-2", "slots": 8},
+        "served": a, "serial_plain": b}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

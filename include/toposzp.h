@@ -166,6 +166,20 @@ toposzp_status toposzp_compress_noalloc(const float* field, int ndim, const uint
 /* Host.  Largest field (points) toposzp_compress_noalloc accepts. */
 uint64_t toposzp_noalloc_max_points(void);
 
+/* Host.  Launch geometry chosen by the autotuner (no counterpart in the
+ * paper; no effect on any output bit).  Process-wide, not thread-safe; zero
+ * fields keep the defaults.  Returns INVALID_ARG for unsupported values.
+ *   cd_threads           threads per CTA of the range + CD pass: 128, 256, 512
+ *   cd_blocks_per_sm     its CTAs per SM: 1..32 (default 8)
+ *   rounds_blocks_per_sm CTAs per SM of the cooperative saddle rounds: 1..4
+ *                        (default: as many as fit, at most 4) */
+typedef struct {
+    int32_t cd_threads;
+    int32_t cd_blocks_per_sm;
+    int32_t rounds_blocks_per_sm;
+} toposzp_tuning;
+toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
+
 /* Host.  Profiling hook (no counterpart in the paper).  After a call with
  * count > 0, every toposzp_compress records events[0..4] (cudaEvent_t handles
  * owned by the caller) on its stream: before the range + CD kernel, after it,

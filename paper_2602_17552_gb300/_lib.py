@@ -32,6 +32,11 @@ class Params(ctypes.Structure):
                 ("rbf_k", ctypes.c_int32), ("rbf_sigma", ctypes.c_float)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("cd_threads", ctypes.c_int32), ("cd_blocks_per_sm", ctypes.c_int32),
+                ("rounds_blocks_per_sm", ctypes.c_int32)]
+
+
 class Info(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_uint64 * 3), ("n", ctypes.c_uint64),
                 ("total_size", ctypes.c_uint64), ("eps", ctypes.c_double), ("flags", ctypes.c_uint32),
@@ -42,7 +47,7 @@ class Info(ctypes.Structure):
 EXPORTS = ("toposzp_default_params", "toposzp_status_string", "toposzp_compress_bound",
            "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size", "toposzp_compress",
            "toposzp_inspect", "toposzp_decompress", "toposzp_critical_points", "toposzp_topo_errors",
-           "toposzp_set_stage_events", "toposzp_compress_noalloc", "toposzp_noalloc_max_points")
+           "toposzp_set_stage_events", "toposzp_compress_noalloc", "toposzp_noalloc_max_points", "toposzp_set_tuning")
 
 _lib = None
 
@@ -81,6 +86,8 @@ def load() -> ctypes.CDLL:
     L.toposzp_compress_noalloc.argtypes = [vp, c_int, dims_t, c_int, ctypes.c_double, ctypes.POINTER(Params),
                                            vp, u64, vp, i32p, vp]
     L.toposzp_compress_noalloc.restype = c_int
+    L.toposzp_set_tuning.argtypes = [ctypes.POINTER(Tuning)]
+    L.toposzp_set_tuning.restype = c_int
     L.toposzp_noalloc_max_points.argtypes = []
     L.toposzp_noalloc_max_points.restype = u64
     _lib = L

@@ -12,6 +12,8 @@
 
 namespace tsz {
 
+Tuning g_tuning;
+
 constexpr uint64_t a256(uint64_t x) { return (x + 255) & ~uint64_t(255); }
 
 constexpr uint64_t CTRL_BYTES = 4096;
@@ -331,6 +333,20 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
     if (e != cudaSuccess) return TOPOSZP_ERR_CUDA;
     stage(8, st);
     return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;
+}
+
+toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
+    if (!t) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->cd_threads && t->cd_threads != 128 && t->cd_threads != 256 && t->cd_threads != 512)
+        return TOPOSZP_ERR_INVALID_ARG;
+    if (t->cd_blocks_per_sm < 0 || t->cd_blocks_per_sm > 32) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->rounds_blocks_per_sm < 0 || t->rounds_blocks_per_sm > 4) return TOPOSZP_ERR_INVALID_ARG;
+    Tuning u;
+    if (t->cd_threads) u.cd_threads = t->cd_threads;
+    if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
+    u.rounds_blocks_per_sm = t->rounds_blocks_per_sm;
+    g_tuning = u;
+    return TOPOSZP_OK;
 }
 
 toposzp_status toposzp_set_stage_events(void* const* events, int count) {

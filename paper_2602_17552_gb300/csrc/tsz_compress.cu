@@ -126,7 +126,7 @@ __device__ __forceinline__ uint32_t cd_fast(float v, float l, float r, bool xl, 
 }
 
 template <bool TOPO, bool COUNTS, bool STATS>
-__global__ void __launch_bounds__(256) k_range_cd_vec(const float* __restrict__ a, const Geo g, Ctrl* c,
+__global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ a, const Geo g, Ctrl* c,
                                                       uint32_t* __restrict__ labels,
                                                       unsigned long long* counts) {
     const int lane = threadIdx.x & 31;
@@ -952,9 +952,12 @@ static bool vec_ok(const float* a, const Geo& g) {
 void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bool topo, int sms,
                      cudaStream_t st) {
     if (vec_ok(a, g)) {
-        uint32_t blocks = hmin<uint32_t>((g.n / 128 + 7) / 8 + 1, (uint32_t)sms * 8);
-        if (topo) k_range_cd_vec<true, false, true><<<blocks, 256, 0, st>>>(a, g, c, labels, nullptr);
-        else k_range_cd_vec<false, false, true><<<blocks, 256, 0, st>>>(a, g, c, labels, nullptr);
+        const int th = g_tuning.cd_threads;
+        const uint32_t per_cta_chunks = (uint32_t)th / 32;   // one 128-point chunk per warp
+        uint32_t blocks = hmin<uint32_t>((g.n / 128 + per_cta_chunks - 1) / per_cta_chunks + 1,
+                                         (uint32_t)sms * (uint32_t)g_tuning.cd_blocks_per_sm);
+        if (topo) k_range_cd_vec<true, false, true><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
+        else k_range_cd_vec<false, false, true><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
         return;
     }
     uint32_t nchunks = (g.n + 511) / 512;

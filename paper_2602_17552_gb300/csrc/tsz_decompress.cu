@@ -881,13 +881,15 @@ void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned 
 
 cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, uint32_t* sadb,
                                  float* sadv, uint32_t sad_cap, int sms, int* status, cudaStream_t st) {
-    static int per_sm = -1;
-    if (per_sm < 0) {
+    static int fit = -1;
+    if (fit < 0) {
         int b = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_saddle_rounds, 256, 0) != cudaSuccess || b < 1)
             b = 1;
-        per_sm = b < 4 ? b : 4;
+        fit = b;
     }
+    int per_sm = g_tuning.rounds_blocks_per_sm > 0 ? g_tuning.rounds_blocks_per_sm : 4;
+    if (per_sm > fit) per_sm = fit;   // a cooperative grid must be co-resident
     void* args[] = {(void*)&in, (void*)&c, (void*)&out, (void*)&sad, (void*)&sadb, (void*)&sadv,
                     (void*)&sad_cap, (void*)&status};
     return cudaLaunchCooperativeKernel((const void*)k_saddle_rounds, dim3(per_sm * sms), dim3(256), args, 0, st);

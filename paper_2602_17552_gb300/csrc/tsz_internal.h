@@ -8,6 +8,14 @@ namespace tsz {
 constexpr int SORT_TILE = 2048;   // keys per sort step of one CTA
 constexpr int RANK_TILE = 2048;   // entries per dense-rank tile
 
+// ---- launch geometry (set by toposzp_set_tuning; never changes results)
+struct Tuning {
+    int cd_threads = 256;
+    int cd_blocks_per_sm = 8;
+    int rounds_blocks_per_sm = 0;   // 0: occupancy, capped at 4
+};
+extern Tuning g_tuning;
+
 // ---- workspace carving (all offsets 256-byte aligned)
 struct CompressWs {
     uint64_t ctrl, desc, rdesc, listM, listm, tmpM, tmpm, hist, agg, delta, end;

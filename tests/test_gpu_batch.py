@@ -48,3 +48,19 @@ def test_batch_no_topo_and_abs():
         want = codec.compress(f, 1e-2, "abs", no_topo=True)
         assert torch.equal(s, want)
         assert torch.equal(it.dec, codec.decompress(want, tuple(f.shape)))
+
+
+def test_launch_tuning_never_changes_bits():
+    from paper_2602_17552_gb300 import autotune
+    f3 = synth.turbulence_3d(40, seed=6, device="cuda")
+    f2 = synth.climate_2d(300, 640, seed=6, device="cuda")
+    want = [codec.compress(f, 1e-3, "rel") for f in (f3, f2)]
+    try:
+        for th, bps, rb in ((128, 4, 1), (512, 16, 2), (256, 32, 4)):
+            autotune.apply({"cd_threads": th, "cd_blocks_per_sm": bps, "rounds_blocks_per_sm": rb})
+            for f, w in zip((f3, f2), want):
+                got = codec.compress(f, 1e-3, "rel")
+                assert torch.equal(got, w)
+                assert torch.equal(codec.decompress(got, tuple(f.shape)), codec.decompress(w, tuple(f.shape)))
+    finally:
+        autotune.apply(autotune.DEFAULT)
