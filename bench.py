@@ -319,8 +319,9 @@ def run_ours(args):
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
     nbytes_all = 4 * n * ws_n
     value = nbytes_all * args.steps / (total_ms * 1e-3) / 1e9
-    launches_c = 22 if topo else 5
-    launches_d = 4
+    # kernels per call (tsz_api.cu launch sequences)
+    launches_c = 16 if topo else 5
+    launches_d = 6
     result = {
         "metric": "compress+decompress throughput (uncompressed bytes / round-trip time)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": ws_n, "steps": args.steps,

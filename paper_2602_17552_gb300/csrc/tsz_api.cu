@@ -55,15 +55,20 @@ constexpr CompressWs compress_ws_c(uint64_t n) {
     w.ntiles = (uint32_t)cdiv(nb, TILE_BLOCKS);
     w.rank_tiles = (uint32_t)cdiv(cdiv(n + 2, L), TILE_BLOCKS) + 1;
     w.agg_stride = (uint32_t)cdiv(w.list_cap, RANK_TILE) + 1;
+    w.os_tiles = (uint32_t)cdiv(w.list_cap, 4096);
+    w.os_stride = w.os_tiles * 256u;
     uint64_t o = 0;
     w.ctrl = o; o = a256(o + CTRL_BYTES);
     w.desc = o; o = a256(o + 16ull * (w.ntiles + 1));
     w.rdesc = o; o = a256(o + 16ull * (w.rank_tiles + 1));
+    w.os_small = o; o = a256(o + 4ull * (2 * 4 * 256) * 2 + 4ull * 8);   // histograms, bases, counters
+    // end of the region zeroed at the start of every call
+    w.os_desc_a = o; o = a256(o + 4ull * 2 * w.os_stride);
+    w.os_desc_b = o; o = a256(o + 4ull * 2 * w.os_stride);
     w.listM = o; o = a256(o + 8ull * w.list_cap);
     w.listm = o; o = a256(o + 8ull * w.list_cap);
     w.tmpM = o; o = a256(o + 8ull * w.list_cap);
     w.tmpm = o; o = a256(o + 8ull * w.list_cap);
-    w.hist = o; o = a256(o + 4ull * 2 * 256 * SORT_G);
     w.agg = o; o = a256(o + 8ull * 2 * w.agg_stride);
     w.delta = o; o = a256(o + 4ull * (n + 2));
     w.end = o;
@@ -232,7 +237,7 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     uint32_t* labels = reinterpret_cast<uint32_t*>(o + lo.s6);
 
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
-    cudaMemsetAsync(ws, 0, w.listM, st);   // control block and both look-back descriptor arrays
+    cudaMemsetAsync(ws, 0, w.os_desc_a, st);   // control block, look-back descriptors, sort counters
     k_init_ctrl<<<1, 1, 0, st>>>(c, g, mode == TOPOSZP_EB_REL ? 1 : 0, eb, p.flags, (int)p.rs_sweeps);
     stage(0, st);
     launch_range_cd(field, g, c, labels, topo, sms, st);
@@ -241,10 +246,17 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     launch_encode_field(field, labels, c, desc, o, lo, listM, listm, topo, g.nb, sms, status, st);
     stage(2, st);
     if (topo) {
+        SortWs sw;
+        sw.hist = reinterpret_cast<uint32_t*>(ws + w.os_small);
+        sw.base = sw.hist + 2 * 4 * 256;
+        sw.ctr = sw.base + 2 * 4 * 256;
+        sw.desc_a = reinterpret_cast<uint32_t*>(ws + w.os_desc_a);
+        sw.desc_b = reinterpret_cast<uint32_t*>(ws + w.os_desc_b);
+        sw.stride = w.os_stride;
+        sw.max_tiles = w.os_tiles;
         launch_ranks(c, listM, listm, reinterpret_cast<uint2*>(ws + w.tmpM),
-                     reinterpret_cast<uint2*>(ws + w.tmpm), reinterpret_cast<uint32_t*>(ws + w.hist),
-                     reinterpret_cast<uint2*>(ws + w.agg), w.agg_stride,
-                     reinterpret_cast<int32_t*>(ws + w.delta), w.G, status, st);
+                     reinterpret_cast<uint2*>(ws + w.tmpm), sw, reinterpret_cast<uint2*>(ws + w.agg),
+                     w.agg_stride, reinterpret_cast<int32_t*>(ws + w.delta), w.G, sms, status, st);
         launch_encode_ranks(reinterpret_cast<int32_t*>(ws + w.delta), c, rdesc, o, w.rank_tiles, sms,
                             status, st);
         launch_count_saddles(labels, c, g.n, sms, status, st);

@@ -585,122 +585,171 @@ __global__ void __launch_bounds__(256) k_encode_ranks(const int32_t* __restrict_
 
 // ================================================================ rank sort
 //
-// LSD radix sort of (key, position) pairs, 8-bit digits, stable.  Both lists
-// (maxima: key = ord(v); minima: key = ~ord(v)) are sorted in the same
-// launches (blockIdx.y selects the list).  Each CTA owns one contiguous range of
-// the list; per-CTA digit histograms are scanned digit-major, so the scatter
-// keeps the input order within a digit.
+// LSD radix sort of (key, position) pairs, 8-bit digits, stable, after the
+// "onesweep" scheme: one pass builds the digit histograms of all four passes;
+// then every pass is a single kernel over tiles of 4096 keys.  A tile ranks its
+// keys per digit with warp match masks (stable: keys keep their input order
+// within a digit), publishes its per-digit counts, and finds its global offset
+// per digit with a decoupled look-back over the earlier tiles (one thread per
+// digit).  Both lists (maxima: key = ord(v); minima: key = ~ord(v)) are sorted
+// by the same launches (blockIdx.y selects the list).
 
-__device__ __forceinline__ void list_range(uint32_t k, int G, uint32_t& beg, uint32_t& end) {
-    uint32_t chunk = (uint32_t)cdiv(cdiv(k, (uint64_t)G), SORT_TILE) * SORT_TILE;
-    beg = min(k, blockIdx.x * chunk);
-    end = min(k, beg + chunk);
+constexpr int OS_WARPS = 8;
+constexpr int OS_ITEMS = 16;                       // keys per lane
+constexpr int OS_TILE = OS_WARPS * 32 * OS_ITEMS;  // 4096
+constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_MASK = (1u << 30) - 1;
+
+__device__ __forceinline__ uint32_t list_count(const Ctrl* c, int list) {
+    return list ? c->cnt_min : c->cnt_max;
 }
 
-__global__ void __launch_bounds__(256) k_sort_hist(const uint2* src0, const uint2* src1, const Ctrl* c,
-                                                   uint32_t* hist, int shift, int G, const int* status) {
-    __shared__ uint32_t h[256];
+// All four digit histograms of both lists, and zeroed look-back descriptors
+// for the tiles the passes will use.
+__global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s1, const Ctrl* c,
+                                                 uint32_t* ghist /* [2][4][256] */, uint32_t* desc_a,
+                                                 uint32_t* desc_b, uint32_t desc_stride, const int* status) {
+    __shared__ uint32_t h[4][256];
     if (*status) return;
     const int list = blockIdx.y;
-    const uint2* src = list ? src1 : src0;
-    const uint32_t k = list ? c->cnt_min : c->cnt_max;
-    h[threadIdx.x] = 0;
+    const uint2* s = list ? s1 : s0;
+    const uint32_t k = list_count(c, list);
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    uint32_t beg, end;
-    list_range(k, G, beg, end);
-    for (uint32_t i = beg + threadIdx.x; i < end; i += blockDim.x)
-        atomicAdd(&h[(src[i].x >> shift) & 0xFFu], 1u);
-    __syncthreads();
-    hist[(size_t)list * 256 * G + (size_t)threadIdx.x * G + blockIdx.x] = h[threadIdx.x];
-}
-
-// exclusive scan of 256 * G counters per list (one CTA per list)
-__global__ void __launch_bounds__(1024) k_sort_scan(uint32_t* hist, int G, const int* status) {
-    __shared__ uint32_t part[1024];
-    if (*status) return;
-    uint32_t* hst = hist + (size_t)blockIdx.x * 256 * G;
-    const uint32_t total = 256u * G;
-    const uint32_t per = (total + 1023) / 1024;
-    const uint32_t b = threadIdx.x * per, e = min(total, b + per);
-    uint32_t s = 0;
-#pragma unroll 16
-    for (uint32_t i = b; i < e; i++) s += hst[i];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        uint32_t t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += t;
-        __syncthreads();
-    }
-    uint32_t run = part[threadIdx.x] - s;
-#pragma unroll 16
-    for (uint32_t i = b; i < e; i++) {
-        uint32_t v = hst[i];
-        hst[i] = run;
-        run += v;
-    }
-}
-
-// Scatter: a tile of 2048 keys is split into 8 warp slices of 256; each warp
-// counts its digits, a per-digit scan over the warps gives every warp its own
-// running offsets, then each warp places its keys in order (match_any gives the
-// rank among equal digits inside a 32-key step).
-__global__ void __launch_bounds__(256) k_sort_scatter(const uint2* src0, const uint2* src1, uint2* dst0,
-                                                      uint2* dst1, const Ctrl* c, const uint32_t* hist,
-                                                      int shift, int G, const int* status) {
-    __shared__ uint32_t run[256];
-    __shared__ uint32_t wcnt[TILE_WARPS][256];
-    if (*status) return;
-    const int list = blockIdx.y;
-    const uint2* src = list ? src1 : src0;
-    uint2* dst = list ? dst1 : dst0;
-    const uint32_t k = list ? c->cnt_min : c->cnt_max;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t beg, end;
-    list_range(k, G, beg, end);
-    run[threadIdx.x] = hist[(size_t)list * 256 * G + (size_t)threadIdx.x * G + blockIdx.x];
     const uint32_t lt = lanemask_lt();
-    for (uint32_t t0 = beg; t0 < end; t0 += SORT_TILE) {
-        for (int d = 0; d < TILE_WARPS; d++) wcnt[d][threadIdx.x] = 0;
-        __syncthreads();
-        uint2 e[SORT_TILE / 256];
-        uint32_t dg[SORT_TILE / 256];
-        const uint32_t ws = t0 + warp * (SORT_TILE / TILE_WARPS);
+    for (uint32_t base = blockIdx.x * blockDim.x; base < k; base += gridDim.x * blockDim.x) {
+        const uint32_t i = base + threadIdx.x;
+        const bool ok = i < k;
+        const uint32_t key = ok ? s[i].x : 0u;
 #pragma unroll
-        for (int r = 0; r < SORT_TILE / 256; r++) {
-            uint32_t p = ws + r * 32 + lane;
-            bool ok = p < end;
-            e[r] = ok ? src[p] : make_uint2(0, 0);
-            dg[r] = ok ? ((e[r].x >> shift) & 0xFFu) : 256u + lane;
-            uint32_t peers = __match_any_sync(FULL, dg[r]);
-            if (ok && (peers & lt) == 0) wcnt[warp][dg[r]] += __popc(peers);
+        for (int p = 0; p < 4; p++) {
+            const uint32_t d = ok ? (key >> (8 * p)) & 0xFFu : 256u + (threadIdx.x & 31);
+            const uint32_t peers = __match_any_sync(FULL, d);
+            if (ok && (peers & lt) == 0) atomicAdd(&h[p][d], __popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
+        const uint32_t v = (&h[0][0])[i];
+        if (v) atomicAdd(&ghist[list * 1024 + i], v);
+    }
+    // zero the descriptors of the tiles in use (both alternating buffers)
+    const uint32_t words = (uint32_t)cdiv(k, OS_TILE) * 256u;
+    uint32_t* da = desc_a + (size_t)list * desc_stride;
+    uint32_t* db = desc_b + (size_t)list * desc_stride;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x) {
+        da[i] = 0u;
+        db[i] = 0u;
+    }
+}
+
+// exclusive scan of each 256-digit histogram -> digit bases
+__global__ void k_os_bases(const uint32_t* ghist, uint32_t* base, const int* status) {
+    if (*status) return;
+    const int row = blockIdx.x;   // list * 4 + pass
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int d = 0; d < 256; d++) {
+            base[row * 256 + d] = run;
+            run += ghist[row * 256 + d];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_os_pass(const uint2* s0, const uint2* s1, uint2* d0, uint2* d1,
+                                                 const Ctrl* c, const uint32_t* base, uint32_t* desc,
+                                                 uint32_t* desc_next, uint32_t desc_stride, uint32_t* tile_ctr,
+                                                 int pass, int* status) {
+    __shared__ uint32_t s_tile;
+    __shared__ uint16_t wcnt[OS_WARPS][256];
+    __shared__ uint32_t gofs[256];
+    if (*status) return;
+    const int list = blockIdx.y;
+    const uint2* src = list ? s1 : s0;
+    uint2* dst = list ? d1 : d0;
+    const uint32_t k = list_count(c, list);
+    const uint32_t ntiles = (uint32_t)cdiv(k, OS_TILE);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int shift = 8 * pass;
+    uint32_t* dsc = desc + (size_t)list * desc_stride;
+    const uint32_t lt = lanemask_lt();
+    while (true) {
+        if (threadIdx.x == 0) s_tile = atomicAdd(&tile_ctr[list], 1u);
+        for (int i = threadIdx.x; i < OS_WARPS * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        __syncthreads();
+        const uint32_t t = s_tile;
+        if (t >= ntiles) break;
+        // load: warp w owns keys [t*4096 + w*512, +512), lane-striped (coalesced)
+        const uint32_t wbase = t * OS_TILE + warp * 32 * OS_ITEMS;
+        uint2 e[OS_ITEMS];
+        uint32_t dg[OS_ITEMS];
+        uint32_t rk[OS_ITEMS];
+#pragma unroll
+        for (int j = 0; j < OS_ITEMS; j++) {
+            const uint32_t p = wbase + j * 32 + lane;
+            const bool ok = p < k;
+            e[j] = ok ? src[p] : make_uint2(0u, 0u);
+            dg[j] = ok ? (e[j].x >> shift) & 0xFFu : 256u + lane;
+        }
+        // stable local ranks inside the warp, in (j, lane) order
+#pragma unroll
+        for (int j = 0; j < OS_ITEMS; j++) {
+            const uint32_t peers = __match_any_sync(FULL, dg[j]);
+            const int leader = __ffs(peers) - 1;
+            uint32_t b = 0;
+            if (dg[j] < 256u && lane == leader) b = wcnt[warp][dg[j]];
+            b = __shfl_sync(FULL, b, leader);
+            rk[j] = b + __popc(peers & lt);
+            __syncwarp();
+            if (dg[j] < 256u && lane == leader) wcnt[warp][dg[j]] = (uint16_t)(b + __popc(peers));
             __syncwarp();
         }
         __syncthreads();
-        {   // per digit: exclusive over warps, then advance the CTA running offset
-            uint32_t s = run[threadIdx.x];
+        // per digit (thread d): offsets of the warps, tile count, look-back
+        {
+            const int d = threadIdx.x;
+            uint32_t run = 0;
 #pragma unroll
-            for (int w = 0; w < TILE_WARPS; w++) {
-                uint32_t v = wcnt[w][threadIdx.x];
-                wcnt[w][threadIdx.x] = s;
-                s += v;
+            for (int w = 0; w < OS_WARPS; w++) {
+                const uint32_t v = wcnt[w][d];
+                wcnt[w][d] = (uint16_t)run;
+                run += v;
             }
-            run[threadIdx.x] = s;
+            const uint32_t tot = run;
+            uint32_t pre = 0;
+            volatile uint32_t* vd = dsc;
+            if (t == 0) {
+                vd[d] = OS_INC | tot;
+            } else {
+                vd[(size_t)t * 256 + d] = OS_AGG | tot;
+                long long j = (long long)t - 1;
+                uint32_t spins = 0;
+                while (j >= 0) {
+                    const uint32_t v = vd[(size_t)j * 256 + d];
+                    if (v & OS_INC) {
+                        pre += v & OS_MASK;
+                        break;
+                    }
+                    if (v & OS_AGG) {
+                        pre += v & OS_MASK;
+                        j--;
+                        continue;
+                    }
+                    if (++spins > SPIN_LIMIT) {
+                        set_status(status, ST_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                vd[(size_t)t * 256 + d] = OS_INC | (pre + tot);
+            }
+            gofs[d] = base[(list * 4 + pass) * 256 + d] + pre;
+            // the next pass uses the other buffer: clear this tile's entry there
+            desc_next[(size_t)list * desc_stride + (size_t)t * 256 + d] = 0u;
         }
         __syncthreads();
 #pragma unroll
-        for (int r = 0; r < SORT_TILE / 256; r++) {
-            uint32_t p = ws + r * 32 + lane;
-            bool ok = p < end;
-            uint32_t peers = __match_any_sync(FULL, dg[r]);
-            if (ok) {
-                uint32_t base = wcnt[warp][dg[r]];
-                dst[base + __popc(peers & lt)] = e[r];
-            }
-            __syncwarp();
-            if (ok && (peers & lt) == 0) wcnt[warp][dg[r]] += __popc(peers);
-            __syncwarp();
+        for (int j = 0; j < OS_ITEMS; j++) {
+            if (dg[j] < 256u) dst[gofs[dg[j]] + wcnt[warp][dg[j]] + rk[j]] = e[j];
         }
         __syncthreads();
     }
@@ -1037,19 +1086,25 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, Desc* 
     else k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
 }
 
-void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint32_t* hist,
-                  uint2* agg, uint32_t agg_stride, int32_t* delta, int G, int* status, cudaStream_t st) {
-    dim3 grid(G, 2);
+void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, const SortWs& sw,
+                  uint2* agg, uint32_t agg_stride, int32_t* delta, int G, int sms, int* status, cudaStream_t st) {
+    const uint32_t max_tiles = sw.max_tiles;
+    uint32_t hg = hmin<uint32_t>((uint32_t)cdiv((uint64_t)max_tiles * OS_TILE, 256), (uint32_t)sms * 4);
+    if (hg == 0) hg = 1;
+    k_os_hist<<<dim3(hg, 2), 256, 0, st>>>(listM, listm, c, sw.hist, sw.desc_a, sw.desc_b, sw.stride, status);
+    k_os_bases<<<8, 32, 0, st>>>(sw.hist, sw.base, status);
     uint2 *a0 = listM, *a1 = listm, *b0 = tmpM, *b1 = tmpm;
+    const uint32_t pg = hmin<uint32_t>(max_tiles, (uint32_t)sms * 4);
     for (int pass = 0; pass < 4; pass++) {
-        int shift = 8 * pass;
-        k_sort_hist<<<grid, 256, 0, st>>>(a0, a1, c, hist, shift, G, status);
-        k_sort_scan<<<2, 1024, 0, st>>>(hist, G, status);
-        k_sort_scatter<<<grid, 256, 0, st>>>(a0, a1, b0, b1, c, hist, shift, G, status);
+        uint32_t* cur = (pass & 1) ? sw.desc_b : sw.desc_a;
+        uint32_t* nxt = (pass & 1) ? sw.desc_a : sw.desc_b;
+        k_os_pass<<<dim3(pg ? pg : 1, 2), 256, 0, st>>>(a0, a1, b0, b1, c, sw.base, cur, nxt, sw.stride,
+                                                         sw.ctr + 2 * pass, pass, status);
         uint2* t0 = a0; a0 = b0; b0 = t0;
         uint2* t1 = a1; a1 = b1; b1 = t1;
     }
     // after 4 passes the sorted data is back in listM / listm
+    dim3 grid(G, 2);
     k_rank_tiles<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, G, status);
     k_rank_scan<<<2, 256, 0, st>>>(agg, agg_stride, c, status);
     k_rank_scatter<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, delta, G, status);

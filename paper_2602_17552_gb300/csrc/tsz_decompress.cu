@@ -388,7 +388,9 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
     if (corrupt) set_status(status, ST_CORRUPT);
 }
 
-// exclusive scans of the tile sums (one CTA); totals must match the header
+// exclusive scans of the tile sums (one CTA); totals must match the header.
+// Each thread owns a contiguous run of tiles and reads it in unrolled groups of
+// 16 independent loads.
 __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t* tile_w, const uint32_t* tile_c,
                                                         unsigned long long* pay_pre, uint32_t* cp_pre, int* status) {
     __shared__ unsigned long long sw[1024];
@@ -398,9 +400,18 @@ __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t*
     const uint32_t per = (ntiles + 1023) / 1024;
     const uint32_t b = threadIdx.x * per, e = hmin<uint32_t>(ntiles, b + per);
     unsigned long long aw = 0, ac = 0;
-    for (uint32_t i = b; i < e; i++) {
-        aw += tile_w[i];
-        ac += tile_c[i];
+    for (uint32_t i0 = b; i0 < e; i0 += 16) {
+        uint32_t vw[16], vc[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            vw[j] = i0 + j < e ? tile_w[i0 + j] : 0u;
+            vc[j] = i0 + j < e ? tile_c[i0 + j] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            aw += vw[j];
+            ac += vc[j];
+        }
     }
     sw[threadIdx.x] = aw;
     sc[threadIdx.x] = ac;
@@ -414,11 +425,22 @@ __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t*
         __syncthreads();
     }
     unsigned long long rw = sw[threadIdx.x] - aw, rc = sc[threadIdx.x] - ac;
-    for (uint32_t i = b; i < e; i++) {
-        pay_pre[i] = rw;
-        cp_pre[i] = (uint32_t)rc;
-        rw += tile_w[i];
-        rc += tile_c[i];
+    for (uint32_t i0 = b; i0 < e; i0 += 16) {
+        uint32_t vw[16], vc[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            vw[j] = i0 + j < e ? tile_w[i0 + j] : 0u;
+            vc[j] = i0 + j < e ? tile_c[i0 + j] : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            if (i0 + j < e) {
+                pay_pre[i0 + j] = rw;
+                cp_pre[i0 + j] = (uint32_t)rc;
+            }
+            rw += vw[j];
+            rc += vc[j];
+        }
     }
     if (threadIdx.x == 1023) {
         pay_pre[ntiles] = sw[1023];

@@ -5,7 +5,6 @@
 
 namespace tsz {
 
-constexpr int SORT_TILE = 2048;   // keys per sort step of one CTA
 constexpr int RANK_TILE = 2048;   // entries per dense-rank tile
 
 // ---- launch geometry (set by toposzp_set_tuning; never changes results)
@@ -18,9 +17,15 @@ extern Tuning g_tuning;
 
 // ---- workspace carving (all offsets 256-byte aligned)
 struct CompressWs {
-    uint64_t ctrl, desc, rdesc, listM, listm, tmpM, tmpm, hist, agg, delta, end;
-    uint32_t list_cap, ntiles, rank_tiles, agg_stride;
+    uint64_t ctrl, desc, rdesc, os_small, os_desc_a, os_desc_b, listM, listm, tmpM, tmpm, agg, delta, end;
+    uint32_t list_cap, ntiles, rank_tiles, agg_stride, os_tiles, os_stride;
     int G;
+};
+// pointers of the radix sort's workspace (histograms, digit bases, tile
+// counters in the zeroed control region; two look-back descriptor buffers)
+struct SortWs {
+    uint32_t *hist, *base, *ctr, *desc_a, *desc_b;
+    uint32_t stride, max_tiles;
 };
 struct DecompressWs {
     uint64_t ctrl, rdesc, flags, tile_w, tile_c, pay_pre, cp_pre, cp_idx, delta, newv, sad, sadv, end;
@@ -38,8 +43,8 @@ void launch_qparams(Ctrl* c, int* status, cudaStream_t st);
 void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, Desc* desc, uint8_t* out,
                          const Layout& lo, uint2* listM, uint2* listm, bool topo, uint32_t nb, int sms,
                          int* status, cudaStream_t st);
-void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint32_t* hist,
-                  uint2* agg, uint32_t agg_stride, int32_t* delta, int G, int* status, cudaStream_t st);
+void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, const SortWs& sw,
+                  uint2* agg, uint32_t agg_stride, int32_t* delta, int G, int sms, int* status, cudaStream_t st);
 void launch_encode_ranks(const int32_t* delta, Ctrl* c, Desc* desc, uint8_t* out, uint32_t max_tiles,
                          int sms, int* status, cudaStream_t st);
 void launch_count_saddles(const uint32_t* labels, Ctrl* c, uint32_t n, int sms, int* status,
