@@ -80,7 +80,7 @@ CompressWs compress_ws(uint64_t n) { return compress_ws_c(n); }
 DecompressWs decompress_ws(uint64_t n) {
     DecompressWs w;
     const uint64_t nb = cdiv(n, L);
-    w.ntiles = (uint32_t)cdiv(nb, TILE_BLOCKS);
+    w.ntiles = (uint32_t)cdiv(nb, 256);   // the fused decoder's 8192-point tiles
     w.rank_tiles = (uint32_t)cdiv(cdiv(n + 2, L), TILE_BLOCKS) + 1;
     w.sad_cap = (uint32_t)n;
     uint64_t o = 0;

@@ -22,6 +22,22 @@ namespace cg = cooperative_groups;
 
 namespace tsz {
 
+// Decode tiles of the fused decoder: 256 blocks (8192 points), 8 warps with
+// one block per lane.
+constexpr int DT_WARPS = 8;
+constexpr int DT_BLOCKS = DT_WARPS * 32;
+
+// Label word wi with the codes of points >= n cleared (a valid stream has
+// them zero already; clearing keeps every count consistent on any stream).
+__device__ __forceinline__ uint32_t label_word(const uint32_t* labels, uint32_t wi, uint32_t n) {
+    const uint32_t nwords = (n + 15) / 16;
+    if (wi >= nwords) return 0u;
+    uint32_t w = __ldg(labels + wi);
+    const uint32_t first = wi * 16u;
+    if (first + 16u > n) w &= (1u << (2u * (n - first))) - 1u;
+    return w;
+}
+
 template <class T>
 __device__ __forceinline__ T get(const uint8_t* h, int off) {
     return *reinterpret_cast<const T*>(h + off);
@@ -358,14 +374,14 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
     const bool topo = !(c->flags & FLAG_NO_TOPO);
     const uint8_t* widths = in + lo.s2;
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(in + lo.s6);
-    const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
-    const uint32_t nwords = (g.n + 15) / 16;
+    const uint32_t ntiles = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
     const int lane = threadIdx.x & 31;
     bool corrupt = false;
     for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += (gridDim.x * blockDim.x) >> 5) {
         uint32_t words = 0, cps = 0;
-        for (int j = 0; j < TILE_BLOCKS / 32; j++) {
-            const uint32_t b = t * TILE_BLOCKS + j * 32 + lane;
+#pragma unroll
+        for (int j = 0; j < DT_BLOCKS / 32; j++) {
+            const uint32_t b = t * DT_BLOCKS + j * 32 + lane;
             if (b < g.nb) {
                 uint32_t w = __ldg(widths + b);
                 if (w > 32) { corrupt = true; w = 0; }
@@ -373,10 +389,9 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
             }
         }
         if (topo) {
-            for (int j = 0; j < TILE_BLOCKS * 2 / 32; j++) {
-                const uint32_t wi = t * TILE_BLOCKS * 2 + j * 32 + lane;
-                if (wi < nwords) cps += __popc(__ldg(labels + wi) & 0x55555555u);   // m = 01, M = 11
-            }
+#pragma unroll
+            for (int j = 0; j < DT_BLOCKS * 2 / 32; j++)
+                cps += __popc(label_word(labels, t * DT_BLOCKS * 2 + j * 32 + lane, g.n) & 0x55555555u);
         }
         words = __reduce_add_sync(FULL, words);
         cps = __reduce_add_sync(FULL, cps);
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t*
     __shared__ unsigned long long sw[1024];
     __shared__ unsigned long long sc[1024];
     if (*status) return;
-    const uint32_t ntiles = (c->g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    const uint32_t ntiles = (c->g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
     const uint32_t per = (ntiles + 1023) / 1024;
     const uint32_t b = threadIdx.x * per, e = hmin<uint32_t>(ntiles, b + per);
     unsigned long long aw = 0, ac = 0;
@@ -519,7 +534,7 @@ __device__ __forceinline__ void mark_done(Ctrl* c, uint32_t* flags, int k, uint3
 // boundary, +1 spare), capped at the tile count.
 __host__ __device__ inline uint32_t fused_reach(const Geo& g, uint32_t ntiles) {
     const uint32_t reach = g.ndim == 3 ? g.nxy : g.nx;
-    const uint32_t h = reach / (TILE_BLOCKS * L) + 2;
+    const uint32_t h = reach / (DT_BLOCKS * L) + 2;
     return h < ntiles ? h : ntiles;
 }
 
@@ -551,33 +566,25 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
     // the tile's payload is one contiguous word range: stage it with coalesced loads
     const unsigned long long P0 = A.pay_pre[t], P1 = A.pay_pre[t + 1];
     uint32_t len = 0;
-    if (P1 >= P0 && P1 - P0 <= (unsigned long long)TILE_BLOCKS * 33 && P1 <= A.c->pay_words) len = (uint32_t)(P1 - P0);
+    if (P1 >= P0 && P1 - P0 <= (unsigned long long)DT_BLOCKS * 33 && P1 <= A.c->pay_words) len = (uint32_t)(P1 - P0);
     else corrupt = true;
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_pay[i] = __ldg(pay + P0 + i);
-    const uint32_t blk0 = t * TILE_BLOCKS + warp * BPW;
-    uint32_t my_w = 0;
+    // lane j of a warp holds block blk0 + j: width, first value, its two label words
+    const uint32_t blk0 = t * DT_BLOCKS + warp * 32;
+    const uint32_t mb = blk0 + lane;
+    uint32_t my_w = 0, lw0 = 0, lw1 = 0;
     int32_t my_first = 0;
-    if (lane < BPW && blk0 + lane < g.nb) {
-        my_w = __ldg(widths + blk0 + lane);
-        my_first = __ldg(firsts + blk0 + lane);
+    if (mb < g.nb) {
+        my_w = __ldg(widths + mb);
+        my_first = __ldg(firsts + mb);
         if (my_w > 32) my_w = 0;
-    }
-    const uint32_t ww = __reduce_add_sync(FULL, (lane < BPW && my_w) ? 1u + my_w : 0u);
-    uint32_t mmask[BPW];
-    uint32_t wcp = 0;
-#pragma unroll
-    for (int j = 0; j < BPW; j++) {
-        mmask[j] = 0;
         if (TOPO) {
-            const uint32_t b = blk0 + j;
-            if (b < g.nb) {
-                const uint32_t i = b * 32u + lane;
-                const int lab = i < g.n ? label_at(labels, i) : 0;
-                mmask[j] = __ballot_sync(FULL, lab & 1);
-                wcp += __popc(mmask[j]);
-            }
+            lw0 = label_word(labels, 2 * mb, g.n);
+            lw1 = label_word(labels, 2 * mb + 1, g.n);
         }
     }
+    const uint32_t ww = __reduce_add_sync(FULL, my_w ? 1u + my_w : 0u);
+    const uint32_t wcp = TOPO ? __reduce_add_sync(FULL, __popc(lw0 & 0x55555555u) + __popc(lw1 & 0x55555555u)) : 0u;
     if (lane == 0) {
         s_w[warp] = ww;
         s_cp[warp] = wcp;
@@ -590,8 +597,7 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
         cpoff += s_cp[w];
     }
     const uint32_t lt = lanemask_lt();
-#pragma unroll
-    for (int j = 0; j < BPW; j++) {
+    for (int j = 0; j < 32; j++) {
         const uint32_t b = blk0 + j;
         if (b >= g.nb) break;
         const uint32_t w = __shfl_sync(FULL, my_w, j);
@@ -605,7 +611,9 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
         const uint32_t i = b * 32u + lane;
         if (i < g.n) A.out[i] = dequantize(q, w_f);
         if (TOPO) {
-            const uint32_t mm = mmask[j];
+            const uint32_t w0 = __shfl_sync(FULL, lw0, j), w1 = __shfl_sync(FULL, lw1, j);
+            const uint32_t word = lane < 16 ? w0 : w1;
+            const uint32_t mm = __ballot_sync(FULL, (word >> (2 * (lane & 15))) & 1u);   // m = 01, M = 11
             if ((mm >> lane) & 1u) {
                 const unsigned long long pos = cpoff + __popc(mm & lt);
                 if (pos < k) A.cp_idx[pos] = i;
@@ -690,53 +698,59 @@ __device__ void stage_apply(const FusedArgs& A, const Geo& g, uint32_t s) {
 
 // Saddles of tile s that the extrema stage left lost go to the candidate list.
 __device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t s) {
-    const uint32_t nwords = (g.n + 15) / 16;
-    if (threadIdx.x >= TILE_BLOCKS * 2) return;   // 128 label words per tile: warps 0..3
     const int lane = threadIdx.x & 31;
-    const uint32_t wi = s * TILE_BLOCKS * 2 + threadIdx.x;
-    const uint32_t word = wi < nwords ? __ldg(labels + wi) : 0u;
-    uint32_t smask = ((word >> 1) & ~word) & 0x55555555u;   // code 10
-    uint32_t lost = 0;
     CgVal val{A.out};
-    while (smask) {
-        const int bit = __ffs(smask) - 1;
-        smask &= smask - 1;
-        const uint32_t p = wi * 16u + (uint32_t)(bit >> 1);
-        if (p >= g.n) break;   // padding bits of a damaged stream
-        uint32_t x, y, z;
-        coords(g, p, x, y, z);
-        if (classify_any(val, g, p, x, y, z, val(p)) != LAB_SAD) lost |= 1u << (bit >> 1);
-    }
-    const uint32_t cnt = __popc(lost);
-    uint32_t incl = cnt;
+    for (int part = 0; part < DT_BLOCKS * 2 / (int)blockDim.x; part++) {
+        const uint32_t wi = s * DT_BLOCKS * 2 + part * blockDim.x + threadIdx.x;
+        const uint32_t word = label_word(labels, wi, g.n);
+        uint32_t smask = ((word >> 1) & ~word) & 0x55555555u;   // code 10
+        uint32_t lost = 0;
+        while (smask) {
+            const int bit = __ffs(smask) - 1;
+            smask &= smask - 1;
+            const uint32_t p = wi * 16u + (uint32_t)(bit >> 1);
+            uint32_t x, y, z;
+            coords(g, p, x, y, z);
+            if (classify_any(val, g, p, x, y, z, val(p)) != LAB_SAD) lost |= 1u << (bit >> 1);
+        }
+        const uint32_t cnt = __popc(lost);
+        uint32_t incl = cnt;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t tt = __shfl_up_sync(FULL, incl, o);
-        if (lane >= o) incl += tt;
-    }
-    const uint32_t tot = __shfl_sync(FULL, incl, 31);
-    uint32_t base = 0;
-    if (lane == 31 && tot) base = atomicAdd(&A.c->sad_cnt[0], tot);
-    base = __shfl_sync(FULL, base, 31);
-    uint32_t slot = base + incl - cnt;
-    while (lost) {
-        const int b = __ffs(lost) - 1;
-        lost &= lost - 1;
-        if (slot < A.sad_cap) A.sad[slot] = wi * 16u + (uint32_t)b;
-        slot++;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t tt = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += tt;
+        }
+        const uint32_t tot = __shfl_sync(FULL, incl, 31);
+        uint32_t base = 0;
+        if (lane == 31 && tot) base = atomicAdd(&A.c->sad_cnt[0], tot);
+        base = __shfl_sync(FULL, base, 31);
+        uint32_t slot = base + incl - cnt;
+        while (lost) {
+            const int b = __ffs(lost) - 1;
+            lost &= lost - 1;
+            if (slot < A.sad_cap) A.sad[slot] = wi * 16u + (uint32_t)b;
+            slot++;
+        }
     }
 }
 
+struct FusedSmem {
+    uint32_t pay[DT_BLOCKS * 33];
+    uint32_t tile;
+    uint32_t w[DT_WARPS], cp[DT_WARPS];
+};
+
 template <bool TOPO>
-__device__ void fused_body(const FusedArgs& A) {
-    __shared__ uint32_t s_pay[TILE_BLOCKS * 33];
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_w[TILE_WARPS], s_cp[TILE_WARPS];
+__device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
+    uint32_t* s_pay = S.pay;
+    uint32_t& s_tile = S.tile;
+    uint32_t* s_w = S.w;
+    uint32_t* s_cp = S.cp;
     Ctrl* c = A.c;
     const Geo g = c->g;
     const Layout lo = c->lo;
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
-    const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    const uint32_t ntiles = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
     const uint32_t H = TOPO ? fused_reach(g, ntiles) : 0u;
     const uint32_t total = ntiles + 3 * H;
     bool corrupt = false;
@@ -783,9 +797,10 @@ __device__ void fused_body(const FusedArgs& A) {
 }
 
 __global__ void __launch_bounds__(256, 6) k_decode_fused(FusedArgs A) {
+    __shared__ FusedSmem S;
     if (*A.status) return;
-    if (A.c->flags & FLAG_NO_TOPO) fused_body<false>(A);
-    else fused_body<true>(A);
+    if (A.c->flags & FLAG_NO_TOPO) fused_body<false>(A, S);
+    else fused_body<true>(A, S);
 }
 
 // RS^ colour rounds over the lost-saddle list (cooperative: the grid syncs
