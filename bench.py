@@ -320,7 +320,7 @@ def run_ours(args):
     nbytes_all = 4 * n * ws_n
     value = nbytes_all * args.steps / (total_ms * 1e-3) / 1e9
     # kernels per call (tsz_api.cu launch sequences)
-    launches_c = 16 if topo else 5
+    launches_c = 15 if topo else 5
     launches_d = 6
     result = {
         "metric": "compress+decompress throughput (uncompressed bytes / round-trip time)",

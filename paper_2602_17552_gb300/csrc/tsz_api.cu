@@ -259,7 +259,6 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
                      w.agg_stride, reinterpret_cast<int32_t*>(ws + w.delta), w.G, sms, status, st);
         launch_encode_ranks(reinterpret_cast<int32_t*>(ws + w.delta), c, rdesc, o, w.rank_tiles, sms,
                             status, st);
-        launch_count_saddles(labels, c, g.n, sms, status, st);
     }
     stage(3, st);
     launch_finalize(c, o, out_size, p.rbf_k, p.rbf_sigma, status, st);

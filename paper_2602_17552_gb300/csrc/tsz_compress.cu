@@ -33,6 +33,7 @@ __global__ void __launch_bounds__(256) k_range_cd(const float* __restrict__ a, c
     uint32_t kmin = 0, kmax = 0;   // min as max of ~key
     bool bad = false;
     unsigned long long cm = 0, cs = 0, cM = 0;
+    uint32_t sad_cnt = 0;
     GlobalVal val{a};
     for (uint32_t ch = warp0; ch < nchunks; ch += nwarps) {
         const uint32_t base = ch * 512u;
@@ -68,6 +69,7 @@ __global__ void __launch_bounds__(256) k_range_cd(const float* __restrict__ a, c
             uint32_t wi = ch * 32u + lane;
             if (wi < nwords) {
                 if (labels) labels[wi] = word;
+                if (STATS) sad_cnt += __popc((word >> 1) & ~word & 0x55555555u);
                 if (COUNTS) {
                     uint32_t lo = word & 0x55555555u, hi = (word >> 1) & 0x55555555u;
                     cm += __popc(lo & ~hi);
@@ -81,10 +83,12 @@ __global__ void __launch_bounds__(256) k_range_cd(const float* __restrict__ a, c
     kmax = __reduce_max_sync(FULL, kmax);
     kmin = __reduce_max_sync(FULL, kmin);
     bool anybad = __any_sync(FULL, bad);
+    const uint32_t sad_tot = __reduce_add_sync(FULL, sad_cnt);
     if (STATS && lane == 0) {
         if (kmax) atomicMax(&c->max_key, kmax);
         if (kmin) atomicMax(&c->min_inv, kmin);
         if (anybad) atomicExch(&c->nonfinite, 1u);
+        if (sad_tot) atomicAdd(&c->k_sad, (unsigned long long)sad_tot);
     }
     if (COUNTS) {
 #pragma unroll
@@ -111,15 +115,31 @@ __global__ void __launch_bounds__(256) k_range_cd(const float* __restrict__ a, c
 // rows fall back to the general rule.  Coordinates advance by the grid stride
 // without divisions.
 
+// NaN-propagating minimum / maximum (PTX min.NaN / max.NaN): a comparison
+// against a NaN result is false, exactly as for the strict comparisons of the
+// rule itself, so "both neighbours higher" == (min(a, b) > v) for any input.
+__device__ __forceinline__ float min_nan(float a, float b) {
+    float r;
+    asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float max_nan(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+
 // Section IV-A(1) at a point whose y (and z) pairs exist: per axis, H = both
 // neighbours higher, L = both lower; m = all H, M = all L, s = every axis H or
-// L with at least one of each.  `xl`/`xr` false: that x neighbour is absent.
+// L with at least one of each.  An absent x neighbour is passed as the other
+// one (`xl` / `xr` false), which leaves H and L of the axis to the neighbour
+// that exists and rules out a saddle.
 __device__ __forceinline__ uint32_t cd_fast(float v, float l, float r, bool xl, bool xr, float ym, float yp,
                                             float zm, float zp, bool three) {
-    const bool hl = !xl || l > v, hr = !xr || r > v, ll = !xl || l < v, lr = !xr || r < v;
-    const bool Hx = hl && hr, Lx = ll && lr;
-    const bool Hy = ym > v && yp > v, Ly = ym < v && yp < v;
-    const bool Hz = !three || (zm > v && zp > v), Lz = !three || (zm < v && zp < v);
+    const float a = xl ? l : r, b = xr ? r : l;
+    const bool Hx = min_nan(a, b) > v, Lx = max_nan(a, b) < v;
+    const bool Hy = min_nan(ym, yp) > v, Ly = max_nan(ym, yp) < v;
+    const bool Hz = !three || min_nan(zm, zp) > v, Lz = !three || max_nan(zm, zp) < v;
     const bool m = Hx && Hy && Hz, M = Lx && Ly && Lz;
     const bool s = xl && xr && (Hx || Lx) && (Hy || Ly) && (Hz || Lz) && !m && !M;
     return (uint32_t)(m | M) | ((uint32_t)(s | M) << 1);
@@ -195,6 +215,7 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
             if (active && (lane & 3) == 0) {
                 const uint32_t word = bits | (b1 << 8) | (b2 << 16) | (b3 << 24);
                 if (labels) labels[i0 >> 4] = word;
+                if (STATS) cs += __popc((word >> 1) & ~word & 0x55555555u);
                 if (COUNTS) {
                     const uint32_t lo = word & 0x55555555u, hi = (word >> 1) & 0x55555555u;
                     cm += __popc(lo & ~hi);
@@ -218,10 +239,12 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
         kmax = __reduce_max_sync(FULL, kmax);
         kmin = __reduce_max_sync(FULL, kmin);
         const bool anybad = __any_sync(FULL, bad);
+        const unsigned long long sad = TOPO ? __reduce_add_sync(FULL, (uint32_t)cs) : 0u;
         if (lane == 0) {
             if (kmax) atomicMax(&c->max_key, kmax);
             if (kmin) atomicMax(&c->min_inv, kmin);
             if (anybad) atomicExch(&c->nonfinite, 1u);
+            if (sad) atomicAdd(&c->k_sad, sad);
         }
     }
     if (COUNTS) {
@@ -599,37 +622,49 @@ constexpr int OS_ITEMS = 16;                       // keys per lane
 constexpr int OS_TILE = OS_WARPS * 32 * OS_ITEMS;  // 4096
 constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_MASK = (1u << 30) - 1;
 
+// Lanes of the warp whose 8-bit digit equals this lane's (a match mask built
+// from eight ballots); lanes with ok == false match nobody and nobody them.
+__device__ __forceinline__ uint32_t match_digit8(uint32_t d, bool ok) {
+    uint32_t m = __ballot_sync(FULL, ok);
+#pragma unroll
+    for (int b = 0; b < 8; b++) {
+        const uint32_t v = __ballot_sync(FULL, (d >> b) & 1u);
+        m &= ((d >> b) & 1u) ? v : ~v;
+    }
+    return ok ? m : (1u << (threadIdx.x & 31));
+}
+
 __device__ __forceinline__ uint32_t list_count(const Ctrl* c, int list) {
     return list ? c->cnt_min : c->cnt_max;
 }
 
 // All four digit histograms of both lists, and zeroed look-back descriptors
-// for the tiles the passes will use.
+// for the tiles the passes will use.  Each warp counts into its own slice of
+// shared memory; the slices are summed at the end.
 __global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s1, const Ctrl* c,
                                                  uint32_t* ghist /* [2][4][256] */, uint32_t* desc_a,
                                                  uint32_t* desc_b, uint32_t desc_stride, const int* status) {
-    __shared__ uint32_t h[4][256];
+    __shared__ uint32_t h[8][4 * 256];
     if (*status) return;
     const int list = blockIdx.y;
+    const int warp = threadIdx.x >> 5;
     const uint2* s = list ? s1 : s0;
     const uint32_t k = list_count(c, list);
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < 8 * 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    const uint32_t lt = lanemask_lt();
-    for (uint32_t base = blockIdx.x * blockDim.x; base < k; base += gridDim.x * blockDim.x) {
-        const uint32_t i = base + threadIdx.x;
-        const bool ok = i < k;
-        const uint32_t key = ok ? s[i].x : 0u;
-#pragma unroll
-        for (int p = 0; p < 4; p++) {
-            const uint32_t d = ok ? (key >> (8 * p)) & 0xFFu : 256u + (threadIdx.x & 31);
-            const uint32_t peers = __match_any_sync(FULL, d);
-            if (ok && (peers & lt) == 0) atomicAdd(&h[p][d], __popc(peers));
-        }
+    uint32_t* hw = h[warp];
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        const uint32_t key = s[i].x;
+        atomicAdd(&hw[0 * 256 + (key & 0xFFu)], 1u);
+        atomicAdd(&hw[1 * 256 + ((key >> 8) & 0xFFu)], 1u);
+        atomicAdd(&hw[2 * 256 + ((key >> 16) & 0xFFu)], 1u);
+        atomicAdd(&hw[3 * 256 + (key >> 24)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
-        const uint32_t v = (&h[0][0])[i];
+        uint32_t v = 0;
+#pragma unroll
+        for (int w = 0; w < 8; w++) v += h[w][i];
         if (v) atomicAdd(&ghist[list * 1024 + i], v);
     }
     // zero the descriptors of the tiles in use (both alternating buffers)
@@ -693,7 +728,7 @@ __global__ void __launch_bounds__(256) k_os_pass(const uint2* s0, const uint2* s
         // stable local ranks inside the warp, in (j, lane) order
 #pragma unroll
         for (int j = 0; j < OS_ITEMS; j++) {
-            const uint32_t peers = __match_any_sync(FULL, dg[j]);
+            const uint32_t peers = match_digit8(dg[j], dg[j] < 256u);
             const int leader = __ffs(peers) - 1;
             uint32_t b = 0;
             if (dg[j] < 256u && lane == leader) b = wcnt[warp][dg[j]];
@@ -900,11 +935,35 @@ __device__ __forceinline__ void put(uint8_t* h, int off, T v) {
 // qmin)) over the integer codes (exact, order independent).
 __global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k_over,
                            float rbf_sigma_over, const int* status) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ float s_g[9];
+    __shared__ float s_sigma;
+    __shared__ int32_t s_k;
+    if (blockIdx.x != 0) return;
     if (*status) {
-        *out_size = 0;
+        if (threadIdx.x == 0) *out_size = 0;
         return;
     }
+    if (threadIdx.x == 0) {
+        // adaptive RBF parameters
+        const float r = c->r_f;
+        int64_t qmin = quantize(c->vmin, r), qmax = quantize(c->vmax, r);
+        int64_t span = qmax - qmin;
+        if (span < 1) span = 1;
+        const uint64_t pairs = (uint64_t)c->g.n - c->g.nb;
+        const double V = pairs ? __ddiv_rn((double)c->sum_abs, __dmul_rn((double)pairs, (double)span)) : 0.0;
+        s_sigma = rbf_sigma_over > 0.0f
+                      ? rbf_sigma_over
+                      : __double2float_rn(__dadd_rn(0.5, __dmul_rn(0.5, __dsub_rn(1.0, fmin(1.0, __ddiv_rn(V, 0.05))))));
+        s_k = rbf_k_over > 0 ? rbf_k_over : (V < 0.002 ? 7 : (V < 0.02 ? 5 : 3));
+    }
+    __syncthreads();
+    if (threadIdx.x < 9) {   // one weight per thread: g(d2) for d2 = 1..9
+        const double sg = (double)s_sigma;
+        const int d2 = threadIdx.x + 1;
+        s_g[threadIdx.x] = __double2float_rn(exp_neg(__ddiv_rn((double)d2, __dmul_rn(__dmul_rn(2.0, sg), sg))));
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     const Geo g = c->g;
     const bool topo = !(c->flags & FLAG_NO_TOPO);
     const uint64_t k = topo ? c->k_total : 0;
@@ -922,21 +981,9 @@ __global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rb
         zero_bytes(out, lo.r2 + nbd, lo.r4);
         zero_bytes(out, lo.r4 + 4 * nbd, lo.r5);
     }
-    // RBF parameters
-    const float r = c->r_f;
-    int64_t qmin = quantize(c->vmin, r), qmax = quantize(c->vmax, r);
-    int64_t span = qmax - qmin;
-    if (span < 1) span = 1;
-    uint64_t pairs = (uint64_t)g.n - g.nb;
-    double V = pairs ? __ddiv_rn((double)c->sum_abs, __dmul_rn((double)pairs, (double)span)) : 0.0;
-    float sigma = rbf_sigma_over > 0.0f
-                      ? rbf_sigma_over
-                      : __double2float_rn(__dadd_rn(0.5, __dmul_rn(0.5, __dsub_rn(1.0, fmin(1.0, __ddiv_rn(V, 0.05))))));
-    int32_t kk = rbf_k_over > 0 ? rbf_k_over : (V < 0.002 ? 7 : (V < 0.02 ? 5 : 3));
-    double s = (double)sigma;
-    float gw[9];
-    for (int d2 = 1; d2 <= 9; d2++)
-        gw[d2 - 1] = __double2float_rn(exp_neg(__ddiv_rn((double)d2, __dmul_rn(__dmul_rn(2.0, s), s))));
+    const float sigma = s_sigma;
+    const int32_t kk = s_k;
+    const float* gw = s_g;
     // header
     uint8_t* h = out;
     for (int i = 0; i < (int)HDR; i += 4) put<uint32_t>(h, i, 0u);
