@@ -172,11 +172,15 @@ uint64_t toposzp_noalloc_max_points(void);
  *   cd_threads           threads per CTA of the range + CD pass: 128, 256, 512
  *   cd_blocks_per_sm     its CTAs per SM: 1..32 (default 8)
  *   rounds_blocks_per_sm CTAs per SM of the cooperative saddle rounds: 1..4
- *                        (default: as many as fit, at most 4) */
+ *                        (default: as many as fit, at most 4)
+ *   dec_slack_tiles      extra lag, in 8192-point tiles, between the stages of
+ *                        the fused decoder: 1..65536 (default: a quarter of its
+ *                        resident CTAs) */
 typedef struct {
     int32_t cd_threads;
     int32_t cd_blocks_per_sm;
     int32_t rounds_blocks_per_sm;
+    int32_t dec_slack_tiles;
 } toposzp_tuning;
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
 

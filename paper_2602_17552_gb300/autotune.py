@@ -1,8 +1,8 @@
 """Autotuner for launch geometry.
 
 Sweeps the library's launch knobs (threads per CTA and CTAs per SM of the range
-+ CD pass, CTAs per SM of the cooperative saddle rounds) on a representative
-field, then the number of parallel branches of the batched CUDA graph on a
++ CD pass, CTAs per SM of the cooperative saddle rounds, then the stage slack
+of the fused decoder) on a representative field, then the number of parallel branches of the batched CUDA graph on a
 mixed batch, timing each setting with CUDA events.  The winners are stored as
 JSON and applied with :func:`apply`.  No knob changes an output bit (the tests
 compare streams across settings), so tuning is always safe.
@@ -19,12 +19,13 @@ from . import _lib, batch, codec, synth
 
 CACHE = os.environ.get("TOPOSZP_TUNING", os.path.join(os.path.expanduser("~"), ".cache", "toposzp",
                                                        "tuning.json"))
-DEFAULT = {"cd_threads": 256, "cd_blocks_per_sm": 8, "rounds_blocks_per_sm": 4, "batch_branches": 8}
+DEFAULT = {"cd_threads": 256, "cd_blocks_per_sm": 8, "rounds_blocks_per_sm": 4, "dec_slack_tiles": 0,
+           "batch_branches": 8}
 
 
 def apply(cfg: dict) -> None:
     t = _lib.Tuning(int(cfg.get("cd_threads", 0)), int(cfg.get("cd_blocks_per_sm", 0)),
-                    int(cfg.get("rounds_blocks_per_sm", 0)))
+                    int(cfg.get("rounds_blocks_per_sm", 0)), int(cfg.get("dec_slack_tiles", 0)))
     st = _lib.load().toposzp_set_tuning(t)
     if st:
         raise _lib.TopoSZpError(st, "toposzp_set_tuning")
@@ -69,6 +70,14 @@ def tune(side: int = 256, batch_fields: int = 32, save: bool = True, verbose: bo
             print(cfg, round(t, 3))
         if t < best_t:
             best_t, best = t, {**best, **cfg}
+    for slack in (16, 64, 256, 1024):
+        cfg = {**best, "dec_slack_tiles": slack}
+        apply(cfg)
+        t = _time(step)
+        if verbose:
+            print(cfg, round(t, 3))
+        if t < best_t:
+            best_t, best = t, cfg
     apply(best)
     specs = synth.mixed_batch(count=batch_fields, side2=(128, 2048), side3=(64, 192))
     fields = [s.make("cuda") for s in specs]

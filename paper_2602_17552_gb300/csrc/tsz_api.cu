@@ -352,10 +352,12 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
         return TOPOSZP_ERR_INVALID_ARG;
     if (t->cd_blocks_per_sm < 0 || t->cd_blocks_per_sm > 32) return TOPOSZP_ERR_INVALID_ARG;
     if (t->rounds_blocks_per_sm < 0 || t->rounds_blocks_per_sm > 4) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->dec_slack_tiles < 0 || t->dec_slack_tiles > 65536) return TOPOSZP_ERR_INVALID_ARG;
     Tuning u;
     if (t->cd_threads) u.cd_threads = t->cd_threads;
     if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
     u.rounds_blocks_per_sm = t->rounds_blocks_per_sm;
+    u.dec_slack_tiles = t->dec_slack_tiles;
     g_tuning = u;
     return TOPOSZP_OK;
 }

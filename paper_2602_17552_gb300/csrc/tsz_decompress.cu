@@ -266,6 +266,26 @@ __device__ void build_rbf_table(RbfTable& T, const Geo& g, const Ctrl* c) {
 __device__ __forceinline__ bool higher_after(float u, float fp, bool up) { return u > fp || (u == fp && !up); }
 __device__ __forceinline__ bool lower_after(float u, float fp, bool up) { return u < fp || (u == fp && up); }
 
+// Could some small move of p (up or down) make it a saddle, given its face
+// neighbours nb[0..2*ndim)?  (RS^ check (a) over every admissible step.)
+__device__ __forceinline__ bool saddle_feasible(const float* nb, int ndim, float fp) {
+    bool any = false;
+#pragma unroll
+    for (int up = 0; up < 2; up++) {
+        int ph = 0, pl = 0, px = 0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ax++) {
+            if (ax >= ndim) break;
+            const float a = nb[2 * ax], b = nb[2 * ax + 1];
+            if (higher_after(a, fp, up) && higher_after(b, fp, up)) ph++;
+            else if (lower_after(a, fp, up) && lower_after(b, fp, up)) pl++;
+            else px++;
+        }
+        any |= px == 0 && ph > 0 && pl > 0;
+    }
+    return any;
+}
+
 // RS^ candidate: returns true and the refined value when accepted.  Runs only
 // inside the cooperative rounds kernel, whose grid syncs order every write of
 // the previous colour before these (L1-cached) reads.
@@ -301,18 +321,7 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
     // Exact shortcut: |v - Fp| <= gmin / 2 keeps every distinct neighbour on its
     // side, so p's type with v depends only on the direction of the move; if
     // neither direction gives a saddle, check (a) below rejects every v.
-    bool feasible[2];
-    for (int up = 0; up < 2; up++) {
-        int ph = 0, pl = 0, px = 0;
-        for (int ax = 0; ax < g.ndim; ax++) {
-            const float a = nb[2 * ax], b = nb[2 * ax + 1];
-            if (higher_after(a, Fp, up) && higher_after(b, Fp, up)) ph++;
-            else if (lower_after(a, Fp, up) && lower_after(b, Fp, up)) pl++;
-            else px++;
-        }
-        feasible[up] = px == 0 && ph > 0 && pl > 0;
-    }
-    if (!feasible[0] && !feasible[1]) return false;
+    if (!saddle_feasible(nb, g.ndim, Fp)) return false;
     // normalised Gaussian kernel over N_r(p) \ {p}, fixed (z, y, x) order
     const int r = c->rbf_k / 2;
     const bool inside = x >= (uint32_t)r && x + r < g.nx && y >= (uint32_t)r && y + r < g.ny &&
@@ -550,6 +559,7 @@ struct FusedArgs {
     uint32_t* flags;
     uint32_t* sad;
     uint32_t sad_cap;
+    uint32_t slack;
     int* status;
 };
 
@@ -626,64 +636,80 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
 
 // CP^ + RP^ on one tile's extrema, reading the D0 snapshot (Jacobi).  Each
 // neighbour is loaded once and serves both the lost test and the extreme
-// neighbour value.
+// neighbour value.  Threads take two extrema at a time, all loads first.
+struct ExtIn {
+    float v0, u[6];
+    long long dl;
+    int lab;
+    uint32_t have;   // bit e: neighbour e exists, (x-, x+, y-, y+, z-, z+)
+    bool ok;
+};
+
+__device__ __forceinline__ void ext_load(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t pos,
+                                         ExtIn& e) {
+    const uint32_t p = __ldcg(A.cp_idx + pos);
+    e.ok = p < g.n;   // only a damaged stream fails this (its checks already failed)
+    if (!e.ok) return;
+    const uint32_t st[3] = {1u, g.nx, g.nxy};
+    e.lab = label_at(labels, p);
+    e.dl = __ldg(A.delta + pos);
+    uint32_t x, y, z;
+    coords(g, p, x, y, z);
+    const uint32_t cc[3] = {x, y, z}, dd[3] = {g.nx, g.ny, g.nz};
+    e.v0 = __ldcg(A.out + p);
+    e.have = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ax++) {
+        const bool on = ax < g.ndim;
+        const bool lo = on && cc[ax] > 0, hi = on && cc[ax] + 1 < dd[ax];
+        e.have |= (lo ? 1u : 0u) << (2 * ax) | (hi ? 1u : 0u) << (2 * ax + 1);
+        e.u[2 * ax] = lo ? __ldcg(A.out + p - st[ax]) : 0.0f;
+        e.u[2 * ax + 1] = hi ? __ldcg(A.out + p + st[ax]) : 0.0f;
+    }
+}
+
+__device__ __forceinline__ float ext_eval(const ExtIn& e, float h_f, unsigned long long& restored,
+                                          unsigned long long& skipped) {
+    float nv = __int_as_float(0x7FC00000);
+    if (!e.ok) return nv;
+    // type of p in D0: for a labelled extremum only m / M matter (no FT)
+    int nn = 0, nhi = 0, nlo = 0;
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        if (!((e.have >> k) & 1u)) continue;
+        nn++;
+        nhi += e.u[k] > e.v0;
+        nlo += e.u[k] < e.v0;
+    }
+    const bool kept = nn > 0 && (e.lab == LAB_MIN ? nhi == nn : nlo == nn);
+    if (!kept) {
+        float ext = 0.0f;
+        bool any = false;
+#pragma unroll
+        for (int k = 0; k < 6; k++) {
+            if (!((e.have >> k) & 1u)) continue;
+            if (!any || (e.lab == LAB_MAX ? e.u[k] > ext : e.u[k] < ext)) ext = e.u[k];
+            any = true;
+        }
+        float v;
+        if (any && step_ulps(ext, e.lab == LAB_MAX ? e.dl : -e.dl, v) && fabsf(__fsub_rn(v, e.v0)) <= h_f) {
+            nv = v;
+            restored++;
+        } else {
+            skipped++;
+        }
+    }
+    return nv;
+}
+
 __device__ void stage_extrema(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t s,
                               unsigned long long& restored, unsigned long long& skipped) {
     const uint32_t P0 = A.cp_pre[s], P1 = A.cp_pre[s + 1];
     const float h_f = A.c->h_f;
-    const uint32_t st[3] = {1u, g.nx, g.nxy};
     for (uint32_t pos = P0 + threadIdx.x; pos < P1; pos += blockDim.x) {
-        const uint32_t p = __ldcg(A.cp_idx + pos);
-        float nv = __int_as_float(0x7FC00000);
-        if (p >= g.n) {   // only a damaged stream gets here (its checks already failed)
-            A.newv[pos] = nv;
-            continue;
-        }
-        const int lab = label_at(labels, p);
-        const long long dl = __ldg(A.delta + pos);
-        uint32_t x, y, z;
-        coords(g, p, x, y, z);
-        const uint32_t cc[3] = {x, y, z}, dd[3] = {g.nx, g.ny, g.nz};
-        const float v0 = __ldcg(A.out + p);
-        // neighbours in (x-, x+, y-, y+, z-, z+) order; absent ones flagged
-        float u[6];
-        bool have[6];
-#pragma unroll
-        for (int ax = 0; ax < 3; ax++) {
-            const bool on = ax < g.ndim;
-            have[2 * ax] = on && cc[ax] > 0;
-            have[2 * ax + 1] = on && cc[ax] + 1 < dd[ax];
-            u[2 * ax] = have[2 * ax] ? __ldcg(A.out + p - st[ax]) : 0.0f;
-            u[2 * ax + 1] = have[2 * ax + 1] ? __ldcg(A.out + p + st[ax]) : 0.0f;
-        }
-        // type of p in D0: for a labelled extremum only m / M matter (no FT)
-        int nn = 0, nhi = 0, nlo = 0;
-#pragma unroll
-        for (int e = 0; e < 6; e++) {
-            if (!have[e]) continue;
-            nn++;
-            nhi += u[e] > v0;
-            nlo += u[e] < v0;
-        }
-        const bool kept = nn > 0 && (lab == LAB_MIN ? nhi == nn : nlo == nn);
-        if (!kept) {
-            float ext = 0.0f;
-            bool any = false;
-#pragma unroll
-            for (int e = 0; e < 6; e++) {
-                if (!have[e]) continue;
-                if (!any || (lab == LAB_MAX ? u[e] > ext : u[e] < ext)) ext = u[e];
-                any = true;
-            }
-            float v;
-            if (any && step_ulps(ext, lab == LAB_MAX ? dl : -dl, v) && fabsf(__fsub_rn(v, v0)) <= h_f) {
-                nv = v;
-                restored++;
-            } else {
-                skipped++;
-            }
-        }
-        A.newv[pos] = nv;
+        ExtIn e1;
+        ext_load(A, g, labels, pos, e1);
+        A.newv[pos] = ext_eval(e1, h_f, restored, skipped);
     }
 }
 
@@ -697,23 +723,17 @@ __device__ void stage_apply(const FusedArgs& A, const Geo& g, uint32_t s) {
 }
 
 // Saddles of tile s that the extrema stage left lost go to the candidate list.
-__device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t s) {
+// The tile's saddle labels are first compacted into shared memory, so that
+// each thread then handles about one saddle with all of its loads in flight.
+__device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t s,
+                              uint32_t* s_list, uint32_t& s_cnt) {
     const int lane = threadIdx.x & 31;
-    CgVal val{A.out};
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
     for (int part = 0; part < DT_BLOCKS * 2 / (int)blockDim.x; part++) {
         const uint32_t wi = s * DT_BLOCKS * 2 + part * blockDim.x + threadIdx.x;
-        const uint32_t word = label_word(labels, wi, g.n);
-        uint32_t smask = ((word >> 1) & ~word) & 0x55555555u;   // code 10
-        uint32_t lost = 0;
-        while (smask) {
-            const int bit = __ffs(smask) - 1;
-            smask &= smask - 1;
-            const uint32_t p = wi * 16u + (uint32_t)(bit >> 1);
-            uint32_t x, y, z;
-            coords(g, p, x, y, z);
-            if (classify_any(val, g, p, x, y, z, val(p)) != LAB_SAD) lost |= 1u << (bit >> 1);
-        }
-        const uint32_t cnt = __popc(lost);
+        uint32_t smask = ((label_word(labels, wi, g.n) >> 1) & ~label_word(labels, wi, g.n)) & 0x55555555u;
+        const uint32_t cnt = __popc(smask);
         uint32_t incl = cnt;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -722,21 +742,72 @@ __device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* 
         }
         const uint32_t tot = __shfl_sync(FULL, incl, 31);
         uint32_t base = 0;
-        if (lane == 31 && tot) base = atomicAdd(&A.c->sad_cnt[0], tot);
-        base = __shfl_sync(FULL, base, 31);
-        uint32_t slot = base + incl - cnt;
-        while (lost) {
-            const int b = __ffs(lost) - 1;
-            lost &= lost - 1;
-            if (slot < A.sad_cap) A.sad[slot] = wi * 16u + (uint32_t)b;
-            slot++;
+        if (lane == 31 && tot) base = atomicAdd(&s_cnt, tot);
+        uint32_t slot = __shfl_sync(FULL, base, 31) + incl - cnt;
+        while (smask) {   // slots stay below the tile's point count
+            const int bit = __ffs(smask) - 1;
+            smask &= smask - 1;
+            s_list[slot++] = wi * 16u + (uint32_t)(bit >> 1);
+        }
+    }
+    __syncthreads();
+    const uint32_t ns = s_cnt;
+    CgVal val{A.out};
+    const uint32_t st[3] = {1u, g.nx, g.nxy};
+    for (uint32_t k0 = 0; k0 < ns; k0 += blockDim.x) {
+        const uint32_t k = k0 + threadIdx.x;
+        bool keep = false;
+        if (k < ns) {
+            const uint32_t p = s_list[k];
+            uint32_t x, y, z;
+            coords(g, p, x, y, z);
+            if (!is_interior(g, x, y, z)) {
+                keep = true;   // never a saddle off the interior: lost
+            } else {
+                const float fp = val(p);
+                const int nd = g.ndim;
+                float nb[6];
+                bool nbsad = false;
+#pragma unroll
+                for (int ax = 0; ax < 3; ax++) {
+                    if (ax >= nd) break;
+                    nb[2 * ax] = val(p - st[ax]);
+                    nb[2 * ax + 1] = val(p + st[ax]);
+                    nbsad |= label_at(labels, p - st[ax]) == LAB_SAD || label_at(labels, p + st[ax]) == LAB_SAD;
+                }
+                int ph = 0, pl = 0, px = 0;
+#pragma unroll
+                for (int ax = 0; ax < 3; ax++) {
+                    if (ax >= nd) break;
+                    const float a = nb[2 * ax], b = nb[2 * ax + 1];
+                    if (a > fp && b > fp) ph++;
+                    else if (a < fp && b < fp) pl++;
+                    else px++;
+                }
+                const bool lost = !(px == 0 && ph > 0 && pl > 0);
+                // A lost saddle whose face neighbours never change during the
+                // rounds (none of them is saddle-labelled) keeps its status for
+                // good: if no small move of p can make it a saddle now, every
+                // colour round would reject it, so it is not listed.
+                keep = lost && (nbsad || saddle_feasible(nb, nd, fp));
+            }
+        }
+        const uint32_t bal = __ballot_sync(FULL, keep);
+        uint32_t base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&A.c->sad_cnt[0], (unsigned)__popc(bal));
+        base = __shfl_sync(FULL, base, 0);
+        if (keep) {
+            const uint32_t slot = base + __popc(bal & lanemask_lt());
+            if (slot < A.sad_cap) A.sad[slot] = s_list[k];
         }
     }
 }
 
 struct FusedSmem {
-    uint32_t pay[DT_BLOCKS * 33];
-    uint32_t tile;
+    uint32_t pay[DT_BLOCKS * 33];   // S1: the tile's payload; S4: its saddle list
+    uint32_t tile, cnt;
+    Geo g;
+    Layout lo;
     uint32_t w[DT_WARPS], cp[DT_WARPS];
 };
 
@@ -747,12 +818,22 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
     uint32_t* s_w = S.w;
     uint32_t* s_cp = S.cp;
     Ctrl* c = A.c;
-    const Geo g = c->g;
-    const Layout lo = c->lo;
+    // geometry and layout live in shared memory: read where used, not held in
+    // registers across the stages
+    if (threadIdx.x == 0) {
+        S.g = c->g;
+        S.lo = c->lo;
+    }
+    __syncthreads();
+    const Geo& g = S.g;
+    const Layout& lo = S.lo;
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
     const uint32_t ntiles = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
     const uint32_t H = TOPO ? fused_reach(g, ntiles) : 0u;
-    const uint32_t total = ntiles + 3 * H;
+    // stage lag: the reach H plus some slack, so that a stage rarely waits for
+    // tiles that CTAs took just before this one
+    const uint32_t Lg = TOPO ? hmin<uint32_t>(H + A.slack, ntiles) : 0u;
+    const uint32_t total = ntiles + 3 * Lg;
     bool corrupt = false;
     unsigned long long restored = 0, skipped = 0;
     while (true) {
@@ -766,7 +847,7 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
         mark_done(c, A.flags, 1, t, ntiles);
     }
     if (TOPO) {
-        const long long s2 = (long long)t - H, s3 = (long long)t - 2 * H, s4 = (long long)t - 3 * H;
+        const long long s2 = (long long)t - Lg, s3 = (long long)t - 2 * Lg, s4 = (long long)t - 3 * Lg;
         if (s2 >= 0 && s2 < ntiles) {
             wait_front(c, A.flags, 1, (uint32_t)hmin<long long>(s2 + H, ntiles - 1) + 1, ntiles, A.status);
             stage_extrema(A, g, labels, (uint32_t)s2, restored, skipped);
@@ -779,7 +860,7 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
         }
         if (s4 >= 0 && s4 < ntiles) {
             wait_front(c, A.flags, 3, (uint32_t)hmin<long long>(s4 + H, ntiles - 1) + 1, ntiles, A.status);
-            stage_saddles(A, g, labels, (uint32_t)s4);
+            stage_saddles(A, g, labels, (uint32_t)s4, s_pay, S.cnt);
         }
     }
     }
@@ -796,7 +877,7 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
     }
 }
 
-__global__ void __launch_bounds__(256, 6) k_decode_fused(FusedArgs A) {
+__global__ void __launch_bounds__(256, 4) k_decode_fused(FusedArgs A) {
     __shared__ FusedSmem S;
     if (*A.status) return;
     if (A.c->flags & FLAG_NO_TOPO) fused_body<false>(A, S);
@@ -907,12 +988,20 @@ void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned 
                          const uint32_t* cp_pre, const int32_t* delta, uint32_t* cp_idx, float* newv,
                          uint32_t* flags, uint32_t* sad, uint32_t sad_cap, uint32_t ntiles_dec, uint32_t h_bound,
                          int sms, int* status, cudaStream_t st) {
-    FusedArgs A{in, c, out, pay_pre, cp_pre, delta, cp_idx, newv, flags, sad, sad_cap, status};
+    static int fit = -1;
+    if (fit < 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_decode_fused, 256, 0) != cudaSuccess || b < 1) b = 1;
+        fit = b;
+    }
+    const uint32_t slack = g_tuning.dec_slack_tiles > 0 ? (uint32_t)g_tuning.dec_slack_tiles
+                                                        : (uint32_t)(fit * sms) / 4u;
+    FusedArgs A{in, c, out, pay_pre, cp_pre, delta, cp_idx, newv, flags, sad, sad_cap, slack, status};
     // About one virtual tile per CTA (ntiles decode tiles plus 3H trailing stage
     // slots; H is known only on the device, so CTAs keep taking virtual tiles
     // until all are done).  Waits only point at lower tiles, taken by CTAs that
     // started earlier, so any residency makes progress.
-    const uint32_t grid = ntiles_dec + 3 * hmin<uint32_t>(ntiles_dec, h_bound);
+    const uint32_t grid = ntiles_dec + 3 * hmin<uint32_t>(ntiles_dec, h_bound + slack);
     k_decode_fused<<<grid, 256, 0, st>>>(A);
 }
 

@@ -12,6 +12,7 @@ struct Tuning {
     int cd_threads = 256;
     int cd_blocks_per_sm = 8;
     int rounds_blocks_per_sm = 0;   // 0: occupancy, capped at 4
+    int dec_slack_tiles = 0;        // 0: a quarter of the fused decoder's resident CTAs
 };
 extern Tuning g_tuning;
 
