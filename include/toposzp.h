@@ -175,12 +175,16 @@ uint64_t toposzp_noalloc_max_points(void);
  *                        (default: as many as fit, at most 4)
  *   dec_slack_tiles      extra lag, in 8192-point tiles, between the stages of
  *                        the fused decoder: 1..65536 (default: a quarter of its
- *                        resident CTAs) */
+ *                        resident CTAs)
+ *   saddle_records       0 or 1: the saddle rounds copy each candidate's
+ *                        neighbourhood into a compact record first (default);
+ *                        -1: they read the field directly */
 typedef struct {
     int32_t cd_threads;
     int32_t cd_blocks_per_sm;
     int32_t rounds_blocks_per_sm;
     int32_t dec_slack_tiles;
+    int32_t saddle_records;
 } toposzp_tuning;
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
 

@@ -337,10 +337,13 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
                         w.sad_cap, w.ntiles, 64u, sms, status, st);
     stage(6, st);
     stage(7, st);
-    // the stencil values are consumed by now: their buffer holds the colour buckets
+    // the stencil values are consumed by now: their buffer holds the colour
+    // buckets; the extremum positions and ranks (contiguous) hold the records
     cudaError_t e = launch_saddle_rounds(src, c, out, reinterpret_cast<uint32_t*>(ws + w.sad),
                                          reinterpret_cast<uint32_t*>(ws + w.newv),
-                                         reinterpret_cast<float*>(ws + w.sadv), w.sad_cap, sms, status, st);
+                                         reinterpret_cast<float*>(ws + w.sadv), w.sad_cap,
+                                         reinterpret_cast<uint32_t*>(ws + w.cp_idx), w.newv - w.cp_idx, sms,
+                                         status, st);
     if (e != cudaSuccess) return TOPOSZP_ERR_CUDA;
     stage(8, st);
     return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;
@@ -353,11 +356,13 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     if (t->cd_blocks_per_sm < 0 || t->cd_blocks_per_sm > 32) return TOPOSZP_ERR_INVALID_ARG;
     if (t->rounds_blocks_per_sm < 0 || t->rounds_blocks_per_sm > 4) return TOPOSZP_ERR_INVALID_ARG;
     if (t->dec_slack_tiles < 0 || t->dec_slack_tiles > 65536) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->saddle_records < -1 || t->saddle_records > 1) return TOPOSZP_ERR_INVALID_ARG;
     Tuning u;
     if (t->cd_threads) u.cd_threads = t->cd_threads;
     if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
     u.rounds_blocks_per_sm = t->rounds_blocks_per_sm;
     u.dec_slack_tiles = t->dec_slack_tiles;
+    u.saddle_records = t->saddle_records;
     g_tuning = u;
     return TOPOSZP_OK;
 }

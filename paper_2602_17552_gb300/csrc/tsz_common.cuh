@@ -132,6 +132,7 @@ struct Ctrl {
     unsigned int front[4];    // per-stage frontiers of the fused decoder
     unsigned int tile_fused, pad5[3];
     unsigned int sad_col[8], sad_fill[8];   // lost saddles per colour (RS^ rounds)
+    unsigned int sad_next[8];               // work counters of the rounds' evaluation
     Layout lo;
     float g_rbf[9];
 };

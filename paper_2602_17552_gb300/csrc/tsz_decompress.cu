@@ -369,6 +369,213 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
     return true;
 }
 
+// ------------------------------------------------- saddle neighbourhood records
+//
+// Every colour round reads each candidate's RBF neighbourhood.  Read from the
+// field, a round's candidates touch about half of its sectors, once per
+// colour.  Instead the rounds kernel first copies, in one pass in list order
+// (consecutive candidates are neighbours in space, so the copy streams through
+// L2), the neighbourhood of every candidate into a compact record stored in
+// its colour bucket.  A round then streams its records.  Points that can
+// change during the rounds are the listed candidates, all saddle-labelled; the
+// record marks the saddle-labelled slots and those are read from the field
+// when a round needs them, so a record always gives current values and the
+// arithmetic is exactly that of saddle_candidate().
+//
+// Slots: the RBF neighbourhood N_r(p) \ {p} in the RBF table's (z, y, x)
+// order, then the remaining points at Manhattan distance 1..2 (the face
+// neighbours and their face neighbours, read by checks (a) and (b)).
+
+template <int ND, int R>
+struct RecStencil {
+    int ns = 0, n = 0;   // RBF slots, all slots (<= 32)
+    int dx[32] = {}, dy[32] = {}, dz[32] = {}, d2[32] = {};
+    int face[6] = {};    // slot of p's face neighbour f, order (x-, x+, y-, y+, z-, z+)
+    int nbr[6][6] = {};  // slot of face neighbour k of face neighbour f; -1: p itself
+    __host__ __device__ constexpr int find(int x, int y, int z) const {
+        for (int i = 0; i < n; i++)
+            if (dx[i] == x && dy[i] == y && dz[i] == z) return i;
+        return -1;
+    }
+    __host__ __device__ constexpr RecStencil() {
+        const int rz = ND == 3 ? R : 0;
+        for (int z = -rz; z <= rz; z++)
+            for (int y = -R; y <= R; y++)
+                for (int x = -R; x <= R; x++) {
+                    const int q = x * x + y * y + z * z;
+                    if (q == 0 || q > R * R) continue;
+                    dx[n] = x, dy[n] = y, dz[n] = z, d2[n] = q;
+                    n++;
+                }
+        ns = n;
+        const int z2 = ND == 3 ? 2 : 0;
+        for (int z = -z2; z <= z2; z++)
+            for (int y = -2; y <= 2; y++)
+                for (int x = -2; x <= 2; x++) {
+                    const int m = (x < 0 ? -x : x) + (y < 0 ? -y : y) + (z < 0 ? -z : z);
+                    if (m == 0 || m > 2 || find(x, y, z) >= 0) continue;
+                    dx[n] = x, dy[n] = y, dz[n] = z, d2[n] = x * x + y * y + z * z;
+                    n++;
+                }
+        for (int f = 0; f < 2 * ND; f++) {
+            const int ax = f / 2, sg = f % 2 ? 1 : -1;
+            const int fx = ax == 0 ? sg : 0, fy = ax == 1 ? sg : 0, fz = ax == 2 ? sg : 0;
+            face[f] = find(fx, fy, fz);
+            for (int k = 0; k < 2 * ND; k++) {
+                const int bx = k / 2, bs = k % 2 ? 1 : -1;
+                const int gx = fx + (bx == 0 ? bs : 0), gy = fy + (bx == 1 ? bs : 0), gz = fz + (bx == 2 ? bs : 0);
+                nbr[f][k] = (gx == 0 && gy == 0 && gz == 0) ? -1 : find(gx, gy, gz);
+            }
+        }
+    }
+    // record words: the slots and the saddle-slot mask, padded to 16 bytes
+    __host__ __device__ constexpr int words() const { return (n + 1 + 3) / 4 * 4; }
+};
+constexpr int REC_MAX_WORDS = 36;   // the largest record (3D, r = 2)
+
+// Record kinds: 3D r = 1, 2 and 2D r = 1, 2, 3 (3D r = 3 keeps the field reads).
+__host__ __device__ inline bool rec_supported(int ndim, int r) {
+    return ndim == 3 ? (r == 1 || r == 2) : (r >= 1 && r <= 3);
+}
+
+// Candidates with records: the whole RBF neighbourhood and both face rings inside the grid.
+__device__ __forceinline__ bool rec_inside(const Geo& g, int r, uint32_t x, uint32_t y, uint32_t z) {
+    const uint32_t m = r > 2 ? (uint32_t)r : 2u;
+    return x >= m && x + m < g.nx && y >= m && y + m < g.ny && (g.ndim == 2 || (z >= m && z + m < g.nz));
+}
+
+template <int ND, int R>
+__device__ __forceinline__ void rec_gather(const float* F, const uint32_t* labels, const Geo& g, uint32_t p,
+                                           uint32_t* rec) {
+    constexpr RecStencil<ND, R> S{};
+    constexpr int W = S.words();
+    uint32_t w[W];
+    uint32_t dyn = 0;
+#pragma unroll
+    for (int e = 0; e < S.n; e++) {
+        const uint32_t q = p + (uint32_t)(S.dx[e] + S.dy[e] * (int)g.nx + S.dz[e] * (int)g.nxy);
+        w[e] = __float_as_uint(F[q]);
+        dyn |= (label_at(labels, q) == LAB_SAD ? 1u : 0u) << e;
+    }
+    w[S.n] = dyn;
+#pragma unroll
+    for (int e = S.n + 1; e < W; e++) w[e] = 0u;
+    uint4* d = reinterpret_cast<uint4*>(rec);
+#pragma unroll
+    for (int k = 0; k < W / 4; k++) d[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+}
+
+// classify_interior()'s rule on explicit values: centre v, face neighbours n[]
+template <int ND>
+__device__ __forceinline__ int cls_vals(float v, const float* n) {
+    const bool Hx = n[0] > v && n[1] > v, Lx = n[0] < v && n[1] < v;
+    const bool Hy = n[2] > v && n[3] > v, Ly = n[2] < v && n[3] < v;
+    const bool Hz = ND != 3 || (n[4] > v && n[5] > v), Lz = ND != 3 || (n[4] < v && n[5] < v);
+    const bool m = Hx && Hy && Hz, M = Lx && Ly && Lz;
+    const bool s = (Hx || Lx) && (Hy || Ly) && (Hz || Lz) && !m && !M;
+    return (int)((uint32_t)(m | M) | ((uint32_t)(s | M) << 1));
+}
+
+// saddle_candidate() for a candidate with a record (rec_inside holds).
+template <int ND, int R>
+__device__ bool saddle_candidate_rec(const float* F, const uint32_t* labels, const Geo& g, const Ctrl* c,
+                                     float den_full, uint32_t p, const uint32_t* rec, float& vout) {
+    constexpr RecStencil<ND, R> S{};
+    constexpr int W = S.words();
+    uint32_t w[W];
+    const uint4* s4 = reinterpret_cast<const uint4*>(rec);
+#pragma unroll
+    for (int k = 0; k < W / 4; k++) {
+        const uint4 t = s4[k];
+        w[4 * k] = t.x, w[4 * k + 1] = t.y, w[4 * k + 2] = t.z, w[4 * k + 3] = t.w;
+    }
+    const uint32_t dyn = w[S.n];
+    float v[S.n];
+#pragma unroll
+    for (int e = 0; e < S.n; e++)
+        v[e] = (dyn >> e) & 1u ? F[p + (uint32_t)(S.dx[e] + S.dy[e] * (int)g.nx + S.dz[e] * (int)g.nxy)]
+                               : __uint_as_float(w[e]);
+    const float Fp = F[p];
+    float nb[2 * ND];
+#pragma unroll
+    for (int f = 0; f < 2 * ND; f++) nb[f] = v[S.face[f]];
+    {
+        int ph = 0, pl = 0, px = 0;
+#pragma unroll
+        for (int ax = 0; ax < ND; ax++) {
+            const float a = nb[2 * ax], b = nb[2 * ax + 1];
+            if (a > Fp && b > Fp) ph++;
+            else if (a < Fp && b < Fp) pl++;
+            else px++;
+        }
+        if (px == 0 && ph > 0 && pl > 0) return false;
+    }
+    float gmin = __int_as_float(0x7F800000);
+#pragma unroll
+    for (int i = 0; i < 2 * ND; i++) {
+        const float gi = fabsf(__fsub_rn(nb[i], Fp));
+        if (gi > 0.0f && gi < gmin) gmin = gi;
+    }
+    if (isinf(gmin)) return false;
+    if (!saddle_feasible(nb, ND, Fp)) return false;
+    float num = 0.0f;
+#pragma unroll
+    for (int e = 0; e < S.ns; e++) num = __fadd_rn(num, __fmul_rn(c->g_rbf[S.d2[e] - 1], v[e]));
+    const float u = __fdiv_rn(num, den_full);
+    const float capv = fminf(__fmul_rn(0.1f, c->h_f), __fmul_rn(0.5f, gmin));
+    float stp = __fsub_rn(u, Fp);
+    if (stp > capv) stp = capv;
+    if (stp < -capv) stp = -capv;
+    const float vn = __fadd_rn(Fp, stp);
+    if (vn == Fp) return false;
+    if (cls_vals<ND>(vn, nb) != LAB_SAD) return false;   // (a)
+    const uint32_t st[3] = {1u, g.nx, g.nxy};
+#pragma unroll
+    for (int f = 0; f < 2 * ND; f++) {                   // (b)
+        float qn[2 * ND], qo[2 * ND];
+#pragma unroll
+        for (int k = 0; k < 2 * ND; k++) {
+            const int sl = S.nbr[f][k];
+            qn[k] = sl < 0 ? vn : v[sl < 0 ? 0 : sl];
+            qo[k] = sl < 0 ? Fp : v[sl < 0 ? 0 : sl];
+        }
+        const float fq = nb[f];
+        const int tn = cls_vals<ND>(fq, qn), to = cls_vals<ND>(fq, qo);
+        if (tn != to) {
+            const uint32_t q = f & 1 ? p + st[f >> 1] : p - st[f >> 1];
+            if (tn != label_at(labels, q)) return false;
+        }
+    }
+    if (!(fabsf(__fsub_rn(vn, Fp)) <= c->h_f)) return false;   // (c)
+    vout = vn;
+    return true;
+}
+
+// Record dispatch on (ndim, r); false when that kind keeps the field reads.
+__device__ __forceinline__ void rec_gather_any(int ndim, int r, const float* F, const uint32_t* labels,
+                                               const Geo& g, uint32_t p, uint32_t* rec) {
+    if (ndim == 3) {
+        if (r == 1) rec_gather<3, 1>(F, labels, g, p, rec);
+        else rec_gather<3, 2>(F, labels, g, p, rec);
+    } else {
+        if (r == 1) rec_gather<2, 1>(F, labels, g, p, rec);
+        else if (r == 2) rec_gather<2, 2>(F, labels, g, p, rec);
+        else rec_gather<2, 3>(F, labels, g, p, rec);
+    }
+}
+
+__device__ __forceinline__ bool saddle_candidate_rec_any(int ndim, int r, const float* F, const uint32_t* labels,
+                                                         const Geo& g, const Ctrl* c, float den_full, uint32_t p,
+                                                         const uint32_t* rec, float& v) {
+    if (ndim == 3) {
+        if (r == 1) return saddle_candidate_rec<3, 1>(F, labels, g, c, den_full, p, rec, v);
+        return saddle_candidate_rec<3, 2>(F, labels, g, c, den_full, p, rec, v);
+    }
+    if (r == 1) return saddle_candidate_rec<2, 1>(F, labels, g, c, den_full, p, rec, v);
+    if (r == 2) return saddle_candidate_rec<2, 2>(F, labels, g, c, den_full, p, rec, v);
+    return saddle_candidate_rec<2, 3>(F, labels, g, c, den_full, p, rec, v);
+}
+
 // ---------------------------------------------------------- offset pre-pass
 //
 // Per decode tile (64 blocks): payload words from the widths and the number of
@@ -887,9 +1094,10 @@ __global__ void __launch_bounds__(256, 4) k_decode_fused(FusedArgs A) {
 // RS^ colour rounds over the lost-saddle list (cooperative: the grid syncs
 // between the evaluation and the write of every colour).  The list is first
 // bucketed by colour so that each round touches only its own candidates.
-__global__ void __launch_bounds__(256) k_saddle_rounds(const uint8_t* __restrict__ in, Ctrl* c, float* out,
+__global__ void __launch_bounds__(256, 4) k_saddle_rounds(const uint8_t* __restrict__ in, Ctrl* c, float* out,
                                                        const uint32_t* sad, uint32_t* sadb, float* sadv,
-                                                       uint32_t sad_cap, int* status) {
+                                                       uint32_t sad_cap, uint32_t* rec, uint32_t rec_cap,
+                                                       int* status) {
     __shared__ RbfTable T;
     __shared__ uint32_t s_cnt[8], s_base[8];
     cg::grid_group grid = cg::this_grid();
@@ -927,27 +1135,46 @@ __global__ void __launch_bounds__(256) k_saddle_rounds(const uint8_t* __restrict
         s_cnt[threadIdx.x] = 0;
     }
     __syncthreads();
+    // records (uniform across the grid): when the kind has them and they fit
+    const int r = c->rbf_k / 2;
+    const bool use_rec = rec_cap > 0 && ns <= rec_cap && rec_supported(g.ndim, r);
+    const uint32_t RW = REC_MAX_WORDS;
     for (uint32_t j = tid; j < ns; j += nth) {
         const uint32_t p = sad[j];
         uint32_t x, y, z;
         coords(g, p, x, y, z);
         const int col = colour_of(g, x, y, z);
-        const uint32_t slot = s_base[col] + atomicAdd(&s_cnt[col], 1u);
-        sadb[base[col] + slot] = p;
+        const uint32_t slot = base[col] + s_base[col] + atomicAdd(&s_cnt[col], 1u);
+        sadb[slot] = p;
+        if (use_rec && rec_inside(g, r, x, y, z)) rec_gather_any(g.ndim, r, out, labels, g, p, rec + (size_t)slot * RW);
     }
     grid.sync();
     unsigned long long fixed = 0;
     for (int sw = 0; sw < c->rs_sweeps; sw++) {
         for (int col = 0; col < ncol; col++) {
             const uint32_t b0 = base[col], nc = cnt[col];
-            for (uint32_t j = tid; j < nc; j += nth) {
-                const uint32_t p = sadb[b0 + j];
-                uint32_t x, y, z;
-                coords(g, p, x, y, z);
-                float v;
-                sadv[b0 + j] = saddle_candidate(out, labels, g, c, T, p, x, y, z, v) ? v : __int_as_float(0x7FC00000);
+            // warps take 32 candidates at a time: evaluation costs vary a lot
+            while (true) {
+                uint32_t k0 = 0;
+                if ((threadIdx.x & 31) == 0) k0 = atomicAdd(&c->sad_next[col], 32u);
+                k0 = __shfl_sync(FULL, k0, 0);
+                if (k0 >= nc) break;
+                const uint32_t j = k0 + (threadIdx.x & 31);
+                if (j < nc) {
+                    const uint32_t p = sadb[b0 + j];
+                    uint32_t x, y, z;
+                    coords(g, p, x, y, z);
+                    float v;
+                    const bool ok = use_rec && rec_inside(g, r, x, y, z)
+                                        ? saddle_candidate_rec_any(g.ndim, r, out, labels, g, c, T.den_full, p,
+                                                                   rec + (size_t)(b0 + j) * RW, v)
+                                        : saddle_candidate(out, labels, g, c, T, p, x, y, z, v);
+                    sadv[b0 + j] = ok ? v : __int_as_float(0x7FC00000);
+                }
             }
             grid.sync();
+            // the counter is next used a sweep later, many grid syncs away
+            if (tid == 0) c->sad_next[col] = 0;
             for (uint32_t j = tid; j < nc; j += nth) {
                 const float v = sadv[b0 + j];
                 if (!isnan(v)) {
@@ -1006,7 +1233,8 @@ void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned 
 }
 
 cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, uint32_t* sadb,
-                                 float* sadv, uint32_t sad_cap, int sms, int* status, cudaStream_t st) {
+                                 float* sadv, uint32_t sad_cap, uint32_t* rec, uint64_t rec_bytes, int sms,
+                                 int* status, cudaStream_t st) {
     static int fit = -1;
     if (fit < 0) {
         int b = 0;
@@ -1016,8 +1244,11 @@ cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const u
     }
     int per_sm = g_tuning.rounds_blocks_per_sm > 0 ? g_tuning.rounds_blocks_per_sm : 4;
     if (per_sm > fit) per_sm = fit;   // a cooperative grid must be co-resident
+    uint32_t rec_cap = 0;
+    if (g_tuning.saddle_records >= 0)
+        rec_cap = (uint32_t)hmin<uint64_t>(rec_bytes / (4ull * REC_MAX_WORDS), 0xFFFFFFFFull);
     void* args[] = {(void*)&in, (void*)&c, (void*)&out, (void*)&sad, (void*)&sadb, (void*)&sadv,
-                    (void*)&sad_cap, (void*)&status};
+                    (void*)&sad_cap, (void*)&rec, (void*)&rec_cap, (void*)&status};
     return cudaLaunchCooperativeKernel((const void*)k_saddle_rounds, dim3(per_sm * sms), dim3(256), args, 0, st);
 }
 }  // namespace tsz

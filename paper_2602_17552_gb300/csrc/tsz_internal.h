@@ -13,6 +13,7 @@ struct Tuning {
     int cd_blocks_per_sm = 8;
     int rounds_blocks_per_sm = 0;   // 0: occupancy, capped at 4
     int dec_slack_tiles = 0;        // 0: a quarter of the fused decoder's resident CTAs
+    int saddle_records = 0;         // >= 0: neighbourhood records in the saddle rounds; < 0: field reads
 };
 extern Tuning g_tuning;
 
@@ -66,7 +67,8 @@ void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned 
                          uint32_t* flags, uint32_t* sad, uint32_t sad_cap, uint32_t ntiles_dec, uint32_t h_bound,
                          int sms, int* status, cudaStream_t st);
 cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, uint32_t* sadb,
-                                 float* sadv, uint32_t sad_cap, int sms, int* status, cudaStream_t st);
+                                 float* sadv, uint32_t sad_cap, uint32_t* rec, uint64_t rec_bytes, int sms,
+                                 int* status, cudaStream_t st);
 
 // ---- analysis
 void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsigned long long* out12,
