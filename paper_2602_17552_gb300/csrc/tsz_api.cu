@@ -59,7 +59,7 @@ constexpr CompressWs compress_ws_c(uint64_t n) {
     w.os_stride = w.os_tiles * 256u;
     uint64_t o = 0;
     w.ctrl = o; o = a256(o + CTRL_BYTES);
-    w.desc = o; o = a256(o + 16ull * (w.ntiles + 1));
+    w.desc = o; o = a256(o + 16ull * (w.ntiles + 1));   // per-tile counts, then prefixes
     w.rdesc = o; o = a256(o + 16ull * (w.rank_tiles + 1));
     w.os_small = o; o = a256(o + 4ull * (2 * 4 * 256) * 2 + 4ull * 8);   // histograms, bases, counters
     // end of the region zeroed at the start of every call
@@ -69,6 +69,9 @@ constexpr CompressWs compress_ws_c(uint64_t n) {
     w.listm = o; o = a256(o + 8ull * w.list_cap);
     w.tmpM = o; o = a256(o + 8ull * w.list_cap);
     w.tmpm = o; o = a256(o + 8ull * w.list_cap);
+    // the encoder's per-tile payload slots share the sort's buffers (used later)
+    const uint64_t slots = 4ull * (TILE_BLOCKS * 33) * w.ntiles;
+    if (w.tmpM + slots > o) o = a256(w.tmpM + slots);
     w.agg = o; o = a256(o + 8ull * 2 * w.agg_stride);
     w.delta = o; o = a256(o + 4ull * (n + 2));
     w.end = o;
@@ -226,7 +229,7 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     uint8_t* ws = reinterpret_cast<uint8_t*>(workspace);
     uint8_t* o = reinterpret_cast<uint8_t*>(out);
     Ctrl* c = reinterpret_cast<Ctrl*>(ws + w.ctrl);
-    Desc* desc = reinterpret_cast<Desc*>(ws + w.desc);
+    uint2* tcnt = reinterpret_cast<uint2*>(ws + w.desc);
     Desc* rdesc = reinterpret_cast<Desc*>(ws + w.rdesc);
     uint2* listM = reinterpret_cast<uint2*>(ws + w.listM);
     uint2* listm = reinterpret_cast<uint2*>(ws + w.listm);
@@ -243,7 +246,8 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     launch_range_cd(field, g, c, labels, topo, sms, st);
     stage(1, st);
     launch_qparams(c, status, st);
-    launch_encode_field(field, labels, c, desc, o, lo, listM, listm, topo, g.nb, sms, status, st);
+    launch_encode_field(field, labels, c, tcnt, reinterpret_cast<uint32_t*>(ws + w.tmpM), o, lo, listM, listm,
+                        topo, g.nb, sms, status, st);
     stage(2, st);
     if (topo) {
         SortWs sw;
@@ -256,7 +260,7 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
         sw.max_tiles = w.os_tiles;
         launch_ranks(c, listM, listm, reinterpret_cast<uint2*>(ws + w.tmpM),
                      reinterpret_cast<uint2*>(ws + w.tmpm), sw, reinterpret_cast<uint2*>(ws + w.agg),
-                     w.agg_stride, reinterpret_cast<int32_t*>(ws + w.delta), w.G, sms, status, st);
+                     w.agg_stride, tcnt, reinterpret_cast<int32_t*>(ws + w.delta), w.G, sms, status, st);
         launch_encode_ranks(reinterpret_cast<int32_t*>(ws + w.delta), c, rdesc, o, w.rank_tiles, sms,
                             status, st);
     }

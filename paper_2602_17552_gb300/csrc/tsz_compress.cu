@@ -318,7 +318,7 @@ __global__ void k_qparams(Ctrl* c, int* status) {
 // tail block repeats its last code); Lorenzo residuals d_0 = 0,
 // d_j = q_j - q_{j-1}; w_b = bit length of max|d|; w_b = 0 is a constant block.
 // A non-constant block stores a sign plane and w_b magnitude planes, one
-// ballot each, at its exclusive prefix offset from the look-back.
+// ballot each, at its exclusive prefix offset in the payload section.
 
 struct EncOut {
     uint32_t* cbits;
@@ -327,26 +327,29 @@ struct EncOut {
     uint32_t* pay;
 };
 
-// Field encoder, one 2048-point tile per CTA (tiles handed out in order by an
-// atomic counter, so the look-back only waits on CTAs that already run).
-// Phase 1 quantises, forms the Lorenzo residuals and widths, and packs every
-// non-constant block's sign and magnitude planes into shared memory; only then
-// does warp 0 run the look-back, after which the tile's payload is one
-// contiguous, coalesced copy.  TOPO also reads the labels, counts the tile's
-// extrema (carried through the same look-back, giving each extremum its
-// position in the delta sequence) and appends (key, position) pairs to the
-// maxima / minima lists.
-constexpr int WARP_PAY = BPW * 33;   // worst-case payload words of one warp's blocks
+// Field encoder, one 2048-point tile per CTA.  Phase 1 quantises, forms the
+// Lorenzo residuals and widths, and packs every non-constant block's sign and
+// magnitude planes into shared memory; phase 2 copies the tile's payload to
+// its fixed-size slot of a scratch area and records the tile's word and
+// extremum counts.  No CTA waits for another: the tile prefixes come from a
+// scan afterwards (k_enc_tile_scan) and k_enc_copy moves every slot to its
+// place in the payload section.  TOPO also reads the labels and appends
+// (key, tile << 11 | index of the extremum within its tile) pairs to the
+// maxima / minima lists; the rank scatter turns the pair into the extremum's
+// position in the delta sequence.
+constexpr int WARP_PAY = BPW * 33;                  // worst-case payload words of one warp's blocks
+constexpr int TILE_PAY = TILE_WARPS * WARP_PAY;     // ... of one tile: its scratch slot
+constexpr int TILE_POS_BITS = 11;                   // 2048 points per tile
+static_assert(TILE_BLOCKS * 32 == (1 << TILE_POS_BITS), "tile size");
 
 template <bool TOPO>
 __global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ a,
                                                       const uint32_t* __restrict__ labels, Ctrl* c,
-                                                      Desc* desc, EncOut o, uint2* listM, uint2* listm,
+                                                      uint2* tcnt, EncOut o, uint2* listM, uint2* listm,
                                                       int* status) {
     __shared__ uint32_t s_pay[TILE_WARPS * WARP_PAY];
     __shared__ uint32_t s_tile;
     __shared__ uint32_t s_w[TILE_WARPS], s_cp[TILE_WARPS], s_M[TILE_WARPS], s_m[TILE_WARPS];
-    __shared__ unsigned long long s_pre_w, s_pre_cp;
     __shared__ uint32_t s_cbits[2];
     __shared__ unsigned long long s_sum;
     if (*status) return;
@@ -439,8 +442,7 @@ __global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ 
             if (tM) bM = atomicAdd(&c->cnt_max, tM);
             if (tm) bm = atomicAdd(&c->cnt_min, tm);
         }
-        unsigned long long pw, pc;
-        lookback(desc, tile, tw, tc, pw, pc, status);
+        if (lane == 0) tcnt[tile] = make_uint2(tw, tc);
         bM = __shfl_sync(FULL, bM, 0);
         bm = __shfl_sync(FULL, bm, 0);
         if (lane < TILE_WARPS) {   // exclusive offsets per warp
@@ -449,20 +451,13 @@ __global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ 
             s_M[lane] = bM + iM - vM;
             s_m[lane] = bm + im - vm;
         }
-        if (lane == 0) {
-            s_pre_w = pw;
-            s_pre_cp = pc;
-            if (tile == ntiles - 1) {
-                c->pay_words = pw + tw;
-                c->k_total = pc + tc;
-            }
-            if (s_sum) atomicAdd(&c->sum_abs, s_sum);
-        }
+        if (lane == 0 && s_sum) atomicAdd(&c->sum_abs, s_sum);
     }
     __syncthreads();
-    // ---- phase 2: coalesced copy of the packed planes, metadata, extremum lists
+    // ---- phase 2: coalesced copy of the packed planes to the tile's slot,
+    // metadata, extremum lists
     {
-        uint32_t* dst = o.pay + s_pre_w + s_w[warp];
+        uint32_t* dst = o.pay + (size_t)tile * TILE_PAY + s_w[warp];
         for (uint32_t k = lane; k < wwords; k += 32) dst[k] = wpay[k];
     }
     if (lane < BPW && blk0 + lane < g.nb) {
@@ -474,7 +469,7 @@ __global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ 
         if (wi < ncw) o.cbits[wi] = s_cbits[threadIdx.x];
     }
     if (TOPO) {
-        unsigned long long cpoff = s_pre_cp + s_cp[warp];
+        uint32_t cpoff = s_cp[warp];
         uint32_t offM = s_M[warp], offm = s_m[warp];
         const uint32_t lt = lanemask_lt();
 #pragma unroll
@@ -485,7 +480,7 @@ __global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ 
             const uint32_t bm = __ballot_sync(FULL, lab == LAB_MIN);
             const uint32_t bb = bM | bm;
             if (lab == LAB_MAX || lab == LAB_MIN) {
-                const uint32_t pos = (uint32_t)(cpoff + __popc(bb & lt));
+                const uint32_t pos = tile << TILE_POS_BITS | (cpoff + __popc(bb & lt));
                 const uint32_t key = ord_key(areg[j]);
                 if (lab == LAB_MAX) listM[offM + __popc(bM & lt)] = make_uint2(key, pos);
                 else listm[offm + __popc(bm & lt)] = make_uint2(~key, pos);
@@ -494,6 +489,60 @@ __global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ 
             offM += __popc(bM);
             offm += __popc(bm);
         }
+    }
+}
+
+// Exclusive prefixes of the tiles' (payload words, extrema) in place, with the
+// totals at index ntiles and in the control block.  One CTA, chunks of
+// consecutive tiles per thread.
+__global__ void __launch_bounds__(1024) k_enc_tile_scan(uint2* tcnt, uint32_t ntiles, Ctrl* c,
+                                                        const int* status) {
+    __shared__ unsigned long long sw[1024], sc[1024];
+    if (*status) return;
+    const uint32_t per = (ntiles + 1023) / 1024;
+    const uint32_t b = threadIdx.x * per, e = min(ntiles, b + per);
+    unsigned long long aw = 0, ac = 0;
+    for (uint32_t i = b; i < e; i++) {
+        const uint2 v = tcnt[i];
+        aw += v.x;
+        ac += v.y;
+    }
+    sw[threadIdx.x] = aw;
+    sc[threadIdx.x] = ac;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        const unsigned long long tw = threadIdx.x >= o ? sw[threadIdx.x - o] : 0;
+        const unsigned long long tc = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
+        __syncthreads();
+        sw[threadIdx.x] += tw;
+        sc[threadIdx.x] += tc;
+        __syncthreads();
+    }
+    unsigned long long rw = sw[threadIdx.x] - aw, rc = sc[threadIdx.x] - ac;
+    for (uint32_t i = b; i < e; i++) {
+        const uint2 v = tcnt[i];
+        tcnt[i] = make_uint2((uint32_t)rw, (uint32_t)rc);
+        rw += v.x;
+        rc += v.y;
+    }
+    if (threadIdx.x == 1023) {
+        tcnt[ntiles] = make_uint2((uint32_t)sw[1023], (uint32_t)sc[1023]);
+        c->pay_words = sw[1023];
+        c->k_total = sc[1023];
+    }
+}
+
+// Every tile's payload slot to its place in the payload section (a warp per tile).
+__global__ void __launch_bounds__(256) k_enc_copy(const uint32_t* __restrict__ scratch, const uint2* tpre,
+                                                  uint32_t ntiles, uint32_t* pay, const int* status) {
+    if (*status) return;
+    const int lane = threadIdx.x & 31;
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
+         t += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t p0 = tpre[t].x, cnt = tpre[t + 1].x - p0;
+        const uint32_t* src = scratch + (size_t)t * TILE_PAY;
+        uint32_t* dst = pay + p0;
+        for (uint32_t k = lane; k < cnt; k += 32) dst[k] = __ldcs(src + k);
     }
 }
 
@@ -876,7 +925,7 @@ __global__ void __launch_bounds__(256) k_rank_scan(uint2* agg, uint32_t agg_stri
 
 // pass 3: per tile, scan with the carried prefix and scatter delta[pos]
 __global__ void __launch_bounds__(256) k_rank_scatter(const uint2* s0, const uint2* s1, const Ctrl* c,
-                                                      const uint2* agg, uint32_t agg_stride,
+                                                      const uint2* agg, uint32_t agg_stride, const uint2* tpre,
                                                       int32_t* delta, int G, const int* status) {
     __shared__ SegCnt sh[256];
     if (*status) return;
@@ -911,7 +960,8 @@ __global__ void __launch_bounds__(256) k_rank_scatter(const uint2* s0, const uin
         for (int j = 0; j < RANK_TILE / 256; j++) {
             if (b + j < k) {
                 run = seg_op(run, el[j]);
-                delta[s[b + j].y] = (int32_t)run.c;
+                const uint32_t y = s[b + j].y;
+                delta[tpre[y >> TILE_POS_BITS].y + (y & ((1u << TILE_POS_BITS) - 1))] = (int32_t)run.c;
             }
         }
         __syncthreads();
@@ -1123,18 +1173,23 @@ void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsign
 
 void launch_qparams(Ctrl* c, int* status, cudaStream_t st) { k_qparams<<<1, 32, 0, st>>>(c, status); }
 
-void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, Desc* desc, uint8_t* out,
-                         const Layout& lo, uint2* listM, uint2* listm, bool topo, uint32_t nb, int sms,
-                         int* status, cudaStream_t st) {
+void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2* tcnt, uint32_t* scratch,
+                         uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo, uint32_t nb,
+                         int sms, int* status, cudaStream_t st) {
     EncOut o{reinterpret_cast<uint32_t*>(out + lo.s1), out + lo.s2,
-             reinterpret_cast<int32_t*>(out + lo.s4), reinterpret_cast<uint32_t*>(out + lo.s5)};
+             reinterpret_cast<int32_t*>(out + lo.s4), scratch};
     const uint32_t ntiles = (nb + TILE_BLOCKS - 1) / TILE_BLOCKS;   // one tile per CTA
-    if (topo) k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
-    else k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, desc, o, listM, listm, status);
+    if (topo) k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, status);
+    else k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, status);
+    k_enc_tile_scan<<<1, 1024, 0, st>>>(tcnt, ntiles, c, status);
+    uint32_t cg = hmin<uint32_t>((ntiles + 7) / 8, (uint32_t)sms * 16);
+    k_enc_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, ntiles, reinterpret_cast<uint32_t*>(out + lo.s5),
+                                            status);
 }
 
 void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, const SortWs& sw,
-                  uint2* agg, uint32_t agg_stride, int32_t* delta, int G, int sms, int* status, cudaStream_t st) {
+                  uint2* agg, uint32_t agg_stride, const uint2* tpre, int32_t* delta, int G, int sms, int* status,
+                  cudaStream_t st) {
     const uint32_t max_tiles = sw.max_tiles;
     uint32_t hg = hmin<uint32_t>((uint32_t)cdiv((uint64_t)max_tiles * OS_TILE, 256), (uint32_t)sms * 4);
     if (hg == 0) hg = 1;
@@ -1154,7 +1209,7 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
     dim3 grid(G, 2);
     k_rank_tiles<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, G, status);
     k_rank_scan<<<2, 256, 0, st>>>(agg, agg_stride, c, status);
-    k_rank_scatter<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, delta, G, status);
+    k_rank_scatter<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, tpre, delta, G, status);
 }
 
 void launch_encode_ranks(const int32_t* delta, Ctrl* c, Desc* desc, uint8_t* out, uint32_t max_tiles,
