@@ -70,7 +70,7 @@ constexpr CompressWs compress_ws_c(uint64_t n) {
     w.tmpM = o; o = a256(o + 8ull * w.list_cap);
     w.tmpm = o; o = a256(o + 8ull * w.list_cap);
     // the encoder's per-tile payload slots share the sort's buffers (used later)
-    const uint64_t slots = 4ull * (TILE_BLOCKS * 33) * w.ntiles;
+    const uint64_t slots = 4ull * (ENC_TILE_BLOCKS * 33) * cdiv(nb, ENC_TILE_BLOCKS);
     if (w.tmpM + slots > o) o = a256(w.tmpM + slots);
     w.agg = o; o = a256(o + 8ull * 2 * w.agg_stride);
     w.delta = o; o = a256(o + 4ull * (n + 2));

@@ -27,6 +27,7 @@ constexpr int ST_OK = 0, ST_INVALID = 1, ST_NONFINITE = 2, ST_EB_SMALL = 3, ST_B
 constexpr int TILE_WARPS = 8;
 constexpr int BPW = 8;
 constexpr int TILE_BLOCKS = TILE_WARPS * BPW;   // 64 blocks = 2048 points
+constexpr int ENC_TILE_BLOCKS = 256;            // the field encoder's tile: 8192 points
 constexpr uint32_t FULL = 0xFFFFFFFFu;
 
 // Bounded waits: a look-back spin gives up after this many polls (each poll
@@ -169,6 +170,16 @@ __device__ __forceinline__ int32_t quantize(float a, float r) {
 // QZ^: bin centre q * w.
 __device__ __forceinline__ float dequantize(int32_t q, float w) {
     return __fmul_rn(__int2float_rn(q), w);
+}
+
+// gather the even bit positions of x into the low 16 bits (inverse of spread16)
+__device__ __forceinline__ uint32_t compact16(uint32_t x) {
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    return x;
 }
 
 // spread the low 16 bits of x to the even bit positions

@@ -327,169 +327,168 @@ struct EncOut {
     uint32_t* pay;
 };
 
-// Field encoder, one 2048-point tile per CTA.  Phase 1 quantises, forms the
-// Lorenzo residuals and widths, and packs every non-constant block's sign and
-// magnitude planes into shared memory; phase 2 copies the tile's payload to
-// its fixed-size slot of a scratch area and records the tile's word and
-// extremum counts.  No CTA waits for another: the tile prefixes come from a
-// scan afterwards (k_enc_tile_scan) and k_enc_copy moves every slot to its
-// place in the payload section.  TOPO also reads the labels and appends
-// (key, tile << 11 | index of the extremum within its tile) pairs to the
-// maxima / minima lists; the rank scatter turns the pair into the extremum's
-// position in the delta sequence.
-constexpr int WARP_PAY = BPW * 33;                  // worst-case payload words of one warp's blocks
-constexpr int TILE_PAY = TILE_WARPS * WARP_PAY;     // ... of one tile: its scratch slot
-constexpr int TILE_POS_BITS = 11;                   // 2048 points per tile
-static_assert(TILE_BLOCKS * 32 == (1 << TILE_POS_BITS), "tile size");
+// Field encoder, one 8192-point tile (256 blocks) per CTA, one block per
+// thread.  The tile's values are staged in shared memory with coalesced
+// 16-byte loads (rows padded to 36 words, so a thread's row reads are
+// conflict-free); each thread then quantises its 32 values, forms the Lorenzo
+// residuals, the width and the sign plane, and builds its magnitude planes
+// with register bit operations (one instruction handles a bit of one block's
+// element, as a ballot would, without moving bits between lanes).  The packed
+// payload of the tile goes to its fixed-size slot of a scratch area; no CTA
+// waits for another: the tile prefixes come from a scan afterwards
+// (k_enc_tile_scan) and k_enc_copy moves every slot to its place in the
+// payload section.  TOPO also reads the labels and appends (key,
+// tile << 13 | index of the extremum within its tile) pairs to the maxima /
+// minima lists; the rank scatter turns the pair into the extremum's position
+// in the delta sequence.
+constexpr int ENC_ROW = 36;                          // shared words per staged block row
+constexpr int TILE_PAY = ENC_TILE_BLOCKS * 33;       // worst-case payload words of a tile: its slot
+constexpr int TILE_POS_BITS = 13;                    // 8192 points per tile
+static_assert(ENC_TILE_BLOCKS * 32 == (1 << TILE_POS_BITS), "tile size");
+static_assert(ENC_TILE_BLOCKS * ENC_ROW >= TILE_PAY, "payload staging");
 
 template <bool TOPO>
-__global__ void __launch_bounds__(256) k_encode_field(const float* __restrict__ a,
-                                                      const uint32_t* __restrict__ labels, Ctrl* c,
-                                                      uint2* tcnt, EncOut o, uint2* listM, uint2* listm,
-                                                      int* status) {
-    __shared__ uint32_t s_pay[TILE_WARPS * WARP_PAY];
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_w[TILE_WARPS], s_cp[TILE_WARPS], s_M[TILE_WARPS], s_m[TILE_WARPS];
-    __shared__ uint32_t s_cbits[2];
+__global__ void __launch_bounds__(256, 3) k_encode_field(const float* __restrict__ a,
+                                                         const uint32_t* __restrict__ labels, Ctrl* c,
+                                                         uint2* tcnt, EncOut o, uint2* listM, uint2* listm,
+                                                         int* status) {
+    __shared__ __align__(16) uint32_t s_buf[ENC_TILE_BLOCKS * ENC_ROW];
+    __shared__ uint32_t s_wsum[8][3];
+    __shared__ uint32_t s_base[2];
     __shared__ unsigned long long s_sum;
     if (*status) return;
-    const Geo g = c->g;
+    const uint32_t n = c->g.n, nb = c->g.nb;
     const float r = c->r_f;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t ntiles = (g.nb + TILE_BLOCKS - 1) / TILE_BLOCKS;
-    const uint32_t ncw = (g.nb + 31) / 32;
-    if (threadIdx.x == 0) {
-        s_tile = atomicAdd(&c->tile_enc, 1u);
-        s_sum = 0;
-    }
-    if (threadIdx.x < 2) s_cbits[threadIdx.x] = 0;
-    __syncthreads();
-    const uint32_t tile = s_tile;
-    if (tile >= ntiles) return;
-    const uint32_t blk0 = tile * TILE_BLOCKS + warp * BPW;
-    uint32_t* wpay = s_pay + warp * WARP_PAY;
-    float areg[BPW];
-    uint32_t labbits = 0;   // 2 bits per block j for this lane
-    uint32_t my_w = 0;
-    int32_t my_first = 0;
-    uint32_t wwords = 0, wM = 0, wm = 0, sum_abs = 0;
-    // issue all loads of the warp's blocks first
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t b = tile * ENC_TILE_BLOCKS + t;   // this thread's block
+    const uint64_t p0 = (uint64_t)tile * (ENC_TILE_BLOCKS * 32);
+    const uint64_t left = (uint64_t)n - p0;
+    const uint32_t npts = left < (uint64_t)(ENC_TILE_BLOCKS * 32) ? (uint32_t)left : (uint32_t)(ENC_TILE_BLOCKS * 32);
+    if (t == 0) s_sum = 0;
+    // ---- stage the tile's values
+    if (npts == ENC_TILE_BLOCKS * 32 && (reinterpret_cast<uintptr_t>(a) & 15u) == 0) {
+        const float4* src = reinterpret_cast<const float4*>(a + p0);
 #pragma unroll
-    for (int j = 0; j < BPW; j++) {
-        const uint32_t i = (blk0 + j) * 32u + lane;
-        areg[j] = (blk0 + j < g.nb && i < g.n) ? __ldg(a + i) : 0.0f;
-        if (TOPO) labbits |= (uint32_t)((blk0 + j < g.nb && i < g.n) ? label_at(labels, i) : 0) << (2 * j);
-    }
-#pragma unroll
-    for (int j = 0; j < BPW; j++) {
-        const uint32_t b = blk0 + j;
-        if (b >= g.nb) break;
-        const uint32_t nvalid = min(32u, g.n - b * 32u);
-        int32_t q = quantize(areg[j], r);
-        const int32_t qlast = __shfl_sync(FULL, q, nvalid - 1);
-        if (lane >= nvalid) q = qlast;
-        const int32_t prev = __shfl_up_sync(FULL, q, 1);
-        const int32_t d = lane ? q - prev : 0;
-        const uint32_t m = (uint32_t)(d < 0 ? -d : d);
-        const uint32_t w = 32u - __clz(__reduce_max_sync(FULL, m));
-        const int32_t first = __shfl_sync(FULL, q, 0);
-        sum_abs += __reduce_add_sync(FULL, m);
-        if (lane == j) {
-            my_w = w;
-            my_first = first;
+        for (int k = 0; k < 8; k++) {
+            const uint32_t idx = k * 256 + t;   // float4 index within the tile
+            const float4 v = __ldcs(src + idx);
+            *reinterpret_cast<float4*>(s_buf + (idx >> 3) * ENC_ROW + (idx & 7) * 4) = v;
         }
-        if (w) {
-            uint32_t word = __ballot_sync(FULL, d < 0);
-            for (uint32_t p = 0; p < w; p++) {
-                const uint32_t bp = __ballot_sync(FULL, (m >> p) & 1u);
-                if (lane == p + 1) word = bp;
+    } else {
+        for (uint32_t i = t; i < npts; i += 256) s_buf[(i >> 5) * ENC_ROW + (i & 31)] = __float_as_uint(__ldcs(a + p0 + i));
+    }
+    uint2 lw = make_uint2(0u, 0u);
+    if (TOPO && b < nb) lw = reinterpret_cast<const uint2*>(labels)[b];
+    __syncthreads();
+    // ---- this thread's block: codes, residuals, width, sign plane
+    uint32_t m[32];
+    uint32_t sgn = 0, orr = 0, sum = 0;
+    int32_t first = 0;
+    if (b < nb) {
+        const uint32_t* row = s_buf + t * ENC_ROW;
+        const uint32_t nvalid = min(32u, n - b * 32u);
+        int32_t prev = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint4 v4 = *reinterpret_cast<const uint4*>(row + 4 * k);
+            const uint32_t vv[4] = {v4.x, v4.y, v4.z, v4.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int e = 4 * k + j;
+                int32_t q = quantize(__uint_as_float(vv[j]), r);
+                if (e > 0 && (uint32_t)e >= nvalid) q = prev;   // the tail block repeats its last code
+                const int32_t d = e ? q - prev : 0;
+                if (e == 0) first = q;
+                if (d < 0) sgn |= 1u << e;
+                m[e] = (uint32_t)(d < 0 ? -d : d);
+                orr |= m[e];
+                sum += m[e];
+                prev = q;
             }
-            if (lane <= w) wpay[wwords + lane] = word;
-            wwords += 1 + w;
-        }
-        if (TOPO) {
-            const int lab = (labbits >> (2 * j)) & 3;
-            wM += __popc(__ballot_sync(FULL, lab == LAB_MAX));
-            wm += __popc(__ballot_sync(FULL, lab == LAB_MIN));
         }
     }
-    if (lane == 0) {
-        s_w[warp] = wwords;
-        s_cp[warp] = wM + wm;
-        s_M[warp] = wM;
-        s_m[warp] = wm;
-        if (sum_abs) atomicAdd(&s_sum, (unsigned long long)sum_abs);
+    const uint32_t w = 32u - __clz(orr);   // bit length of max |d|
+    const uint32_t words = (b < nb && w) ? 1u + w : 0u;
+    uint32_t xmM = 0, xmm = 0;   // extremum masks (bit e: element e), maxima / minima
+    if (TOPO) {
+        const uint32_t lo0 = lw.x & 0x55555555u, hi0 = (lw.x >> 1) & 0x55555555u;
+        const uint32_t lo1 = lw.y & 0x55555555u, hi1 = (lw.y >> 1) & 0x55555555u;
+        const uint32_t valid = b < nb ? (n - b * 32u >= 32u ? FULL : (1u << (n - b * 32u)) - 1u) : 0u;
+        xmM = (compact16(lo0 & hi0) | compact16(lo1 & hi1) << 16) & valid;    // M = 11
+        xmm = (compact16(lo0 & ~hi0) | compact16(lo1 & ~hi1) << 16) & valid;  // m = 01
     }
-    {   // constant-block bits of this warp's 8 blocks
-        const uint32_t cb = __ballot_sync(FULL, lane < BPW && blk0 + lane < g.nb && my_w == 0) & 0xFFu;
-        if (lane == 0 && cb) atomicOr(&s_cbits[warp >> 2], cb << ((warp & 3) * 8));
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const uint32_t vw = lane < TILE_WARPS ? s_w[lane] : 0, vc = lane < TILE_WARPS ? s_cp[lane] : 0;
-        const uint32_t vM = lane < TILE_WARPS ? s_M[lane] : 0, vm = lane < TILE_WARPS ? s_m[lane] : 0;
-        uint32_t iw = vw, ic = vc, iM = vM, im = vm;
+    // ---- exclusive prefixes over the tile's blocks: payload words, maxima, minima
+    uint32_t iw = words, iM = __popc(xmM), im = __popc(xmm);
 #pragma unroll
-        for (int of = 1; of < TILE_WARPS; of <<= 1) {
-            const uint32_t t0 = __shfl_up_sync(FULL, iw, of), t1 = __shfl_up_sync(FULL, ic, of);
-            const uint32_t t2 = __shfl_up_sync(FULL, iM, of), t3 = __shfl_up_sync(FULL, im, of);
-            if (lane >= of) { iw += t0; ic += t1; iM += t2; im += t3; }
-        }
-        const uint32_t tw = __shfl_sync(FULL, iw, TILE_WARPS - 1), tc = __shfl_sync(FULL, ic, TILE_WARPS - 1);
-        const uint32_t tM = __shfl_sync(FULL, iM, TILE_WARPS - 1), tm = __shfl_sync(FULL, im, TILE_WARPS - 1);
-        uint32_t bM = 0, bm = 0;
-        if (TOPO && lane == 0) {
-            if (tM) bM = atomicAdd(&c->cnt_max, tM);
-            if (tm) bm = atomicAdd(&c->cnt_min, tm);
-        }
-        if (lane == 0) tcnt[tile] = make_uint2(tw, tc);
-        bM = __shfl_sync(FULL, bM, 0);
-        bm = __shfl_sync(FULL, bm, 0);
-        if (lane < TILE_WARPS) {   // exclusive offsets per warp
-            s_w[lane] = iw - vw;
-            s_cp[lane] = ic - vc;
-            s_M[lane] = bM + iM - vM;
-            s_m[lane] = bm + im - vm;
-        }
-        if (lane == 0 && s_sum) atomicAdd(&c->sum_abs, s_sum);
+    for (int of = 1; of < 32; of <<= 1) {
+        const uint32_t a0 = __shfl_up_sync(FULL, iw, of), a1 = __shfl_up_sync(FULL, iM, of),
+                       a2 = __shfl_up_sync(FULL, im, of);
+        if (lane >= (uint32_t)of) { iw += a0; iM += a1; im += a2; }
+    }
+    if (lane == 31) { s_wsum[warp][0] = iw; s_wsum[warp][1] = iM; s_wsum[warp][2] = im; }
+    {
+        unsigned long long sa = sum;
+#pragma unroll
+        for (int of = 16; of > 0; of >>= 1) sa += __shfl_xor_sync(FULL, sa, of);
+        if (lane == 0 && sa) atomicAdd(&s_sum, sa);
     }
     __syncthreads();
-    // ---- phase 2: coalesced copy of the packed planes to the tile's slot,
-    // metadata, extremum lists
-    {
-        uint32_t* dst = o.pay + (size_t)tile * TILE_PAY + s_w[warp];
-        for (uint32_t k = lane; k < wwords; k += 32) dst[k] = wpay[k];
+    uint32_t ow = 0, oM = 0, om = 0, tw = 0, tM = 0, tm = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const uint32_t v0 = s_wsum[k][0], v1 = s_wsum[k][1], v2 = s_wsum[k][2];
+        if (k < (int)warp) { ow += v0; oM += v1; om += v2; }
+        tw += v0; tM += v1; tm += v2;
     }
-    if (lane < BPW && blk0 + lane < g.nb) {
-        o.width[blk0 + lane] = (uint8_t)my_w;
-        o.first[blk0 + lane] = my_first;
-    }
-    if (threadIdx.x < 2) {
-        const uint32_t wi = tile * 2 + threadIdx.x;
-        if (wi < ncw) o.cbits[wi] = s_cbits[threadIdx.x];
+    ow += iw - words;
+    oM += iM - __popc(xmM);
+    om += im - __popc(xmm);
+    if (t == 0) {
+        tcnt[tile] = make_uint2(tw, tM + tm);
+        if (TOPO) {
+            s_base[0] = tM ? atomicAdd(&c->cnt_max, tM) : 0u;
+            s_base[1] = tm ? atomicAdd(&c->cnt_min, tm) : 0u;
+        }
+        if (s_sum) atomicAdd(&c->sum_abs, s_sum);
     }
     if (TOPO) {
-        uint32_t cpoff = s_cp[warp];
-        uint32_t offM = s_M[warp], offm = s_m[warp];
-        const uint32_t lt = lanemask_lt();
-#pragma unroll
-        for (int j = 0; j < BPW; j++) {
-            if (blk0 + j >= g.nb) break;
-            const int lab = (labbits >> (2 * j)) & 3;
-            const uint32_t bM = __ballot_sync(FULL, lab == LAB_MAX);
-            const uint32_t bm = __ballot_sync(FULL, lab == LAB_MIN);
-            const uint32_t bb = bM | bm;
-            if (lab == LAB_MAX || lab == LAB_MIN) {
-                const uint32_t pos = tile << TILE_POS_BITS | (cpoff + __popc(bb & lt));
-                const uint32_t key = ord_key(areg[j]);
-                if (lab == LAB_MAX) listM[offM + __popc(bM & lt)] = make_uint2(key, pos);
-                else listm[offm + __popc(bm & lt)] = make_uint2(~key, pos);
-            }
-            cpoff += __popc(bb);
-            offM += __popc(bM);
-            offm += __popc(bm);
+        __syncthreads();
+        // (key, position) pairs of this block's extrema, in index order
+        const uint32_t* row = s_buf + t * ENC_ROW;
+        uint32_t oMg = s_base[0] + oM, omg = s_base[1] + om, local = oM + om;
+        uint32_t xm = xmM | xmm;
+        while (xm) {
+            const int e = __ffs(xm) - 1;
+            xm &= xm - 1;
+            const uint32_t key = ord_key(__uint_as_float(row[e]));
+            const uint32_t pos = tile << TILE_POS_BITS | local++;
+            if ((xmM >> e) & 1u) listM[oMg++] = make_uint2(key, pos);
+            else listm[omg++] = make_uint2(~key, pos);
         }
     }
+    __syncthreads();   // the staged values are no longer read: the buffer takes the payload
+    if (words) {
+        uint32_t* dst = s_buf + ow;
+        dst[0] = sgn;
+        for (uint32_t p = 0; p < w; p++) {
+            uint32_t wd = 0;
+#pragma unroll
+            for (int e = 0; e < 32; e++) wd |= ((m[e] >> p) & 1u) << e;
+            dst[1 + p] = wd;
+        }
+    }
+    if (b < nb) {
+        o.width[b] = (uint8_t)w;
+        o.first[b] = first;
+    }
+    {   // constant-block bits: one word per warp of blocks
+        const uint32_t cb = __ballot_sync(FULL, b < nb && w == 0);
+        if (lane == 0 && (b >> 5) < (nb + 31) / 32) o.cbits[b >> 5] = cb;
+    }
+    __syncthreads();
+    uint32_t* slot = o.pay + (size_t)tile * TILE_PAY;
+    for (uint32_t k = t; k < tw; k += 256) slot[k] = s_buf[k];
 }
 
 // Exclusive prefixes of the tiles' (payload words, extrema) in place, with the
@@ -1178,7 +1177,7 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2*
                          int sms, int* status, cudaStream_t st) {
     EncOut o{reinterpret_cast<uint32_t*>(out + lo.s1), out + lo.s2,
              reinterpret_cast<int32_t*>(out + lo.s4), scratch};
-    const uint32_t ntiles = (nb + TILE_BLOCKS - 1) / TILE_BLOCKS;   // one tile per CTA
+    const uint32_t ntiles = (nb + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;   // one tile per CTA
     if (topo) k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, status);
     else k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, status);
     k_enc_tile_scan<<<1, 1024, 0, st>>>(tcnt, ntiles, c, status);
