@@ -770,15 +770,22 @@ struct FusedArgs {
     int* status;
 };
 
+// S1 for tile t, one block per thread: the tile's payload is staged in shared
+// memory with coalesced loads; every thread finds its block's words from a
+// CTA-wide scan of the widths, rebuilds the 32 magnitudes from the planes with
+// register bit operations, applies the signs and the Lorenzo prefix, and
+// writes D0 through a padded shared buffer so that the stores are coalesced.
+// TOPO: the tile's extrema positions, in index order, go to cp_idx.
+constexpr int DT_ROW = 36;   // shared words per staged output row (conflict-free 16-byte accesses)
+
 template <bool TOPO>
 __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo, uint32_t t, uint32_t* s_pay,
                              uint32_t* s_w, uint32_t* s_cp, bool& corrupt) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint8_t* widths = A.in + lo.s2;
     const int32_t* firsts = reinterpret_cast<const int32_t*>(A.in + lo.s4);
     const uint32_t* pay = reinterpret_cast<const uint32_t*>(A.in + lo.s5);
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
-    const unsigned long long k = A.c->k_total;
     const float w_f = A.c->w_f;
     // the tile's payload is one contiguous word range: stage it with coalesced loads
     const unsigned long long P0 = A.pay_pre[t], P1 = A.pay_pre[t + 1];
@@ -786,58 +793,91 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
     if (P1 >= P0 && P1 - P0 <= (unsigned long long)DT_BLOCKS * 33 && P1 <= A.c->pay_words) len = (uint32_t)(P1 - P0);
     else corrupt = true;
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_pay[i] = __ldg(pay + P0 + i);
-    // lane j of a warp holds block blk0 + j: width, first value, its two label words
-    const uint32_t blk0 = t * DT_BLOCKS + warp * 32;
-    const uint32_t mb = blk0 + lane;
-    uint32_t my_w = 0, lw0 = 0, lw1 = 0;
-    int32_t my_first = 0;
-    if (mb < g.nb) {
-        my_w = __ldg(widths + mb);
-        my_first = __ldg(firsts + mb);
-        if (my_w > 32) my_w = 0;
-        if (TOPO) {
-            lw0 = label_word(labels, 2 * mb, g.n);
-            lw1 = label_word(labels, 2 * mb + 1, g.n);
+    const uint32_t b = t * DT_BLOCKS + threadIdx.x;   // this thread's block
+    uint32_t w = 0, xm = 0;
+    int32_t first = 0;
+    if (b < g.nb) {
+        w = __ldg(widths + b);
+        first = __ldg(firsts + b);
+        if (w > 32) w = 0;   // a damaged stream (the offset pre-pass flags it)
+        if (TOPO) {   // m = 01, M = 11: the low bit marks an extremum
+            xm = compact16(label_word(labels, 2 * b, g.n)) | compact16(label_word(labels, 2 * b + 1, g.n)) << 16;
         }
     }
-    const uint32_t ww = __reduce_add_sync(FULL, my_w ? 1u + my_w : 0u);
-    const uint32_t wcp = TOPO ? __reduce_add_sync(FULL, __popc(lw0 & 0x55555555u) + __popc(lw1 & 0x55555555u)) : 0u;
-    if (lane == 0) {
-        s_w[warp] = ww;
-        s_cp[warp] = wcp;
+    const uint32_t words = w ? 1u + w : 0u, ncp = __popc(xm);
+    uint32_t iw = words, ic = ncp;
+#pragma unroll
+    for (int of = 1; of < 32; of <<= 1) {
+        const uint32_t a0 = __shfl_up_sync(FULL, iw, of), a1 = __shfl_up_sync(FULL, ic, of);
+        if (lane >= (uint32_t)of) { iw += a0; ic += a1; }
+    }
+    if (lane == 31) {
+        s_w[warp] = iw;
+        s_cp[warp] = ic;
     }
     __syncthreads();
-    uint32_t woff = 0;
-    unsigned long long cpoff = A.cp_pre[t];
-    for (int w = 0; w < warp; w++) {
-        woff += s_w[w];
-        cpoff += s_cp[w];
+    uint32_t woff = iw - words, cpl = ic - ncp;
+    for (uint32_t k = 0; k < warp; k++) {
+        woff += s_w[k];
+        cpl += s_cp[k];
     }
-    const uint32_t lt = lanemask_lt();
-    for (int j = 0; j < 32; j++) {
-        const uint32_t b = blk0 + j;
-        if (b >= g.nb) break;
-        const uint32_t w = __shfl_sync(FULL, my_w, j);
-        const int32_t first = __shfl_sync(FULL, my_first, j);
-        int32_t q = first;
-        if (w) {
-            if (woff + 1 + w <= len) q = decode_block(s_pay, woff, w, first, lane);
-            else corrupt = true;
-            woff += 1 + w;
-        }
-        const uint32_t i = b * 32u + lane;
-        if (i < g.n) A.out[i] = dequantize(q, w_f);
-        if (TOPO) {
-            const uint32_t w0 = __shfl_sync(FULL, lw0, j), w1 = __shfl_sync(FULL, lw1, j);
-            const uint32_t word = lane < 16 ? w0 : w1;
-            const uint32_t mm = __ballot_sync(FULL, (word >> (2 * (lane & 15))) & 1u);   // m = 01, M = 11
-            if ((mm >> lane) & 1u) {
-                const unsigned long long pos = cpoff + __popc(mm & lt);
-                if (pos < k) A.cp_idx[pos] = i;
-                else corrupt = true;
+    // magnitudes from the planes, then signs and the Lorenzo prefix
+    uint32_t v[32];
+#pragma unroll
+    for (int e = 0; e < 32; e++) v[e] = 0u;
+    uint32_t sgn = 0;
+    if (w) {
+        if (woff + 1 + w <= len) {
+            sgn = s_pay[woff];
+            for (uint32_t p = w; p-- > 0;) {
+                const uint32_t wd = s_pay[woff + 1 + p];
+#pragma unroll
+                for (int e = 0; e < 32; e++) v[e] = (v[e] << 1) | ((wd >> e) & 1u);
             }
-            cpoff += __popc(mm);
+        } else {
+            corrupt = true;
         }
+    }
+    {
+        int32_t q = first;
+#pragma unroll
+        for (int e = 0; e < 32; e++) {
+            if (e) q += (sgn >> e) & 1u ? -(int32_t)v[e] : (int32_t)v[e];
+            v[e] = __float_as_uint(dequantize(q, w_f));
+        }
+    }
+    __syncthreads();   // the payload is consumed: the buffer stages the output rows
+    {
+        uint32_t* row = s_pay + threadIdx.x * DT_ROW;
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            *reinterpret_cast<uint4*>(row + 4 * k) = make_uint4(v[4 * k], v[4 * k + 1], v[4 * k + 2], v[4 * k + 3]);
+    }
+    if (TOPO && xm) {
+        const unsigned long long k = A.c->k_total;
+        unsigned long long pos = A.cp_pre[t] + cpl;
+        while (xm) {
+            const int e = __ffs(xm) - 1;
+            xm &= xm - 1;
+            if (pos < k) A.cp_idx[pos] = b * 32u + (uint32_t)e;
+            else corrupt = true;
+            pos++;
+        }
+    }
+    __syncthreads();
+    const uint64_t p0 = (uint64_t)t * (DT_BLOCKS * 32);
+    const uint64_t left = (uint64_t)g.n - p0;
+    if (left >= (uint64_t)(DT_BLOCKS * 32) && (reinterpret_cast<uintptr_t>(A.out) & 15u) == 0) {
+        float4* dst = reinterpret_cast<float4*>(A.out + p0);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const uint32_t idx = k * 256 + threadIdx.x;
+            dst[idx] = *reinterpret_cast<const float4*>(s_pay + (idx >> 3) * DT_ROW + (idx & 7) * 4);
+        }
+    } else {
+        const uint32_t np = left < (uint64_t)(DT_BLOCKS * 32) ? (uint32_t)left : (uint32_t)(DT_BLOCKS * 32);
+        for (uint32_t i = threadIdx.x; i < np; i += blockDim.x)
+            A.out[p0 + i] = __uint_as_float(s_pay[(i >> 5) * DT_ROW + (i & 31)]);
     }
 }
 
@@ -1011,7 +1051,7 @@ __device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* 
 }
 
 struct FusedSmem {
-    uint32_t pay[DT_BLOCKS * 33];   // S1: the tile's payload; S4: its saddle list
+    __align__(16) uint32_t pay[DT_BLOCKS * DT_ROW];   // S1: the tile's payload, then its output rows; S4: its saddle list
     uint32_t tile, cnt;
     Geo g;
     Layout lo;
