@@ -853,20 +853,66 @@ __device__ __forceinline__ SegCnt seg_op(SegCnt x, SegCnt y) {
     return SegCnt{x.h | y.h, y.h ? y.c : x.c + y.c};
 }
 
-__device__ __forceinline__ SegCnt rank_elem(const uint2* s, uint32_t i, int list, float r) {
-    uint32_t kk = s[i].x;
-    if (i == 0) return SegCnt{1, 1};
-    uint32_t kp = s[i - 1].x;
-    float v = key_float(list ? ~kk : kk), vp = key_float(list ? ~kp : kp);
-    bool seg = quantize(v, r) != quantize(vp, r);
-    return SegCnt{seg ? 1u : 0u, (seg || kk != kp) ? 1u : 0u};
+// The flags of entries b .. b + RANK_TILE / 256 - 1 (all < k), with each key
+// and its bin read once.
+constexpr int RANK_PER = RANK_TILE / 256;
+__device__ __forceinline__ void rank_elems(const uint2* s, uint32_t b, uint32_t k, int list, float r,
+                                           SegCnt (&el)[RANK_PER]) {
+    uint32_t kp = b ? s[b - 1].x : 0u;
+    int32_t qp = b ? quantize(key_float(list ? ~kp : kp), r) : 0;
+#pragma unroll
+    for (int j = 0; j < RANK_PER; j++) {
+        if (b + j >= k) {
+            el[j] = SegCnt{0, 0};
+            continue;
+        }
+        const uint32_t kk = s[b + j].x;
+        const int32_t q = quantize(key_float(list ? ~kk : kk), r);
+        if (b + j == 0) {
+            el[j] = SegCnt{1, 1};
+        } else {
+            const bool seg = q != qp;
+            el[j] = SegCnt{seg ? 1u : 0u, (seg || kk != kp) ? 1u : 0u};
+        }
+        kp = kk;
+        qp = q;
+    }
+}
+
+// Inclusive scan of a warp's values in lane order (seg_op is associative, not
+// commutative).
+__device__ __forceinline__ SegCnt warp_seg_scan(SegCnt x) {
+    const uint32_t lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t h = __shfl_up_sync(FULL, x.h, o), c = __shfl_up_sync(FULL, x.c, o);
+        if (lane >= (uint32_t)o) x = seg_op(SegCnt{h, c}, x);
+    }
+    return x;
+}
+
+// Exclusive scan of the CTA's 256 per-thread values after `pre`; also returns
+// the CTA total (after pre).  Uses s_tot[8].
+__device__ __forceinline__ SegCnt cta_seg_scan(SegCnt x, SegCnt pre, SegCnt* s_tot, SegCnt& total) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const SegCnt incl = warp_seg_scan(x);
+    SegCnt ex{__shfl_up_sync(FULL, incl.h, 1), __shfl_up_sync(FULL, incl.c, 1)};
+    if (lane == 0) ex = SegCnt{0, 0};
+    if (lane == 31) s_tot[warp] = incl;
+    __syncthreads();
+    SegCnt run = pre;
+    for (uint32_t k = 0; k < warp; k++) run = seg_op(run, s_tot[k]);
+    total = run;
+    for (uint32_t k = warp; k < 8; k++) total = seg_op(total, s_tot[k]);
+    __syncthreads();
+    return seg_op(run, ex);
 }
 
 // pass 1: aggregate per tile of RANK_TILE entries
 __global__ void __launch_bounds__(256) k_rank_tiles(const uint2* s0, const uint2* s1, const Ctrl* c,
                                                     uint2* agg, uint32_t agg_stride, int G,
                                                     const int* status) {
-    __shared__ SegCnt sh[256];
+    __shared__ SegCnt s_tot[8];
     if (*status) return;
     const int list = blockIdx.y;
     const uint2* s = list ? s1 : s0;
@@ -874,19 +920,15 @@ __global__ void __launch_bounds__(256) k_rank_tiles(const uint2* s0, const uint2
     const float r = c->r_f;
     const uint32_t ntiles = (uint32_t)cdiv(k, RANK_TILE);
     for (uint32_t t = blockIdx.x; t < ntiles; t += G) {
+        const uint32_t b = t * RANK_TILE + threadIdx.x * RANK_PER;
+        SegCnt el[RANK_PER];
+        rank_elems(s, b, k, list, r, el);
         SegCnt acc{0, 0};
-        const uint32_t b = t * RANK_TILE + threadIdx.x * (RANK_TILE / 256);
-#pragma unroll 4
-        for (int j = 0; j < RANK_TILE / 256; j++)
-            if (b + j < k) acc = seg_op(acc, rank_elem(s, b + j, list, r));
-        sh[threadIdx.x] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            SegCnt tot{0, 0};
-            for (int j = 0; j < 256; j++) tot = seg_op(tot, sh[j]);
-            agg[(size_t)list * agg_stride + t] = make_uint2(tot.h, tot.c);
-        }
-        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < RANK_PER; j++) acc = seg_op(acc, el[j]);
+        SegCnt tot;
+        cta_seg_scan(acc, SegCnt{0, 0}, s_tot, tot);
+        if (threadIdx.x == 0) agg[(size_t)list * agg_stride + t] = make_uint2(tot.h, tot.c);
     }
 }
 
@@ -926,7 +968,7 @@ __global__ void __launch_bounds__(256) k_rank_scan(uint2* agg, uint32_t agg_stri
 __global__ void __launch_bounds__(256) k_rank_scatter(const uint2* s0, const uint2* s1, const Ctrl* c,
                                                       const uint2* agg, uint32_t agg_stride, const uint2* tpre,
                                                       int32_t* delta, int G, const int* status) {
-    __shared__ SegCnt sh[256];
+    __shared__ SegCnt s_tot[8];
     if (*status) return;
     const int list = blockIdx.y;
     const uint2* s = list ? s1 : s0;
@@ -934,29 +976,17 @@ __global__ void __launch_bounds__(256) k_rank_scatter(const uint2* s0, const uin
     const float r = c->r_f;
     const uint32_t ntiles = (uint32_t)cdiv(k, RANK_TILE);
     for (uint32_t t = blockIdx.x; t < ntiles; t += G) {
+        const uint32_t b = t * RANK_TILE + threadIdx.x * RANK_PER;
+        SegCnt el[RANK_PER];
+        rank_elems(s, b, k, list, r, el);
         SegCnt acc{0, 0};
-        const uint32_t b = t * RANK_TILE + threadIdx.x * (RANK_TILE / 256);
-        SegCnt el[RANK_TILE / 256];
 #pragma unroll
-        for (int j = 0; j < RANK_TILE / 256; j++) {
-            el[j] = (b + j < k) ? rank_elem(s, b + j, list, r) : SegCnt{0, 0};
-            acc = seg_op(acc, el[j]);
-        }
-        sh[threadIdx.x] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint2 pre = agg[(size_t)list * agg_stride + t];
-            SegCnt run{pre.x, pre.y};
-            for (int j = 0; j < 256; j++) {
-                SegCnt v = sh[j];
-                sh[j] = run;
-                run = seg_op(run, v);
-            }
-        }
-        __syncthreads();
-        SegCnt run = sh[threadIdx.x];
+        for (int j = 0; j < RANK_PER; j++) acc = seg_op(acc, el[j]);
+        const uint2 pre = agg[(size_t)list * agg_stride + t];
+        SegCnt tot;
+        SegCnt run = cta_seg_scan(acc, SegCnt{pre.x, pre.y}, s_tot, tot);
 #pragma unroll
-        for (int j = 0; j < RANK_TILE / 256; j++) {
+        for (int j = 0; j < RANK_PER; j++) {
             if (b + j < k) {
                 run = seg_op(run, el[j]);
                 const uint32_t y = s[b + j].y;
