@@ -145,7 +145,31 @@ __device__ __forceinline__ uint32_t cd_fast(float v, float l, float r, bool xl, 
     return (uint32_t)(m | M) | ((uint32_t)(s | M) << 1);
 }
 
-template <bool TOPO, bool COUNTS, bool STATS>
+// cd_fast() for finite values, with the comparisons on the FMA pipe: for
+// finite u != v, fl(u - v) is nonzero with the sign of u - v (no flush to
+// zero, overflow keeps the sign) and fl(v - v) = +0, so with -0 folded to +0
+// beforehand (cz4) bit 31 of fl(u - v) is u < v.  The per-axis tests are then bitwise ANDs of sign words.  Used by
+// the compression pass only, where a non-finite field is rejected anyway.
+__device__ __forceinline__ uint32_t lt_bit(float u, float v) { return __float_as_uint(__fsub_rn(u, v)); }
+__device__ __forceinline__ float4 cz4(float4 v) {
+    return make_float4(__fadd_rn(v.x, 0.0f), __fadd_rn(v.y, 0.0f), __fadd_rn(v.z, 0.0f), __fadd_rn(v.w, 0.0f));
+}
+
+template <bool THREE>
+__device__ __forceinline__ uint32_t cd_sign(float v, float l, float r, bool xl, bool xr, float ym, float yp,
+                                            float zm, float zp) {
+    const float a = xl ? l : r, b = xr ? r : l;
+    const uint32_t Lx = lt_bit(a, v) & lt_bit(b, v), Hx = lt_bit(v, a) & lt_bit(v, b);
+    const uint32_t Ly = lt_bit(ym, v) & lt_bit(yp, v), Hy = lt_bit(v, ym) & lt_bit(v, yp);
+    const uint32_t Lz = THREE ? lt_bit(zm, v) & lt_bit(zp, v) : 0x80000000u;
+    const uint32_t Hz = THREE ? lt_bit(v, zm) & lt_bit(v, zp) : 0x80000000u;
+    const uint32_t m = Hx & Hy & Hz, M = Lx & Ly & Lz;
+    uint32_t s = (Hx | Lx) & (Hy | Ly) & (Hz | Lz) & ~m & ~M;
+    if (!(xl && xr)) s = 0u;
+    return ((m | M) >> 31) | (((s | M) >> 31) << 1);
+}
+
+template <bool TOPO, bool COUNTS, bool STATS, bool THREE>
 __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ a, const Geo g, Ctrl* c,
                                                       uint32_t* __restrict__ labels,
                                                       unsigned long long* counts) {
@@ -153,7 +177,7 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
     const uint32_t nchunks = (g.n + 127) / 128;
     const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-    const bool three = g.ndim == 3;
+    constexpr bool three = THREE;
     // coordinates of this lane's first quad, and the grid stride in (x, y, z) digits
     uint32_t x, y, z;
     {
@@ -166,7 +190,7 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
     const uint32_t sy = (uint32_t)(sr % g.ny);
     const uint32_t sz = (uint32_t)(sr / g.ny);
     float vmin = __int_as_float(0x7F800000), vmax = __int_as_float(0xFF800000);
-    bool bad = false;
+    float fin = 0.0f;   // sum of (v - v): +0 while every value is finite, NaN after an inf or NaN
     unsigned long long cm = 0, cs = 0, cM = 0;
     GlobalVal val{a};
     for (uint32_t ch = warp0; ch < nchunks; ch += nwarps) {
@@ -177,8 +201,8 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
         if (STATS && active) {
             vmin = fminf(fminf(vmin, v.x), fminf(v.y, fminf(v.z, v.w)));
             vmax = fmaxf(fmaxf(vmax, v.x), fmaxf(v.y, fmaxf(v.z, v.w)));
-            bad |= !(fabsf(v.x) <= 3.402823466e38f) || !(fabsf(v.y) <= 3.402823466e38f) ||
-                   !(fabsf(v.z) <= 3.402823466e38f) || !(fabsf(v.w) <= 3.402823466e38f);
+            fin = __fadd_rn(fin, __fadd_rn(__fadd_rn(__fsub_rn(v.x, v.x), __fsub_rn(v.y, v.y)),
+                                           __fadd_rn(__fsub_rn(v.z, v.z), __fsub_rn(v.w, v.w))));
         }
         if (TOPO) {
             float left = __shfl_up_sync(FULL, v.w, 1);
@@ -197,10 +221,20 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
                         zm = __ldg(reinterpret_cast<const float4*>(a + i0 - g.nxy));
                         zp = __ldg(reinterpret_cast<const float4*>(a + i0 + g.nxy));
                     }
-                    bits = cd_fast(v.x, left, v.y, xl, true, ym.x, yp.x, zm.x, zp.x, three) |
-                           cd_fast(v.y, v.x, v.z, true, true, ym.y, yp.y, zm.y, zp.y, three) << 2 |
-                           cd_fast(v.z, v.y, v.w, true, true, ym.z, yp.z, zm.z, zp.z, three) << 4 |
-                           cd_fast(v.w, v.z, right, true, xr, ym.w, yp.w, zm.w, zp.w, three) << 6;
+                    if (STATS) {
+                        // -0 - (+0) = -0 would read as "less": fold every -0 to +0 first
+                        const float4 c = cz4(v), cym = cz4(ym), cyp = cz4(yp);
+                        const float4 czm = THREE ? cz4(zm) : cym, czp = THREE ? cz4(zp) : cyp;
+                        const float cl = __fadd_rn(left, 0.0f), cr = __fadd_rn(right, 0.0f);
+                        bits = cd_sign<THREE>(c.x, cl, c.y, xl, true, cym.x, cyp.x, czm.x, czp.x) |
+                               cd_sign<THREE>(c.y, c.x, c.z, true, true, cym.y, cyp.y, czm.y, czp.y) << 2 |
+                               cd_sign<THREE>(c.z, c.y, c.w, true, true, cym.z, cyp.z, czm.z, czp.z) << 4 |
+                               cd_sign<THREE>(c.w, c.z, cr, true, xr, cym.w, cyp.w, czm.w, czp.w) << 6;
+                    } else
+                        bits = cd_fast(v.x, left, v.y, xl, true, ym.x, yp.x, zm.x, zp.x, three) |
+                               cd_fast(v.y, v.x, v.z, true, true, ym.y, yp.y, zm.y, zp.y, three) << 2 |
+                               cd_fast(v.z, v.y, v.w, true, true, ym.z, yp.z, zm.z, zp.z, three) << 4 |
+                               cd_fast(v.w, v.z, right, true, xr, ym.w, yp.w, zm.w, zp.w, three) << 6;
                 } else {
                     const float vv[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -238,7 +272,7 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
         uint32_t kmin = vmax >= vmin ? ~ord_key(vmin) : 0u;
         kmax = __reduce_max_sync(FULL, kmax);
         kmin = __reduce_max_sync(FULL, kmin);
-        const bool anybad = __any_sync(FULL, bad);
+        const bool anybad = __any_sync(FULL, isnan(fin));
         const unsigned long long sad = TOPO ? __reduce_add_sync(FULL, (uint32_t)cs) : 0u;
         if (lane == 0) {
             if (kmax) atomicMax(&c->max_key, kmax);
@@ -1131,8 +1165,10 @@ void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bo
         const uint32_t per_cta_chunks = (uint32_t)th / 32;   // one 128-point chunk per warp
         uint32_t blocks = hmin<uint32_t>((g.n / 128 + per_cta_chunks - 1) / per_cta_chunks + 1,
                                          (uint32_t)sms * (uint32_t)g_tuning.cd_blocks_per_sm);
-        if (topo) k_range_cd_vec<true, false, true><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
-        else k_range_cd_vec<false, false, true><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
+        const bool three = g.ndim == 3;
+        if (topo && three) k_range_cd_vec<true, false, true, true><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
+        else if (topo) k_range_cd_vec<true, false, true, false><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
+        else k_range_cd_vec<false, false, true, false><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
         return;
     }
     uint32_t nchunks = (g.n + 511) / 512;
@@ -1146,11 +1182,14 @@ void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsi
                             int sms, cudaStream_t st) {
     if (vec_ok(a, g)) {
         uint32_t blocks = hmin<uint32_t>((g.n / 128 + 7) / 8 + 1, (uint32_t)sms * 8);
+        const bool three = g.ndim == 3;
         if (counts) {
-            k_range_cd_vec<true, true, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, counts);
+            if (three) k_range_cd_vec<true, true, false, true><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, counts);
+            else k_range_cd_vec<true, true, false, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, counts);
             k_count_regular<<<1, 1, 0, st>>>(g.n, counts);
         } else {
-            k_range_cd_vec<true, false, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, nullptr);
+            if (three) k_range_cd_vec<true, false, false, true><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, nullptr);
+            else k_range_cd_vec<true, false, false, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, nullptr);
         }
         return;
     }
