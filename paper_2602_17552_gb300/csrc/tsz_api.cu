@@ -230,7 +230,6 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     uint8_t* o = reinterpret_cast<uint8_t*>(out);
     Ctrl* c = reinterpret_cast<Ctrl*>(ws + w.ctrl);
     uint2* tcnt = reinterpret_cast<uint2*>(ws + w.desc);
-    Desc* rdesc = reinterpret_cast<Desc*>(ws + w.rdesc);
     uint2* listM = reinterpret_cast<uint2*>(ws + w.listM);
     uint2* listm = reinterpret_cast<uint2*>(ws + w.listm);
     const bool topo = !(p.flags & TOPOSZP_NO_TOPO);
@@ -261,8 +260,9 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
         launch_ranks(c, listM, listm, reinterpret_cast<uint2*>(ws + w.tmpM),
                      reinterpret_cast<uint2*>(ws + w.tmpm), sw, reinterpret_cast<uint2*>(ws + w.agg),
                      w.agg_stride, tcnt, reinterpret_cast<int32_t*>(ws + w.delta), w.G, sms, status, st);
-        launch_encode_ranks(reinterpret_cast<int32_t*>(ws + w.delta), c, rdesc, o, w.rank_tiles, sms,
-                            status, st);
+        // the rank payload slots reuse the sort's buffers (free again by now)
+        launch_encode_ranks(reinterpret_cast<int32_t*>(ws + w.delta), c, reinterpret_cast<uint2*>(ws + w.rdesc),
+                            reinterpret_cast<uint32_t*>(ws + w.tmpM), o, g.n, sms, status, st);
     }
     stage(3, st);
     launch_finalize(c, o, out_size, p.rbf_k, p.rbf_sigma, status, st);

@@ -182,6 +182,44 @@ __device__ __forceinline__ uint32_t compact16(uint32_t x) {
     return x;
 }
 
+// Exclusive scan of pairs (a_i, b_i), i < cnt, by one CTA of 1024 threads:
+// coalesced chunks of 1024 entries, a shuffle scan per warp, one shared step
+// per chunk, running 64-bit carries.  load(i) -> uint2; store(i, pa, pb).
+// Returns the totals.  Shared scratch: s_w[32] pairs.
+template <class Load, class Store>
+__device__ void cta_scan_pairs(uint32_t cnt, Load load, Store store, unsigned long long (*s_w)[2],
+                               unsigned long long& tot_a, unsigned long long& tot_b) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned long long ca = 0, cb = 0;
+    uint2 nxt = threadIdx.x < cnt ? load(threadIdx.x) : make_uint2(0u, 0u);
+    for (uint32_t base = 0; base < cnt; base += 1024) {
+        const uint32_t i = base + threadIdx.x;
+        const uint2 v = nxt;
+        nxt = i + 1024 < cnt ? load(i + 1024) : make_uint2(0u, 0u);   // next chunk in flight
+        unsigned long long ia = v.x, ib = v.y;
+#pragma unroll
+        for (int of = 1; of < 32; of <<= 1) {
+            const unsigned long long ta = __shfl_up_sync(0xFFFFFFFFu, ia, of), tb = __shfl_up_sync(0xFFFFFFFFu, ib, of);
+            if (lane >= (uint32_t)of) { ia += ta; ib += tb; }
+        }
+        if (lane == 31) { s_w[warp][0] = ia; s_w[warp][1] = ib; }
+        __syncthreads();
+        unsigned long long pa = ca, pb = cb, ta = 0, tb = 0;
+        for (uint32_t k = 0; k < 32; k++) {
+            const unsigned long long xa = s_w[k][0], xb = s_w[k][1];
+            if (k < warp) { pa += xa; pb += xb; }
+            ta += xa;
+            tb += xb;
+        }
+        __syncthreads();
+        if (i < cnt) store(i, pa + ia - v.x, pb + ib - v.y);
+        ca += ta;
+        cb += tb;
+    }
+    tot_a = ca;
+    tot_b = cb;
+}
+
 // spread the low 16 bits of x to the even bit positions
 __device__ __forceinline__ uint32_t spread16(uint32_t x) {
     x &= 0xFFFFu;

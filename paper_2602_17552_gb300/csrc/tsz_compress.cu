@@ -530,38 +530,19 @@ __global__ void __launch_bounds__(256, 3) k_encode_field(const float* __restrict
 // consecutive tiles per thread.
 __global__ void __launch_bounds__(1024) k_enc_tile_scan(uint2* tcnt, uint32_t ntiles, Ctrl* c,
                                                         const int* status) {
-    __shared__ unsigned long long sw[1024], sc[1024];
+    __shared__ unsigned long long s_w[32][2];
     if (*status) return;
-    const uint32_t per = (ntiles + 1023) / 1024;
-    const uint32_t b = threadIdx.x * per, e = min(ntiles, b + per);
-    unsigned long long aw = 0, ac = 0;
-    for (uint32_t i = b; i < e; i++) {
-        const uint2 v = tcnt[i];
-        aw += v.x;
-        ac += v.y;
-    }
-    sw[threadIdx.x] = aw;
-    sc[threadIdx.x] = ac;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        const unsigned long long tw = threadIdx.x >= o ? sw[threadIdx.x - o] : 0;
-        const unsigned long long tc = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
-        __syncthreads();
-        sw[threadIdx.x] += tw;
-        sc[threadIdx.x] += tc;
-        __syncthreads();
-    }
-    unsigned long long rw = sw[threadIdx.x] - aw, rc = sc[threadIdx.x] - ac;
-    for (uint32_t i = b; i < e; i++) {
-        const uint2 v = tcnt[i];
-        tcnt[i] = make_uint2((uint32_t)rw, (uint32_t)rc);
-        rw += v.x;
-        rc += v.y;
-    }
-    if (threadIdx.x == 1023) {
-        tcnt[ntiles] = make_uint2((uint32_t)sw[1023], (uint32_t)sc[1023]);
-        c->pay_words = sw[1023];
-        c->k_total = sc[1023];
+    unsigned long long tw, tc;
+    cta_scan_pairs(
+        ntiles, [&](uint32_t i) { return tcnt[i]; },
+        [&](uint32_t i, unsigned long long pw, unsigned long long pc) {
+            tcnt[i] = make_uint2((uint32_t)pw, (uint32_t)pc);
+        },
+        s_w, tw, tc);
+    if (threadIdx.x == 0) {
+        tcnt[ntiles] = make_uint2((uint32_t)tw, (uint32_t)tc);
+        c->pay_words = tw;
+        c->k_total = tc;
     }
 }
 
@@ -580,111 +561,127 @@ __global__ void __launch_bounds__(256) k_enc_copy(const uint32_t* __restrict__ s
 }
 
 // Rank-sequence encoder: the same codec on the delta sequence (Section IV-A:
-// B + LZ and BE again, no QZ).  Length and output offsets are read from the
-// control block, so the launch does not depend on data-dependent sizes.
-__global__ void __launch_bounds__(256) k_encode_ranks(const int32_t* __restrict__ delta, Ctrl* c,
-                                                      Desc* desc, uint8_t* out, int* status) {
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_w[TILE_WARPS];
-    __shared__ unsigned long long s_pre_w;
-    __shared__ uint32_t s_cbits[2];
+// B + LZ and BE again, no QZ), organised like the field encoder: 8192-delta
+// tiles, one block per thread, payload to per-tile scratch slots, then a tile
+// scan (k_rank_tile_scan) and a copy (k_rank_copy).  The sequence length and
+// the section offsets are read from the control block, so the launches do not
+// depend on data-dependent sizes.
+__global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restrict__ delta, Ctrl* c, uint2* tcnt,
+                                                         uint32_t* scratch, uint8_t* out, int* status) {
+    __shared__ __align__(16) uint32_t s_buf[ENC_TILE_BLOCKS * ENC_ROW];
+    __shared__ uint32_t s_wsum[8];
     if (*status) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const uint64_t k = c->k_total;
     const uint32_t nbd = (uint32_t)cdiv(k, L);
-    const uint32_t ntiles = (nbd + TILE_BLOCKS - 1) / TILE_BLOCKS;
-    const uint32_t ncw = (nbd + 31) / 32;
+    const uint32_t ntiles = (nbd + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;
     Layout lo;
     make_layout(c->g.n, c->g.nb, true, c->pay_words, k, 0, lo);
     uint32_t* cbits = reinterpret_cast<uint32_t*>(out + lo.r1);
     uint8_t* width = out + lo.r2;
     int32_t* first = reinterpret_cast<int32_t*>(out + lo.r4);
-    uint32_t* pay = reinterpret_cast<uint32_t*>(out + lo.r5);
-    if (threadIdx.x < 2) s_cbits[threadIdx.x] = 0;
-    while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_rank, 1u);
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t p0 = (uint64_t)tile * (ENC_TILE_BLOCKS * 32);
+        const uint64_t left = k - p0;
+        const uint32_t np = left < (uint64_t)(ENC_TILE_BLOCKS * 32) ? (uint32_t)left : (uint32_t)(ENC_TILE_BLOCKS * 32);
+        for (uint32_t i = t; i < np; i += 256) s_buf[(i >> 5) * ENC_ROW + (i & 31)] = (uint32_t)__ldcs(delta + p0 + i);
         __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t blk0 = tile * TILE_BLOCKS + warp * BPW;
-        int32_t dreg[BPW];
-        uint32_t my_w = 0;
-        int32_t my_first = 0;
-        uint32_t wwords = 0;
+        const uint32_t b = tile * ENC_TILE_BLOCKS + t;
+        uint32_t m[32];
+        uint32_t sgn = 0, orr = 0;
+        int32_t f = 0;
+        if (b < nbd) {
+            const uint32_t* row = s_buf + t * ENC_ROW;
+            const uint64_t nv64 = k - (uint64_t)b * 32u;
+            const uint32_t nvalid = nv64 < 32 ? (uint32_t)nv64 : 32u;
+            int32_t prev = 0;
 #pragma unroll
-        for (int j = 0; j < BPW; j++) {
-            const uint32_t b = blk0 + j;
-            dreg[j] = 0;
-            if (b < nbd) {
-                const uint64_t i = (uint64_t)b * 32u + lane;
-                const uint32_t nvalid = (uint32_t)min((uint64_t)32, k - (uint64_t)b * 32u);
-                int32_t q = (lane < nvalid) ? delta[i] : 0;
-                int32_t qlast = __shfl_sync(FULL, q, nvalid - 1);
-                if (lane >= nvalid) q = qlast;
-                int32_t prev = __shfl_up_sync(FULL, q, 1);
-                int32_t d = lane ? q - prev : 0;
-                uint32_t m = (uint32_t)(d < 0 ? -d : d);
-                uint32_t w = 32u - __clz(__reduce_max_sync(FULL, m));
-                int32_t f = __shfl_sync(FULL, q, 0);
-                if (lane == j) {
-                    my_w = w;
-                    my_first = f;
-                }
-                dreg[j] = d;
-                wwords += w ? 1u + w : 0u;
+            for (int e = 0; e < 32; e++) {
+                int32_t q = (int32_t)row[e];
+                if (e > 0 && (uint32_t)e >= nvalid) q = prev;   // the tail block repeats its last value
+                const int32_t d = e ? q - prev : 0;
+                if (e == 0) f = q;
+                if (d < 0) sgn |= 1u << e;
+                m[e] = (uint32_t)(d < 0 ? -d : d);
+                orr |= m[e];
+                prev = q;
             }
         }
-        if (lane == 0) s_w[warp] = wwords;
+        const uint32_t w = 32u - __clz(orr);
+        const uint32_t words = (b < nbd && w) ? 1u + w : 0u;
+        uint32_t iw = words;
+#pragma unroll
+        for (int of = 1; of < 32; of <<= 1) {
+            const uint32_t a0 = __shfl_up_sync(FULL, iw, of);
+            if (lane >= (uint32_t)of) iw += a0;
+        }
+        if (lane == 31) s_wsum[warp] = iw;
+        __syncthreads();   // also: every staged value has been read
+        uint32_t ow = iw - words, tw = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t v = s_wsum[q];
+            if (q < (int)warp) ow += v;
+            tw += v;
+        }
+        if (t == 0) tcnt[tile] = make_uint2(tw, 0u);
+        if (words) {
+            uint32_t* dst = s_buf + ow;
+            dst[0] = sgn;
+            for (uint32_t p = 0; p < w; p++) {
+                uint32_t wd = 0;
+#pragma unroll
+                for (int e = 0; e < 32; e++) wd |= ((m[e] >> p) & 1u) << e;
+                dst[1 + p] = wd;
+            }
+        }
+        if (b < nbd) {
+            width[b] = (uint8_t)w;
+            first[b] = f;
+        }
         {
-            uint32_t cb = __ballot_sync(FULL, lane < BPW && blk0 + lane < nbd && my_w == 0) & 0xFFu;
-            if (lane == 0 && cb) atomicOr(&s_cbits[warp >> 2], cb << ((warp & 3) * 8));
+            const uint32_t cb = __ballot_sync(FULL, b < nbd && w == 0);
+            if (lane == 0 && (b >> 5) < (nbd + 31) / 32) cbits[b >> 5] = cb;
         }
         __syncthreads();
-        if (warp == 0) {
-            uint32_t vw = lane < TILE_WARPS ? s_w[lane] : 0, iw = vw;
-#pragma unroll
-            for (int o = 1; o < TILE_WARPS; o <<= 1) {
-                uint32_t t0 = __shfl_up_sync(FULL, iw, o);
-                if (lane >= o) iw += t0;
-            }
-            uint32_t tw = __shfl_sync(FULL, iw, TILE_WARPS - 1);
-            unsigned long long pw, pc;
-            lookback(desc, tile, tw, 0, pw, pc, status);
-            if (lane < TILE_WARPS) s_w[lane] = iw - vw;
-            if (lane == 0) {
-                s_pre_w = pw;
-                if (tile == ntiles - 1) c->rank_words = pw + tw;
-            }
-        }
+        uint32_t* slot = scratch + (size_t)tile * TILE_PAY;
+        for (uint32_t q = t; q < tw; q += 256) slot[q] = s_buf[q];
         __syncthreads();
-        unsigned long long woff = s_pre_w + s_w[warp];
-#pragma unroll
-        for (int j = 0; j < BPW; j++) {
-            const uint32_t b = blk0 + j;
-            if (b >= nbd) break;
-            const uint32_t w = __shfl_sync(FULL, my_w, j);
-            if (w) {
-                const int32_t d = dreg[j];
-                const uint32_t m = (uint32_t)(d < 0 ? -d : d);
-                uint32_t word = __ballot_sync(FULL, d < 0);
-                for (uint32_t p = 0; p < w; p++) {
-                    uint32_t bp = __ballot_sync(FULL, (m >> p) & 1u);
-                    if (lane == p + 1) word = bp;
-                }
-                if (lane <= w) pay[woff + lane] = word;
-                woff += 1 + w;
-            }
-        }
-        if (lane < BPW && blk0 + lane < nbd) {
-            width[blk0 + lane] = (uint8_t)my_w;
-            first[blk0 + lane] = my_first;
-        }
-        __syncthreads();
-        if (threadIdx.x < 2) {
-            uint32_t wi = tile * 2 + threadIdx.x;
-            if (wi < ncw) cbits[wi] = s_cbits[threadIdx.x];
-            s_cbits[threadIdx.x] = 0;
-        }
+    }
+}
+
+// Tile prefixes of the rank payload (tiles of the delta sequence); sets rank_words.
+__global__ void __launch_bounds__(1024) k_rank_tile_scan(uint2* tcnt, Ctrl* c, const int* status) {
+    __shared__ unsigned long long s_w[32][2];
+    if (*status) return;
+    const uint32_t nbd = (uint32_t)cdiv(c->k_total, L);
+    const uint32_t ntiles = (nbd + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;
+    unsigned long long tw, tz;
+    cta_scan_pairs(
+        ntiles, [&](uint32_t i) { return tcnt[i]; },
+        [&](uint32_t i, unsigned long long pw, unsigned long long) { tcnt[i] = make_uint2((uint32_t)pw, 0u); },
+        s_w, tw, tz);
+    if (threadIdx.x == 0) {
+        tcnt[ntiles] = make_uint2((uint32_t)tw, 0u);
+        c->rank_words = tw;
+    }
+}
+
+// Rank payload slots to the rank payload section (a warp per tile).
+__global__ void __launch_bounds__(256) k_rank_copy(const uint32_t* __restrict__ scratch, const uint2* tpre,
+                                                   const Ctrl* c, uint8_t* out, const int* status) {
+    if (*status) return;
+    const int lane = threadIdx.x & 31;
+    const uint64_t k = c->k_total;
+    const uint32_t nbd = (uint32_t)cdiv(k, L);
+    const uint32_t ntiles = (nbd + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;
+    Layout lo;
+    make_layout(c->g.n, c->g.nb, true, c->pay_words, k, 0, lo);
+    uint32_t* pay = reinterpret_cast<uint32_t*>(out + lo.r5);
+    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += (gridDim.x * blockDim.x) >> 5) {
+        const uint32_t p0 = tpre[t].x, cnt = tpre[t + 1].x - p0;
+        const uint32_t* src = scratch + (size_t)t * TILE_PAY;
+        for (uint32_t q = lane; q < cnt; q += 32) pay[p0 + q] = __ldcs(src + q);
     }
 }
 
@@ -759,17 +756,24 @@ __global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s
     }
 }
 
-// exclusive scan of each 256-digit histogram -> digit bases
-__global__ void k_os_bases(const uint32_t* ghist, uint32_t* base, const int* status) {
+// exclusive scan of each 256-digit histogram -> digit bases (a CTA per row)
+__global__ void __launch_bounds__(256) k_os_bases(const uint32_t* ghist, uint32_t* base, const int* status) {
+    __shared__ uint32_t s_w[8];
     if (*status) return;
     const int row = blockIdx.x;   // list * 4 + pass
-    if (threadIdx.x == 0) {
-        uint32_t run = 0;
-        for (int d = 0; d < 256; d++) {
-            base[row * 256 + d] = run;
-            run += ghist[row * 256 + d];
-        }
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t v = ghist[row * 256 + threadIdx.x];
+    uint32_t inc = v;
+#pragma unroll
+    for (int of = 1; of < 32; of <<= 1) {
+        const uint32_t t = __shfl_up_sync(FULL, inc, of);
+        if (lane >= (uint32_t)of) inc += t;
     }
+    if (lane == 31) s_w[warp] = inc;
+    __syncthreads();
+    uint32_t pre = 0;
+    for (uint32_t k = 0; k < warp; k++) pre += s_w[k];
+    base[row * 256 + threadIdx.x] = pre + inc - v;
 }
 
 __global__ void __launch_bounds__(256) k_os_pass(const uint2* s0, const uint2* s1, uint2* d0, uint2* d1,
@@ -1262,7 +1266,7 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
     uint32_t hg = hmin<uint32_t>((uint32_t)cdiv((uint64_t)max_tiles * OS_TILE, 256), (uint32_t)sms * 4);
     if (hg == 0) hg = 1;
     k_os_hist<<<dim3(hg, 2), 256, 0, st>>>(listM, listm, c, sw.hist, sw.desc_a, sw.desc_b, sw.stride, status);
-    k_os_bases<<<8, 32, 0, st>>>(sw.hist, sw.base, status);
+    k_os_bases<<<8, 256, 0, st>>>(sw.hist, sw.base, status);
     uint2 *a0 = listM, *a1 = listm, *b0 = tmpM, *b1 = tmpm;
     const uint32_t pg = hmin<uint32_t>(max_tiles, (uint32_t)sms * 4);
     for (int pass = 0; pass < 4; pass++) {
@@ -1280,11 +1284,15 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
     k_rank_scatter<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, tpre, delta, G, status);
 }
 
-void launch_encode_ranks(const int32_t* delta, Ctrl* c, Desc* desc, uint8_t* out, uint32_t max_tiles,
-                         int sms, int* status, cudaStream_t st) {
-    uint32_t grid = hmin<uint32_t>(max_tiles, (uint32_t)sms * 6);
+void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* scratch, uint8_t* out,
+                         uint64_t max_k, int sms, int* status, cudaStream_t st) {
+    const uint32_t max_tiles = (uint32_t)cdiv(cdiv(max_k, L), ENC_TILE_BLOCKS);
+    uint32_t grid = hmin<uint32_t>(max_tiles, (uint32_t)sms * 3);
     if (grid == 0) grid = 1;
-    k_encode_ranks<<<grid, 256, 0, st>>>(delta, c, desc, out, status);
+    k_encode_ranks<<<grid, 256, 0, st>>>(delta, c, tcnt, scratch, out, status);
+    k_rank_tile_scan<<<1, 1024, 0, st>>>(tcnt, c, status);
+    uint32_t cg = hmin<uint32_t>((max_tiles + 7) / 8, (uint32_t)sms * 16);
+    k_rank_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, c, out, status);
 }
 
 void launch_count_saddles(const uint32_t* labels, Ctrl* c, uint32_t n, int sms, int* status,

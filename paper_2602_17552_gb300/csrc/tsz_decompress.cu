@@ -624,60 +624,22 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
 // 16 independent loads.
 __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t* tile_w, const uint32_t* tile_c,
                                                         unsigned long long* pay_pre, uint32_t* cp_pre, int* status) {
-    __shared__ unsigned long long sw[1024];
-    __shared__ unsigned long long sc[1024];
+    __shared__ unsigned long long s_w[32][2];
     if (*status) return;
     const uint32_t ntiles = (c->g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
-    const uint32_t per = (ntiles + 1023) / 1024;
-    const uint32_t b = threadIdx.x * per, e = hmin<uint32_t>(ntiles, b + per);
-    unsigned long long aw = 0, ac = 0;
-    for (uint32_t i0 = b; i0 < e; i0 += 16) {
-        uint32_t vw[16], vc[16];
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            vw[j] = i0 + j < e ? tile_w[i0 + j] : 0u;
-            vc[j] = i0 + j < e ? tile_c[i0 + j] : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            aw += vw[j];
-            ac += vc[j];
-        }
-    }
-    sw[threadIdx.x] = aw;
-    sc[threadIdx.x] = ac;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-        unsigned long long tw = threadIdx.x >= o ? sw[threadIdx.x - o] : 0;
-        unsigned long long tc = threadIdx.x >= o ? sc[threadIdx.x - o] : 0;
-        __syncthreads();
-        sw[threadIdx.x] += tw;
-        sc[threadIdx.x] += tc;
-        __syncthreads();
-    }
-    unsigned long long rw = sw[threadIdx.x] - aw, rc = sc[threadIdx.x] - ac;
-    for (uint32_t i0 = b; i0 < e; i0 += 16) {
-        uint32_t vw[16], vc[16];
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            vw[j] = i0 + j < e ? tile_w[i0 + j] : 0u;
-            vc[j] = i0 + j < e ? tile_c[i0 + j] : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            if (i0 + j < e) {
-                pay_pre[i0 + j] = rw;
-                cp_pre[i0 + j] = (uint32_t)rc;
-            }
-            rw += vw[j];
-            rc += vc[j];
-        }
-    }
-    if (threadIdx.x == 1023) {
-        pay_pre[ntiles] = sw[1023];
-        cp_pre[ntiles] = (uint32_t)sc[1023];
+    unsigned long long tw, tc;
+    cta_scan_pairs(
+        ntiles, [&](uint32_t i) { return make_uint2(tile_w[i], tile_c[i]); },
+        [&](uint32_t i, unsigned long long pw, unsigned long long pc) {
+            pay_pre[i] = pw;
+            cp_pre[i] = (uint32_t)pc;
+        },
+        s_w, tw, tc);
+    if (threadIdx.x == 0) {
+        pay_pre[ntiles] = tw;
+        cp_pre[ntiles] = (uint32_t)tc;
         const bool topo = !(c->flags & FLAG_NO_TOPO);
-        if (sw[1023] != c->pay_words || (topo && sc[1023] != c->k_total)) set_status(status, ST_CORRUPT);
+        if (tw != c->pay_words || (topo && tc != c->k_total)) set_status(status, ST_CORRUPT);
     }
 }
 

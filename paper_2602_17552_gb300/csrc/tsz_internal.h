@@ -48,8 +48,8 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2*
 void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, const SortWs& sw,
                   uint2* agg, uint32_t agg_stride, const uint2* tpre, int32_t* delta, int G, int sms, int* status,
                   cudaStream_t st);
-void launch_encode_ranks(const int32_t* delta, Ctrl* c, Desc* desc, uint8_t* out, uint32_t max_tiles,
-                         int sms, int* status, cudaStream_t st);
+void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* scratch, uint8_t* out,
+                         uint64_t max_k, int sms, int* status, cudaStream_t st);
 void launch_count_saddles(const uint32_t* labels, Ctrl* c, uint32_t n, int sms, int* status,
                           cudaStream_t st);
 void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, float rbf_sigma,
