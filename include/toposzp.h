@@ -171,8 +171,8 @@ uint64_t toposzp_noalloc_max_points(void);
  * fields keep the defaults.  Returns INVALID_ARG for unsupported values.
  *   cd_threads           threads per CTA of the range + CD pass: 128, 256, 512
  *   cd_blocks_per_sm     its CTAs per SM: 1..32 (default 8)
- *   rounds_blocks_per_sm CTAs per SM of the cooperative saddle rounds: 1..4
- *                        (default: as many as fit, at most 4)
+ *   rounds_blocks_per_sm CTAs per SM of the cooperative saddle rounds, which
+ *                        run 1024 threads per SM: 1, 2 or 4 (default 1)
  *   dec_slack_tiles      extra lag, in 8192-point tiles, between the stages of
  *                        the fused decoder: 1..65536 (default: a quarter of its
  *                        resident CTAs)

@@ -19,7 +19,7 @@ from . import _lib, batch, codec, synth
 
 CACHE = os.environ.get("TOPOSZP_TUNING", os.path.join(os.path.expanduser("~"), ".cache", "toposzp",
                                                        "tuning.json"))
-DEFAULT = {"cd_threads": 256, "cd_blocks_per_sm": 8, "rounds_blocks_per_sm": 4, "dec_slack_tiles": 0,
+DEFAULT = {"cd_threads": 256, "cd_blocks_per_sm": 8, "rounds_blocks_per_sm": 1, "dec_slack_tiles": 0,
            "batch_branches": 8}
 
 

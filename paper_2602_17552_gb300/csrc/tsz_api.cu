@@ -358,7 +358,9 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     if (t->cd_threads && t->cd_threads != 128 && t->cd_threads != 256 && t->cd_threads != 512)
         return TOPOSZP_ERR_INVALID_ARG;
     if (t->cd_blocks_per_sm < 0 || t->cd_blocks_per_sm > 32) return TOPOSZP_ERR_INVALID_ARG;
-    if (t->rounds_blocks_per_sm < 0 || t->rounds_blocks_per_sm > 4) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->rounds_blocks_per_sm != 0 && t->rounds_blocks_per_sm != 1 && t->rounds_blocks_per_sm != 2 &&
+        t->rounds_blocks_per_sm != 4)
+        return TOPOSZP_ERR_INVALID_ARG;
     if (t->dec_slack_tiles < 0 || t->dec_slack_tiles > 65536) return TOPOSZP_ERR_INVALID_ARG;
     if (t->saddle_records < -1 || t->saddle_records > 1) return TOPOSZP_ERR_INVALID_ARG;
     Tuning u;

@@ -1096,7 +1096,7 @@ __global__ void __launch_bounds__(256, 4) k_decode_fused(FusedArgs A) {
 // RS^ colour rounds over the lost-saddle list (cooperative: the grid syncs
 // between the evaluation and the write of every colour).  The list is first
 // bucketed by colour so that each round touches only its own candidates.
-__global__ void __launch_bounds__(256, 4) k_saddle_rounds(const uint8_t* __restrict__ in, Ctrl* c, float* out,
+__global__ void __launch_bounds__(1024, 1) k_saddle_rounds(const uint8_t* __restrict__ in, Ctrl* c, float* out,
                                                        const uint32_t* sad, uint32_t* sadb, float* sadv,
                                                        uint32_t sad_cap, uint32_t* rec, uint32_t rec_cap,
                                                        int* status) {
@@ -1237,20 +1237,22 @@ void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned 
 cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, uint32_t* sadb,
                                  float* sadv, uint32_t sad_cap, uint32_t* rec, uint64_t rec_bytes, int sms,
                                  int* status, cudaStream_t st) {
-    static int fit = -1;
-    if (fit < 0) {
+    // 1024 threads per SM, as one CTA by default (the grid syncs are cheaper
+    // with fewer CTAs) or split into 2 or 4
+    const int per_sm = g_tuning.rounds_blocks_per_sm > 0 ? g_tuning.rounds_blocks_per_sm : 1;
+    const int th = 1024 / per_sm;
+    static int fit[5] = {-1, -1, -1, -1, -1};
+    if (fit[per_sm] < 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_saddle_rounds, 256, 0) != cudaSuccess || b < 1)
-            b = 1;
-        fit = b;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_saddle_rounds, th, 0) != cudaSuccess) b = 0;
+        fit[per_sm] = b;
     }
-    int per_sm = g_tuning.rounds_blocks_per_sm > 0 ? g_tuning.rounds_blocks_per_sm : 4;
-    if (per_sm > fit) per_sm = fit;   // a cooperative grid must be co-resident
+    if (fit[per_sm] < per_sm) return cudaErrorCooperativeLaunchTooLarge;   // the grid must be co-resident
     uint32_t rec_cap = 0;
     if (g_tuning.saddle_records >= 0)
         rec_cap = (uint32_t)hmin<uint64_t>(rec_bytes / (4ull * REC_MAX_WORDS), 0xFFFFFFFFull);
     void* args[] = {(void*)&in, (void*)&c, (void*)&out, (void*)&sad, (void*)&sadb, (void*)&sadv,
                     (void*)&sad_cap, (void*)&rec, (void*)&rec_cap, (void*)&status};
-    return cudaLaunchCooperativeKernel((const void*)k_saddle_rounds, dim3(per_sm * sms), dim3(256), args, 0, st);
+    return cudaLaunchCooperativeKernel((const void*)k_saddle_rounds, dim3(per_sm * sms), dim3(th), args, 0, st);
 }
 }  // namespace tsz

@@ -11,7 +11,7 @@ constexpr int RANK_TILE = 2048;   // entries per dense-rank tile
 struct Tuning {
     int cd_threads = 256;
     int cd_blocks_per_sm = 8;
-    int rounds_blocks_per_sm = 0;   // 0: occupancy, capped at 4
+    int rounds_blocks_per_sm = 0;   // CTAs per SM of the saddle rounds (1024 threads per SM): 0 = 1
     int dec_slack_tiles = 0;        // 0: a quarter of the fused decoder's resident CTAs
     int saddle_records = 0;         // >= 0: neighbourhood records in the saddle rounds; < 0: field reads
 };
