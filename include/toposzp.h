@@ -178,13 +178,16 @@ uint64_t toposzp_noalloc_max_points(void);
  *                        resident CTAs)
  *   saddle_records       0 or 1: the saddle rounds copy each candidate's
  *                        neighbourhood into a compact record first (default);
- *                        -1: they read the field directly */
+ *                        -1: they read the field directly
+ *   dec_split            0: one fused wavefront kernel decodes (default);
+ *                        1: its four stages run as separate launches */
 typedef struct {
     int32_t cd_threads;
     int32_t cd_blocks_per_sm;
     int32_t rounds_blocks_per_sm;
     int32_t dec_slack_tiles;
     int32_t saddle_records;
+    int32_t dec_split;
 } toposzp_tuning;
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
 

@@ -2,7 +2,7 @@
 
 Sweeps the library's launch knobs (threads per CTA and CTAs per SM of the range
 + CD pass, CTAs per SM of the cooperative saddle rounds, then the stage slack
-of the fused decoder) on a representative field, then the number of parallel branches of the batched CUDA graph on a
+of the fused decoder or its split form) on a representative field, then the number of parallel branches of the batched CUDA graph on a
 mixed batch, timing each setting with CUDA events.  The winners are stored as
 JSON and applied with :func:`apply`.  No knob changes an output bit (the tests
 compare streams across settings), so tuning is always safe.
@@ -26,7 +26,7 @@ DEFAULT = {"cd_threads": 256, "cd_blocks_per_sm": 8, "rounds_blocks_per_sm": 1, 
 def apply(cfg: dict) -> None:
     t = _lib.Tuning(int(cfg.get("cd_threads", 0)), int(cfg.get("cd_blocks_per_sm", 0)),
                     int(cfg.get("rounds_blocks_per_sm", 0)), int(cfg.get("dec_slack_tiles", 0)),
-                    int(cfg.get("saddle_records", 0)))
+                    int(cfg.get("saddle_records", 0)), int(cfg.get("dec_split", 0)))
     st = _lib.load().toposzp_set_tuning(t)
     if st:
         raise _lib.TopoSZpError(st, "toposzp_set_tuning")
@@ -71,8 +71,8 @@ def tune(side: int = 256, batch_fields: int = 32, save: bool = True, verbose: bo
             print(cfg, round(t, 3))
         if t < best_t:
             best_t, best = t, {**best, **cfg}
-    for slack in (16, 64, 256, 1024):
-        cfg = {**best, "dec_slack_tiles": slack}
+    for slack, split in ((16, 0), (64, 0), (256, 0), (1024, 0), (0, 1)):
+        cfg = {**best, "dec_slack_tiles": slack, "dec_split": split}
         apply(cfg)
         t = _time(step)
         if verbose:

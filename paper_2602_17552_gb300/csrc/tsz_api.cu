@@ -328,11 +328,12 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     cudaMemsetAsync(ws, 0, w.tile_w, st);   // control block, rank look-back descriptors, stage flags
     launch_parse_header(src, in_size, n_out, c, status, st);
+    // the rank stream's tile sums and prefixes live in the (no longer used) rank descriptor region
+    uint32_t* rtile = reinterpret_cast<uint32_t*>(ws + w.rdesc);
     launch_dec_offsets(src, c, reinterpret_cast<uint32_t*>(ws + w.tile_w), reinterpret_cast<uint32_t*>(ws + w.tile_c),
                        reinterpret_cast<unsigned long long*>(ws + w.pay_pre), reinterpret_cast<uint32_t*>(ws + w.cp_pre),
-                       w.ntiles, sms, status, st);
-    launch_decode_ranks(src, c, reinterpret_cast<Desc*>(ws + w.rdesc),
-                        reinterpret_cast<int32_t*>(ws + w.delta), w.rank_tiles, sms, status, st);
+                       rtile, w.ntiles, sms, status, st);
+    launch_decode_ranks(src, c, rtile, reinterpret_cast<int32_t*>(ws + w.delta), n_out, sms, status, st);
     stage(5, st);
     launch_decode_fused(src, c, out, reinterpret_cast<unsigned long long*>(ws + w.pay_pre),
                         reinterpret_cast<uint32_t*>(ws + w.cp_pre), reinterpret_cast<int32_t*>(ws + w.delta),
@@ -363,12 +364,14 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
         return TOPOSZP_ERR_INVALID_ARG;
     if (t->dec_slack_tiles < 0 || t->dec_slack_tiles > 65536) return TOPOSZP_ERR_INVALID_ARG;
     if (t->saddle_records < -1 || t->saddle_records > 1) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->dec_split < 0 || t->dec_split > 1) return TOPOSZP_ERR_INVALID_ARG;
     Tuning u;
     if (t->cd_threads) u.cd_threads = t->cd_threads;
     if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
     u.rounds_blocks_per_sm = t->rounds_blocks_per_sm;
     u.dec_slack_tiles = t->dec_slack_tiles;
     u.saddle_records = t->saddle_records;
+    u.dec_split = t->dec_split;
     g_tuning = u;
     return TOPOSZP_OK;
 }

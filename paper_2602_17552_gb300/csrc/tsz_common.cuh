@@ -121,7 +121,6 @@ struct Ctrl {
     double eps, eb;
     Geo g;
     // tile allocators of the persistent codec kernels
-    unsigned int tile_enc, tile_rank, tile_dec, tile_rdec;
     // extrema lists (compress) and counts
     unsigned int cnt_max, cnt_min, pad2, pad3;
     unsigned long long sum_abs;
@@ -185,7 +184,7 @@ __device__ __forceinline__ uint32_t compact16(uint32_t x) {
 // Exclusive scan of pairs (a_i, b_i), i < cnt, by one CTA of 1024 threads:
 // coalesced chunks of 1024 entries, a shuffle scan per warp, one shared step
 // per chunk, running 64-bit carries.  load(i) -> uint2; store(i, pa, pb).
-// Returns the totals.  Shared scratch: s_w[32] pairs.
+// Returns the totals.  Shared scratch: s_w[33] pairs.
 template <class Load, class Store>
 __device__ void cta_scan_pairs(uint32_t cnt, Load load, Store store, unsigned long long (*s_w)[2],
                                unsigned long long& tot_a, unsigned long long& tot_b) {
@@ -204,17 +203,23 @@ __device__ void cta_scan_pairs(uint32_t cnt, Load load, Store store, unsigned lo
         }
         if (lane == 31) { s_w[warp][0] = ia; s_w[warp][1] = ib; }
         __syncthreads();
-        unsigned long long pa = ca, pb = cb, ta = 0, tb = 0;
-        for (uint32_t k = 0; k < 32; k++) {
-            const unsigned long long xa = s_w[k][0], xb = s_w[k][1];
-            if (k < warp) { pa += xa; pb += xb; }
-            ta += xa;
-            tb += xb;
+        if (warp == 0) {   // exclusive prefixes of the 32 warp totals, and the chunk total
+            const unsigned long long xa = s_w[lane][0], xb = s_w[lane][1];
+            unsigned long long sa = xa, sb = xb;
+#pragma unroll
+            for (int of = 1; of < 32; of <<= 1) {
+                const unsigned long long ta = __shfl_up_sync(0xFFFFFFFFu, sa, of), tb = __shfl_up_sync(0xFFFFFFFFu, sb, of);
+                if (lane >= (uint32_t)of) { sa += ta; sb += tb; }
+            }
+            s_w[lane][0] = sa - xa;
+            s_w[lane][1] = sb - xb;
+            if (lane == 31) { s_w[32][0] = sa; s_w[32][1] = sb; }
         }
         __syncthreads();
-        if (i < cnt) store(i, pa + ia - v.x, pb + ib - v.y);
-        ca += ta;
-        cb += tb;
+        if (i < cnt) store(i, ca + s_w[warp][0] + ia - v.x, cb + s_w[warp][1] + ib - v.y);
+        ca += s_w[32][0];
+        cb += s_w[32][1];
+        __syncthreads();
     }
     tot_a = ca;
     tot_b = cb;
@@ -315,82 +320,6 @@ __device__ __forceinline__ int classify_any(const Val& val, const Geo& g, uint32
     return is_interior(g, x, y, z) ? classify_interior(val, g, i, v) : classify(val, g, i, x, y, z, v);
 }
 
-// ----------------------------------------------------- decoupled look-back
-//
-// Single-pass exclusive scan over tiles of (payload words, extremum count).
-// Each tile publishes two 64-bit words; the top two bits carry the state
-// (1 = tile aggregate, 2 = inclusive prefix).  A reader accepts a pair only
-// when both words carry the same state, so no fence is needed between them.
-
-struct Desc {
-    unsigned long long a, b;
-};
-constexpr unsigned long long ST_AGG = 1ull << 62, ST_INC = 2ull << 62, VAL_MASK = (1ull << 62) - 1;
-
-__device__ __forceinline__ void desc_store(Desc* d, unsigned long long state, unsigned long long va,
-                                           unsigned long long vb) {
-    volatile unsigned long long* p = reinterpret_cast<volatile unsigned long long*>(d);
-    p[0] = state | va;
-    p[1] = state | vb;
-}
-
-// Called by one full warp.  Returns the exclusive prefix (va, vb) of tile t
-// and publishes its inclusive value.  Tiles are handed out in increasing order
-// by an atomic counter, so every tile waited on belongs to a running CTA.
-__device__ __forceinline__ void lookback(Desc* desc, uint32_t t, unsigned long long agg_a,
-                                         unsigned long long agg_b, unsigned long long& pre_a,
-                                         unsigned long long& pre_b, int* status) {
-    const int lane = threadIdx.x & 31;
-    pre_a = 0;
-    pre_b = 0;
-    if (t == 0) {
-        if (lane == 0) desc_store(&desc[0], ST_INC, agg_a, agg_b);
-        return;
-    }
-    if (lane == 0) desc_store(&desc[t], ST_AGG, agg_a, agg_b);
-    __threadfence();
-    long long base = (long long)t - 1;
-    uint32_t spins = 0;
-    bool timed_out = false;
-    while (true) {
-        long long j = base - lane;
-        unsigned long long A = 0, B = 0;
-        int st;
-        if (j >= 0) {
-            volatile unsigned long long* p = reinterpret_cast<volatile unsigned long long*>(&desc[j]);
-            A = p[0];
-            B = p[1];
-            st = ((A >> 62) == (B >> 62)) ? (int)(A >> 62) : 0;
-        } else {
-            st = 2;   // before tile 0: inclusive prefix 0
-        }
-        uint32_t inc = __ballot_sync(FULL, st == 2);
-        uint32_t none = __ballot_sync(FULL, st == 0);
-        int first = inc ? __ffs(inc) - 1 : 32;
-        uint32_t need = first >= 31 ? FULL : ((2u << first) - 1u);
-        if (none & need) {
-            if (++spins > SPIN_LIMIT) {
-                timed_out = true;
-                break;
-            }
-            __nanosleep(spins < 64 ? 32 : 256);
-            continue;
-        }
-        unsigned long long va = (lane <= first) ? (A & VAL_MASK) : 0;
-        unsigned long long vb = (lane <= first) ? (B & VAL_MASK) : 0;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            va += __shfl_xor_sync(FULL, va, o);
-            vb += __shfl_xor_sync(FULL, vb, o);
-        }
-        pre_a += va;
-        pre_b += vb;
-        if (first < 32) break;
-        base -= 32;
-    }
-    if (timed_out && lane == 0) set_status(status, ST_TIMEOUT);
-    if (lane == 0) desc_store(&desc[t], ST_INC, pre_a + agg_a, pre_b + agg_b);
-}
 
 // exp(-t), t >= 0, by scaling and squaring with a 12-term Taylor polynomial:
 // only binary64 + * /, so host and device give identical bits.

@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(256, 3) k_encode_field(const float* __restrict
 // consecutive tiles per thread.
 __global__ void __launch_bounds__(1024) k_enc_tile_scan(uint2* tcnt, uint32_t ntiles, Ctrl* c,
                                                         const int* status) {
-    __shared__ unsigned long long s_w[32][2];
+    __shared__ unsigned long long s_w[33][2];
     if (*status) return;
     unsigned long long tw, tc;
     cta_scan_pairs(
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restri
 
 // Tile prefixes of the rank payload (tiles of the delta sequence); sets rank_words.
 __global__ void __launch_bounds__(1024) k_rank_tile_scan(uint2* tcnt, Ctrl* c, const int* status) {
-    __shared__ unsigned long long s_w[32][2];
+    __shared__ unsigned long long s_w[33][2];
     if (*status) return;
     const uint32_t nbd = (uint32_t)cdiv(c->k_total, L);
     const uint32_t ntiles = (nbd + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;

@@ -127,75 +127,87 @@ __device__ __forceinline__ int32_t decode_block(const uint32_t* pay, unsigned lo
     return (int32_t)((uint32_t)first + d);
 }
 
-__global__ void __launch_bounds__(256) k_decode_ranks(const uint8_t* __restrict__ in, Ctrl* c, Desc* desc,
-                                                      int32_t* __restrict__ delta, int* status) {
-    __shared__ uint32_t s_tile;
-    __shared__ uint32_t s_w[TILE_WARPS];
-    __shared__ unsigned long long s_pre_w;
+// Rank-sequence decoder (BE^, LZ^ + B^ on the delta sequence): 8192-delta
+// tiles with payload offsets from the pre-pass, one block per thread (the
+// field decoder's scheme), output through a padded shared buffer.
+__global__ void __launch_bounds__(256, 3) k_decode_ranks(const uint8_t* __restrict__ in, Ctrl* c,
+                                                         const uint32_t* rpre, int32_t* __restrict__ delta,
+                                                         int* status) {
+    __shared__ __align__(16) uint32_t s_buf[DT_BLOCKS * 36];
+    __shared__ uint32_t s_w[8];
     if (*status || (c->flags & FLAG_NO_TOPO)) return;
     const Layout lo = c->lo;
     const uint64_t k = c->k_total;
     const unsigned long long rwords = c->rank_words;
     const uint32_t nbd = (uint32_t)cdiv(k, L);
+    const uint32_t nrt = (nbd + DT_BLOCKS - 1) / DT_BLOCKS;
     const uint8_t* widths = in + lo.r2;
     const int32_t* firsts = reinterpret_cast<const int32_t*>(in + lo.r4);
     const uint32_t* pay = reinterpret_cast<const uint32_t*>(in + lo.r5);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t ntiles = (nbd + TILE_BLOCKS - 1) / TILE_BLOCKS;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     bool corrupt = false;
-    while (true) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_rdec, 1u);
+    for (uint32_t t = blockIdx.x; t < nrt; t += gridDim.x) {
+        const uint32_t P0 = rpre[t], P1 = rpre[t + 1];
+        uint32_t len = 0;
+        if (P1 >= P0 && P1 - P0 <= DT_BLOCKS * 33u && P1 <= rwords) len = P1 - P0;
+        else corrupt = true;
+        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_buf[i] = __ldg(pay + P0 + i);
+        const uint32_t b = t * DT_BLOCKS + threadIdx.x;
+        uint32_t w = 0;
+        int32_t f = 0;
+        if (b < nbd) {
+            w = __ldg(widths + b);
+            f = __ldg(firsts + b);
+            if (w > 32) w = 0;
+        }
+        const uint32_t words = w ? 1u + w : 0u;
+        uint32_t iw = words;
+#pragma unroll
+        for (int of = 1; of < 32; of <<= 1) {
+            const uint32_t a0 = __shfl_up_sync(FULL, iw, of);
+            if (lane >= (uint32_t)of) iw += a0;
+        }
+        if (lane == 31) s_w[warp] = iw;
         __syncthreads();
-        const uint32_t tile = s_tile;
-        if (tile >= ntiles) break;
-        const uint32_t blk0 = tile * TILE_BLOCKS + warp * BPW;
-        uint32_t my_w = 0;
-        int32_t my_first = 0;
-        if (lane < BPW && blk0 + lane < nbd) {
-            my_w = widths[blk0 + lane];
-            my_first = firsts[blk0 + lane];
-            if (my_w > 32) {
+        uint32_t woff = iw - words;
+        for (uint32_t q = 0; q < warp; q++) woff += s_w[q];
+        uint32_t v[32];
+#pragma unroll
+        for (int e = 0; e < 32; e++) v[e] = 0u;
+        uint32_t sgn = 0;
+        if (w) {
+            if (woff + 1 + w <= len) {
+                sgn = s_buf[woff];
+                for (uint32_t p = w; p-- > 0;) {
+                    const uint32_t wd = s_buf[woff + 1 + p];
+#pragma unroll
+                    for (int e = 0; e < 32; e++) v[e] = (v[e] << 1) | ((wd >> e) & 1u);
+                }
+            } else {
                 corrupt = true;
-                my_w = 0;
             }
         }
-        uint32_t ww = (lane < BPW && my_w) ? 1u + my_w : 0u;
-        ww = __reduce_add_sync(FULL, ww);
-        if (lane == 0) s_w[warp] = ww;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t vw = lane < TILE_WARPS ? s_w[lane] : 0, iw = vw;
+        {
+            int32_t q = f;
 #pragma unroll
-            for (int o = 1; o < TILE_WARPS; o <<= 1) {
-                uint32_t t0 = __shfl_up_sync(FULL, iw, o);
-                if (lane >= o) iw += t0;
+            for (int e = 0; e < 32; e++) {
+                if (e) q += (sgn >> e) & 1u ? -(int32_t)v[e] : (int32_t)v[e];
+                v[e] = (uint32_t)q;
             }
-            uint32_t tw = __shfl_sync(FULL, iw, TILE_WARPS - 1);
-            unsigned long long pw, pc;
-            lookback(desc, tile, tw, 0, pw, pc, status);
-            if (lane < TILE_WARPS) s_w[lane] = iw - vw;
-            if (lane == 0) {
-                s_pre_w = pw;
-                if (tile == ntiles - 1 && pw + tw != rwords) set_status(status, ST_CORRUPT);
-            }
+        }
+        __syncthreads();   // the payload is consumed: the buffer stages the output rows
+        {
+            uint32_t* row = s_buf + threadIdx.x * 36;
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                *reinterpret_cast<uint4*>(row + 4 * q) = make_uint4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
         }
         __syncthreads();
-        unsigned long long woff = s_pre_w + s_w[warp];
-#pragma unroll
-        for (int j = 0; j < BPW; j++) {
-            const uint32_t b = blk0 + j;
-            if (b >= nbd) break;
-            const uint32_t w = __shfl_sync(FULL, my_w, j);
-            const int32_t first = __shfl_sync(FULL, my_first, j);
-            int32_t q = first;
-            if (w) {
-                if (woff + 1 + w <= rwords) q = decode_block(pay, woff, w, first, lane);
-                else corrupt = true;
-                woff += 1 + w;
-            }
-            const uint64_t i = (uint64_t)b * 32u + lane;
-            if (i < k) delta[i] = q;
-        }
+        const uint64_t p0 = (uint64_t)t * (DT_BLOCKS * 32);
+        const uint64_t left = k - p0;
+        const uint32_t np = left < (uint64_t)(DT_BLOCKS * 32) ? (uint32_t)left : (uint32_t)(DT_BLOCKS * 32);
+        for (uint32_t i = threadIdx.x; i < np; i += blockDim.x)
+            delta[p0 + i] = (int32_t)s_buf[(i >> 5) * 36 + (i & 31)];
         __syncthreads();
     }
     if (corrupt) set_status(status, ST_CORRUPT);
@@ -583,7 +595,8 @@ __device__ __forceinline__ bool saddle_candidate_rec_any(int ndim, int r, const 
 // up front the fused decoder needs no look-back.
 
 __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict__ in, Ctrl* c,
-                                                       uint32_t* tile_w, uint32_t* tile_c, int* status) {
+                                                       uint32_t* tile_w, uint32_t* tile_c, uint32_t* rtile_w,
+                                                       int* status) {
     if (*status) return;
     const Geo g = c->g;
     const Layout lo = c->lo;
@@ -616,6 +629,25 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
             tile_c[t] = cps;
         }
     }
+    if (topo) {   // payload words of the rank stream's tiles (8192 deltas each)
+        const uint8_t* rwidths = in + lo.r2;
+        const uint32_t nbd = (uint32_t)cdiv(c->k_total, L);
+        const uint32_t nrt = (nbd + DT_BLOCKS - 1) / DT_BLOCKS;
+        for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < nrt; t += (gridDim.x * blockDim.x) >> 5) {
+            uint32_t words = 0;
+#pragma unroll
+            for (int j = 0; j < DT_BLOCKS / 32; j++) {
+                const uint32_t b = t * DT_BLOCKS + j * 32 + lane;
+                if (b < nbd) {
+                    uint32_t w = __ldg(rwidths + b);
+                    if (w > 32) { corrupt = true; w = 0; }
+                    words += w ? 1u + w : 0u;
+                }
+            }
+            words = __reduce_add_sync(FULL, words);
+            if (lane == 0) rtile_w[t] = words;
+        }
+    }
     if (corrupt) set_status(status, ST_CORRUPT);
 }
 
@@ -623,9 +655,22 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
 // Each thread owns a contiguous run of tiles and reads it in unrolled groups of
 // 16 independent loads.
 __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t* tile_w, const uint32_t* tile_c,
-                                                        unsigned long long* pay_pre, uint32_t* cp_pre, int* status) {
-    __shared__ unsigned long long s_w[32][2];
+                                                        unsigned long long* pay_pre, uint32_t* cp_pre,
+                                                        uint32_t* rtile_w, int* status) {
+    __shared__ unsigned long long s_w[33][2];
     if (*status) return;
+    if (!(c->flags & FLAG_NO_TOPO)) {   // the rank stream's tile prefixes, in place
+        const uint32_t nbd = (uint32_t)cdiv(c->k_total, L);
+        const uint32_t nrt = (nbd + DT_BLOCKS - 1) / DT_BLOCKS;
+        unsigned long long rw, rz;
+        cta_scan_pairs(
+            nrt, [&](uint32_t i) { return make_uint2(rtile_w[i], 0u); },
+            [&](uint32_t i, unsigned long long pw, unsigned long long) { rtile_w[i] = (uint32_t)pw; }, s_w, rw, rz);
+        if (threadIdx.x == 0) {
+            rtile_w[nrt] = (uint32_t)rw;
+            if (rw != c->rank_words) set_status(status, ST_CORRUPT);
+        }
+    }
     const uint32_t ntiles = (c->g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
     unsigned long long tw, tc;
     cta_scan_pairs(
@@ -1093,6 +1138,53 @@ __global__ void __launch_bounds__(256, 4) k_decode_fused(FusedArgs A) {
     else fused_body<true>(A, S);
 }
 
+// The same four stages as separate launches (one CTA per tile per stage; the
+// kernel boundaries order the stages, so there are no waits).
+template <int K>
+__global__ void __launch_bounds__(256, 4) k_decode_stage(FusedArgs A) {
+    __shared__ FusedSmem S;
+    if (*A.status) return;
+    Ctrl* c = A.c;
+    const bool topo = !(c->flags & FLAG_NO_TOPO);
+    if (K > 1 && !topo) return;
+    if (threadIdx.x == 0) {
+        S.g = c->g;
+        S.lo = c->lo;
+    }
+    __syncthreads();
+    const Geo& g = S.g;
+    const Layout& lo = S.lo;
+    const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
+    const uint32_t ntiles = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
+    bool corrupt = false;
+    unsigned long long restored = 0, skipped = 0;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        if (K == 1) {
+            if (topo) stage_decode<true>(A, g, lo, t, S.pay, S.w, S.cp, corrupt);
+            else stage_decode<false>(A, g, lo, t, S.pay, S.w, S.cp, corrupt);
+            __syncthreads();
+        } else if (K == 2) {
+            stage_extrema(A, g, labels, t, restored, skipped);
+        } else if (K == 3) {
+            stage_apply(A, g, t);
+        } else {
+            stage_saddles(A, g, labels, t, S.pay, S.cnt);
+            __syncthreads();
+        }
+    }
+    if (corrupt) set_status(A.status, ST_CORRUPT);
+    if (K == 2) {
+        for (int o = 16; o > 0; o >>= 1) {
+            restored += __shfl_xor_sync(FULL, restored, o);
+            skipped += __shfl_xor_sync(FULL, skipped, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            if (restored) atomicAdd(&c->stat_restored, restored);
+            if (skipped) atomicAdd(&c->stat_skipped, skipped);
+        }
+    }
+}
+
 // RS^ colour rounds over the lost-saddle list (cooperative: the grid syncs
 // between the evaluation and the write of every colour).  The list is first
 // bucketed by colour so that each round touches only its own candidates.
@@ -1197,20 +1289,20 @@ void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ct
     k_parse_header<<<1, 32, 0, st>>>(in, in_size, n_out, c, status);
 }
 
-void launch_decode_ranks(const uint8_t* in, Ctrl* c, Desc* desc, int32_t* delta, uint32_t max_tiles,
+void launch_decode_ranks(const uint8_t* in, Ctrl* c, const uint32_t* rpre, int32_t* delta, uint64_t max_k,
                          int sms, int* status, cudaStream_t st) {
-    uint32_t grid = hmin<uint32_t>(max_tiles, (uint32_t)sms * 6);
+    uint32_t grid = hmin<uint32_t>((uint32_t)cdiv(cdiv(max_k, L), DT_BLOCKS), (uint32_t)sms * 3);
     if (grid == 0) grid = 1;
-    k_decode_ranks<<<grid, 256, 0, st>>>(in, c, desc, delta, status);
+    k_decode_ranks<<<grid, 256, 0, st>>>(in, c, rpre, delta, status);
 }
 
 void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* tile_c,
-                        unsigned long long* pay_pre, uint32_t* cp_pre, uint32_t ntiles, int sms, int* status,
-                        cudaStream_t st) {
+                        unsigned long long* pay_pre, uint32_t* cp_pre, uint32_t* rtile_w, uint32_t ntiles, int sms,
+                        int* status, cudaStream_t st) {
     uint32_t blocks = hmin<uint32_t>((ntiles + 7) / 8, (uint32_t)sms * 8);
     if (blocks == 0) blocks = 1;
-    k_dec_tile_sums<<<blocks, 256, 0, st>>>(in, c, tile_w, tile_c, status);
-    k_dec_tile_scan<<<1, 1024, 0, st>>>(c, tile_w, tile_c, pay_pre, cp_pre, status);
+    k_dec_tile_sums<<<blocks, 256, 0, st>>>(in, c, tile_w, tile_c, rtile_w, status);
+    k_dec_tile_scan<<<1, 1024, 0, st>>>(c, tile_w, tile_c, pay_pre, cp_pre, rtile_w, status);
 }
 
 void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
@@ -1230,6 +1322,14 @@ void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned 
     // slots; H is known only on the device, so CTAs keep taking virtual tiles
     // until all are done).  Waits only point at lower tiles, taken by CTAs that
     // started earlier, so any residency makes progress.
+    if (g_tuning.dec_split > 0) {
+        const uint32_t sg = hmin<uint32_t>(ntiles_dec, (uint32_t)(fit * sms) * 4u);
+        k_decode_stage<1><<<sg, 256, 0, st>>>(A);
+        k_decode_stage<2><<<sg, 256, 0, st>>>(A);
+        k_decode_stage<3><<<sg, 256, 0, st>>>(A);
+        k_decode_stage<4><<<sg, 256, 0, st>>>(A);
+        return;
+    }
     const uint32_t grid = ntiles_dec + 3 * hmin<uint32_t>(ntiles_dec, h_bound + slack);
     k_decode_fused<<<grid, 256, 0, st>>>(A);
 }

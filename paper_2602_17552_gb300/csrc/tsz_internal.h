@@ -14,6 +14,7 @@ struct Tuning {
     int rounds_blocks_per_sm = 0;   // CTAs per SM of the saddle rounds (1024 threads per SM): 0 = 1
     int dec_slack_tiles = 0;        // 0: a quarter of the fused decoder's resident CTAs
     int saddle_records = 0;         // >= 0: neighbourhood records in the saddle rounds; < 0: field reads
+    int dec_split = 0;              // > 0: the decoder stages as separate launches instead of fused
 };
 extern Tuning g_tuning;
 
@@ -59,9 +60,9 @@ void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, f
 void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c, int* status,
                          cudaStream_t st);
 void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* tile_c,
-                        unsigned long long* pay_pre, uint32_t* cp_pre, uint32_t ntiles, int sms, int* status,
-                        cudaStream_t st);
-void launch_decode_ranks(const uint8_t* in, Ctrl* c, Desc* desc, int32_t* delta, uint32_t max_tiles,
+                        unsigned long long* pay_pre, uint32_t* cp_pre, uint32_t* rtile_w, uint32_t ntiles, int sms,
+                        int* status, cudaStream_t st);
+void launch_decode_ranks(const uint8_t* in, Ctrl* c, const uint32_t* rpre, int32_t* delta, uint64_t max_k,
                          int sms, int* status, cudaStream_t st);
 void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
                          const uint32_t* cp_pre, const int32_t* delta, uint32_t* cp_idx, float* newv,
