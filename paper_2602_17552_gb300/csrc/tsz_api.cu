@@ -56,12 +56,12 @@ constexpr CompressWs compress_ws_c(uint64_t n) {
     w.rank_tiles = (uint32_t)cdiv(cdiv(n + 2, L), TILE_BLOCKS) + 1;
     w.agg_stride = (uint32_t)cdiv(w.list_cap, RANK_TILE) + 1;
     w.os_tiles = (uint32_t)cdiv(w.list_cap, 4096);
-    w.os_stride = w.os_tiles * 256u;
+    w.os_stride = w.os_tiles * 512u;   // up to 512 digits per tile
     uint64_t o = 0;
     w.ctrl = o; o = a256(o + CTRL_BYTES);
     w.desc = o; o = a256(o + 16ull * (w.ntiles + 1));   // per-tile counts, then prefixes
     w.rdesc = o; o = a256(o + 16ull * (w.rank_tiles + 1));
-    w.os_small = o; o = a256(o + 4ull * (2 * 4 * 256) * 2 + 4ull * 8);   // histograms, bases, counters
+    w.os_small = o; o = a256(o + 4ull * (2 * 4 * 512) * 2 + 4ull * 8);   // histograms, bases, counters
     // end of the region zeroed at the start of every call
     w.os_desc_a = o; o = a256(o + 4ull * 2 * w.os_stride);
     w.os_desc_b = o; o = a256(o + 4ull * 2 * w.os_stride);
@@ -251,8 +251,8 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     if (topo) {
         SortWs sw;
         sw.hist = reinterpret_cast<uint32_t*>(ws + w.os_small);
-        sw.base = sw.hist + 2 * 4 * 256;
-        sw.ctr = sw.base + 2 * 4 * 256;
+        sw.base = sw.hist + 2 * 4 * 512;
+        sw.ctr = sw.base + 2 * 4 * 512;
         sw.desc_a = reinterpret_cast<uint32_t*>(ws + w.os_desc_a);
         sw.desc_b = reinterpret_cast<uint32_t*>(ws + w.os_desc_b);
         sw.stride = w.os_stride;

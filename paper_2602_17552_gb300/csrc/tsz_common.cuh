@@ -111,7 +111,7 @@ __host__ __device__ inline void make_layout(uint64_t n, uint64_t nb, bool topo, 
 // wrapper before the first kernel of a call.
 struct Ctrl {
     // range pass
-    unsigned int min_inv, max_key, nonfinite, pad0;
+    unsigned int min_inv, max_key, nonfinite, sort_passes;
     // quantiser (Section II-C) and geometry, filled by the parameter kernel or
     // by the header parser
     int const_field, rel, rbf_k, rs_sweeps;

@@ -546,17 +546,30 @@ __global__ void __launch_bounds__(1024) k_enc_tile_scan(uint2* tcnt, uint32_t nt
     }
 }
 
-// Every tile's payload slot to its place in the payload section (a warp per tile).
+// Every tile's payload slot to its place in the payload section (a CTA per
+// tile, every thread a few words with all its loads in flight).
+__device__ __forceinline__ void copy_slot(const uint32_t* __restrict__ src, uint32_t* dst, uint32_t cnt) {
+    for (uint32_t k0 = 0; k0 < cnt; k0 += 4 * 256) {
+        uint32_t v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t k = k0 + j * 256 + threadIdx.x;
+            v[j] = k < cnt ? __ldcs(src + k) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t k = k0 + j * 256 + threadIdx.x;
+            if (k < cnt) dst[k] = v[j];
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) k_enc_copy(const uint32_t* __restrict__ scratch, const uint2* tpre,
                                                   uint32_t ntiles, uint32_t* pay, const int* status) {
     if (*status) return;
-    const int lane = threadIdx.x & 31;
-    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles;
-         t += (gridDim.x * blockDim.x) >> 5) {
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint32_t p0 = tpre[t].x, cnt = tpre[t + 1].x - p0;
-        const uint32_t* src = scratch + (size_t)t * TILE_PAY;
-        uint32_t* dst = pay + p0;
-        for (uint32_t k = lane; k < cnt; k += 32) dst[k] = __ldcs(src + k);
+        copy_slot(scratch + (size_t)t * TILE_PAY, pay + p0, cnt);
     }
 }
 
@@ -667,48 +680,71 @@ __global__ void __launch_bounds__(1024) k_rank_tile_scan(uint2* tcnt, Ctrl* c, c
     }
 }
 
-// Rank payload slots to the rank payload section (a warp per tile).
+// Rank payload slots to the rank payload section (a CTA per tile).
 __global__ void __launch_bounds__(256) k_rank_copy(const uint32_t* __restrict__ scratch, const uint2* tpre,
                                                    const Ctrl* c, uint8_t* out, const int* status) {
     if (*status) return;
-    const int lane = threadIdx.x & 31;
     const uint64_t k = c->k_total;
     const uint32_t nbd = (uint32_t)cdiv(k, L);
     const uint32_t ntiles = (nbd + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;
     Layout lo;
     make_layout(c->g.n, c->g.nb, true, c->pay_words, k, 0, lo);
     uint32_t* pay = reinterpret_cast<uint32_t*>(out + lo.r5);
-    for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += (gridDim.x * blockDim.x) >> 5) {
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint32_t p0 = tpre[t].x, cnt = tpre[t + 1].x - p0;
-        const uint32_t* src = scratch + (size_t)t * TILE_PAY;
-        for (uint32_t q = lane; q < cnt; q += 32) pay[p0 + q] = __ldcs(src + q);
+        copy_slot(scratch + (size_t)t * TILE_PAY, pay + p0, cnt);
     }
 }
 
 // ================================================================ rank sort
 //
-// LSD radix sort of (key, position) pairs, 8-bit digits, stable, after the
-// "onesweep" scheme: one pass builds the digit histograms of all four passes;
-// then every pass is a single kernel over tiles of 4096 keys.  A tile ranks its
-// keys per digit with warp match masks (stable: keys keep their input order
-// within a digit), publishes its per-digit counts, and finds its global offset
-// per digit with a decoupled look-back over the earlier tiles (one thread per
-// digit).  Both lists (maxima: key = ord(v); minima: key = ~ord(v)) are sorted
-// by the same launches (blockIdx.y selects the list).
+// LSD radix sort of (key, position) pairs, stable, after the "onesweep"
+// scheme: one pass builds the digit histograms of every pass; then every pass
+// is a single kernel over tiles of 4096 keys.  A tile ranks its keys per digit
+// with warp match masks (stable: keys keep their input order within a digit),
+// publishes its per-digit counts, and finds its global offset per digit with a
+// decoupled look-back over the earlier tiles.  Both lists (maxima: key =
+// ord(v); minima: key = ~ord(v)) are sorted by the same launches (blockIdx.y
+// selects the list).
+//
+// Only the bits that vary are sorted: every key lies in the field's key range
+// [ord(vmin), ord(vmax)], so the digits come from key - (the list's smallest
+// possible key), whose bit length B is known from the range pass.  B <= 8, 16,
+// 27 or 32 bits take 1, 2, 3 or 4 passes of ceil(B / passes) <= 9 bits.
 
-constexpr int OS_WARPS = 8;
-constexpr int OS_ITEMS = 16;                       // keys per lane
+constexpr int OS_WARPS = 16;                       // 512 threads: one per digit in the look-back
+constexpr int OS_ITEMS = 8;                        // keys per lane
 constexpr int OS_TILE = OS_WARPS * 32 * OS_ITEMS;  // 4096
+constexpr int OS_ND = 512;                         // most digits of a pass (9 bits)
 constexpr uint32_t OS_AGG = 1u << 30, OS_INC = 2u << 30, OS_MASK = (1u << 30) - 1;
 
-// Lanes of the warp whose 8-bit digit equals this lane's (a match mask built
-// from eight ballots); lanes with ok == false match nobody and nobody them.
-__device__ __forceinline__ uint32_t match_digit8(uint32_t d, bool ok) {
+struct SortPlan {
+    int passes, bits;
+    uint32_t base[2];   // subtracted from the keys of list 0 / 1
+};
+
+__device__ __forceinline__ SortPlan sort_plan(const Ctrl* c) {
+    SortPlan sp;
+    const uint32_t kmax = c->max_key, kmin = ~c->min_inv;   // ord(vmax), ord(vmin)
+    const uint32_t span = kmax > kmin ? kmax - kmin : 0u;
+    const int B = span ? 32 - __clz(span) : 0;
+    sp.passes = B == 0 ? 0 : B <= 8 ? 1 : B <= 16 ? 2 : B <= 27 ? 3 : 4;
+    sp.bits = sp.passes ? (B + sp.passes - 1) / sp.passes : 0;
+    sp.base[0] = kmin;
+    sp.base[1] = ~kmax;
+    return sp;
+}
+
+// Lanes of the warp whose `bits`-bit digit equals this lane's (a match mask
+// built from ballots); lanes with ok == false match nobody and nobody them.
+__device__ __forceinline__ uint32_t match_digit(uint32_t d, bool ok, int bits) {
     uint32_t m = __ballot_sync(FULL, ok);
 #pragma unroll
-    for (int b = 0; b < 8; b++) {
-        const uint32_t v = __ballot_sync(FULL, (d >> b) & 1u);
-        m &= ((d >> b) & 1u) ? v : ~v;
+    for (int b = 0; b < 9; b++) {
+        if (b < bits) {
+            const uint32_t v = __ballot_sync(FULL, (d >> b) & 1u);
+            m &= ((d >> b) & 1u) ? v : ~v;
+        }
     }
     return ok ? m : (1u << (threadIdx.x & 31));
 }
@@ -717,37 +753,40 @@ __device__ __forceinline__ uint32_t list_count(const Ctrl* c, int list) {
     return list ? c->cnt_min : c->cnt_max;
 }
 
-// All four digit histograms of both lists, and zeroed look-back descriptors
-// for the tiles the passes will use.  Each warp counts into its own slice of
-// shared memory; the slices are summed at the end.
-__global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s1, const Ctrl* c,
-                                                 uint32_t* ghist /* [2][4][256] */, uint32_t* desc_a,
+// The digit histograms of every pass of both lists, and zeroed look-back
+// descriptors for the tiles the passes will use.  Warps count into four
+// shared slices, summed at the end.  Records the pass count for the rank
+// kernels (the sorted lists end in the second buffer when it is odd).
+__global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s1, Ctrl* c,
+                                                 uint32_t* ghist /* [2][4][512] */, uint32_t* desc_a,
                                                  uint32_t* desc_b, uint32_t desc_stride, const int* status) {
-    __shared__ uint32_t h[8][4 * 256];
+    __shared__ uint32_t h[4][4 * OS_ND];
     if (*status) return;
+    const SortPlan sp = sort_plan(c);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) c->sort_passes = (uint32_t)sp.passes;
+    if (sp.passes == 0) return;
     const int list = blockIdx.y;
-    const int warp = threadIdx.x >> 5;
     const uint2* s = list ? s1 : s0;
     const uint32_t k = list_count(c, list);
-    for (int i = threadIdx.x; i < 8 * 4 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+    const uint32_t base = sp.base[list], mask = (1u << sp.bits) - 1u;
+    for (int i = threadIdx.x; i < 4 * 4 * OS_ND; i += blockDim.x) (&h[0][0])[i] = 0;
     __syncthreads();
-    uint32_t* hw = h[warp];
+    uint32_t* hw = h[(threadIdx.x >> 5) & 3];
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
-        const uint32_t key = s[i].x;
-        atomicAdd(&hw[0 * 256 + (key & 0xFFu)], 1u);
-        atomicAdd(&hw[1 * 256 + ((key >> 8) & 0xFFu)], 1u);
-        atomicAdd(&hw[2 * 256 + ((key >> 16) & 0xFFu)], 1u);
-        atomicAdd(&hw[3 * 256 + (key >> 24)], 1u);
+        const uint32_t key = s[i].x - base;
+#pragma unroll
+        for (int p = 0; p < 4; p++)
+            if (p < sp.passes) atomicAdd(&hw[p * OS_ND + ((key >> (p * sp.bits)) & mask)], 1u);
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) {
-        uint32_t v = 0;
-#pragma unroll
-        for (int w = 0; w < 8; w++) v += h[w][i];
-        if (v) atomicAdd(&ghist[list * 1024 + i], v);
+    const uint32_t nd = 1u << sp.bits;
+    for (uint32_t i = threadIdx.x; i < 4 * OS_ND; i += blockDim.x) {
+        if ((i >> 9) >= (uint32_t)sp.passes || (i & (OS_ND - 1)) >= nd) continue;
+        const uint32_t v = h[0][i] + h[1][i] + h[2][i] + h[3][i];
+        if (v) atomicAdd(&ghist[list * 4 * OS_ND + i], v);
     }
     // zero the descriptors of the tiles in use (both alternating buffers)
-    const uint32_t words = (uint32_t)cdiv(k, OS_TILE) * 256u;
+    const uint32_t words = (uint32_t)cdiv(k, OS_TILE) * nd;
     uint32_t* da = desc_a + (size_t)list * desc_stride;
     uint32_t* db = desc_b + (size_t)list * desc_stride;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x) {
@@ -756,13 +795,15 @@ __global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s
     }
 }
 
-// exclusive scan of each 256-digit histogram -> digit bases (a CTA per row)
-__global__ void __launch_bounds__(256) k_os_bases(const uint32_t* ghist, uint32_t* base, const int* status) {
-    __shared__ uint32_t s_w[8];
+// exclusive scan of each digit histogram -> digit bases (a CTA of 512 per row)
+__global__ void __launch_bounds__(512) k_os_bases(const Ctrl* c, const uint32_t* ghist, uint32_t* base,
+                                                  const int* status) {
+    __shared__ uint32_t s_w[16];
     if (*status) return;
     const int row = blockIdx.x;   // list * 4 + pass
+    if ((row & 3) >= (int)c->sort_passes) return;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t v = ghist[row * 256 + threadIdx.x];
+    const uint32_t v = ghist[row * OS_ND + threadIdx.x];
     uint32_t inc = v;
 #pragma unroll
     for (int of = 1; of < 32; of <<= 1) {
@@ -773,33 +814,36 @@ __global__ void __launch_bounds__(256) k_os_bases(const uint32_t* ghist, uint32_
     __syncthreads();
     uint32_t pre = 0;
     for (uint32_t k = 0; k < warp; k++) pre += s_w[k];
-    base[row * 256 + threadIdx.x] = pre + inc - v;
+    base[row * OS_ND + threadIdx.x] = pre + inc - v;
 }
 
-__global__ void __launch_bounds__(256) k_os_pass(const uint2* s0, const uint2* s1, uint2* d0, uint2* d1,
+__global__ void __launch_bounds__(OS_WARPS * 32) k_os_pass(const uint2* s0, const uint2* s1, uint2* d0, uint2* d1,
                                                  const Ctrl* c, const uint32_t* base, uint32_t* desc,
                                                  uint32_t* desc_next, uint32_t desc_stride, uint32_t* tile_ctr,
                                                  int pass, int* status) {
     __shared__ uint32_t s_tile;
-    __shared__ uint16_t wcnt[OS_WARPS][256];
-    __shared__ uint32_t gofs[256];
+    __shared__ uint16_t wcnt[OS_WARPS][OS_ND];
+    __shared__ uint32_t gofs[OS_ND];
     if (*status) return;
+    const SortPlan sp = sort_plan(c);
+    if (pass >= sp.passes) return;
     const int list = blockIdx.y;
     const uint2* src = list ? s1 : s0;
     uint2* dst = list ? d1 : d0;
     const uint32_t k = list_count(c, list);
     const uint32_t ntiles = (uint32_t)cdiv(k, OS_TILE);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int shift = 8 * pass;
+    const int shift = pass * sp.bits;
+    const uint32_t nd = 1u << sp.bits, mask = nd - 1u, kb = sp.base[list];
     uint32_t* dsc = desc + (size_t)list * desc_stride;
     const uint32_t lt = lanemask_lt();
     while (true) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&tile_ctr[list], 1u);
-        for (int i = threadIdx.x; i < OS_WARPS * 256; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+        for (int i = threadIdx.x; i < OS_WARPS * OS_ND; i += blockDim.x) (&wcnt[0][0])[i] = 0;
         __syncthreads();
         const uint32_t t = s_tile;
         if (t >= ntiles) break;
-        // load: warp w owns keys [t*4096 + w*512, +512), lane-striped (coalesced)
+        // load: warp w owns keys [t*4096 + w*256, +256), lane-striped (coalesced)
         const uint32_t wbase = t * OS_TILE + warp * 32 * OS_ITEMS;
         uint2 e[OS_ITEMS];
         uint32_t dg[OS_ITEMS];
@@ -809,25 +853,25 @@ __global__ void __launch_bounds__(256) k_os_pass(const uint2* s0, const uint2* s
             const uint32_t p = wbase + j * 32 + lane;
             const bool ok = p < k;
             e[j] = ok ? src[p] : make_uint2(0u, 0u);
-            dg[j] = ok ? (e[j].x >> shift) & 0xFFu : 256u + lane;
+            dg[j] = ok ? ((e[j].x - kb) >> shift) & mask : (uint32_t)OS_ND + lane;
         }
         // stable local ranks inside the warp, in (j, lane) order
 #pragma unroll
         for (int j = 0; j < OS_ITEMS; j++) {
-            const uint32_t peers = match_digit8(dg[j], dg[j] < 256u);
+            const bool ok = dg[j] < (uint32_t)OS_ND;
+            const uint32_t peers = match_digit(dg[j], ok, sp.bits);
             const int leader = __ffs(peers) - 1;
             uint32_t b = 0;
-            if (dg[j] < 256u && lane == leader) b = wcnt[warp][dg[j]];
+            if (ok && lane == leader) b = wcnt[warp][dg[j]];
             b = __shfl_sync(FULL, b, leader);
             rk[j] = b + __popc(peers & lt);
             __syncwarp();
-            if (dg[j] < 256u && lane == leader) wcnt[warp][dg[j]] = (uint16_t)(b + __popc(peers));
+            if (ok && lane == leader) wcnt[warp][dg[j]] = (uint16_t)(b + __popc(peers));
             __syncwarp();
         }
         __syncthreads();
-        // per digit (thread d): offsets of the warps, tile count, look-back
-        {
-            const int d = threadIdx.x;
+        // per digit: offsets of the warps, tile count, look-back
+        for (uint32_t d = threadIdx.x; d < nd; d += blockDim.x) {
             uint32_t run = 0;
 #pragma unroll
             for (int w = 0; w < OS_WARPS; w++) {
@@ -841,11 +885,11 @@ __global__ void __launch_bounds__(256) k_os_pass(const uint2* s0, const uint2* s
             if (t == 0) {
                 vd[d] = OS_INC | tot;
             } else {
-                vd[(size_t)t * 256 + d] = OS_AGG | tot;
+                vd[(size_t)t * nd + d] = OS_AGG | tot;
                 long long j = (long long)t - 1;
                 uint32_t spins = 0;
                 while (j >= 0) {
-                    const uint32_t v = vd[(size_t)j * 256 + d];
+                    const uint32_t v = vd[(size_t)j * nd + d];
                     if (v & OS_INC) {
                         pre += v & OS_MASK;
                         break;
@@ -861,16 +905,16 @@ __global__ void __launch_bounds__(256) k_os_pass(const uint2* s0, const uint2* s
                     }
                     __nanosleep(32);
                 }
-                vd[(size_t)t * 256 + d] = OS_INC | (pre + tot);
+                vd[(size_t)t * nd + d] = OS_INC | (pre + tot);
             }
-            gofs[d] = base[(list * 4 + pass) * 256 + d] + pre;
+            gofs[d] = base[(list * 4 + pass) * OS_ND + d] + pre;
             // the next pass uses the other buffer: clear this tile's entry there
-            desc_next[(size_t)list * desc_stride + (size_t)t * 256 + d] = 0u;
+            desc_next[(size_t)list * desc_stride + (size_t)t * nd + d] = 0u;
         }
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < OS_ITEMS; j++) {
-            if (dg[j] < 256u) dst[gofs[dg[j]] + wcnt[warp][dg[j]] + rk[j]] = e[j];
+            if (dg[j] < (uint32_t)OS_ND) dst[gofs[dg[j]] + wcnt[warp][dg[j]] + rk[j]] = e[j];
         }
         __syncthreads();
     }
@@ -947,13 +991,15 @@ __device__ __forceinline__ SegCnt cta_seg_scan(SegCnt x, SegCnt pre, SegCnt* s_t
 }
 
 // pass 1: aggregate per tile of RANK_TILE entries
-__global__ void __launch_bounds__(256) k_rank_tiles(const uint2* s0, const uint2* s1, const Ctrl* c,
+__global__ void __launch_bounds__(256) k_rank_tiles(const uint2* l0, const uint2* l1, const uint2* t0, const uint2* t1,
+                                                    const Ctrl* c,
                                                     uint2* agg, uint32_t agg_stride, int G,
                                                     const int* status) {
     __shared__ SegCnt s_tot[8];
     if (*status) return;
     const int list = blockIdx.y;
-    const uint2* s = list ? s1 : s0;
+    const bool odd = c->sort_passes & 1u;   // an odd number of passes ends in the second buffer
+    const uint2* s = list ? (odd ? t1 : l1) : (odd ? t0 : l0);
     const uint32_t k = list ? c->cnt_min : c->cnt_max;
     const float r = c->r_f;
     const uint32_t ntiles = (uint32_t)cdiv(k, RANK_TILE);
@@ -1003,13 +1049,15 @@ __global__ void __launch_bounds__(256) k_rank_scan(uint2* agg, uint32_t agg_stri
 }
 
 // pass 3: per tile, scan with the carried prefix and scatter delta[pos]
-__global__ void __launch_bounds__(256) k_rank_scatter(const uint2* s0, const uint2* s1, const Ctrl* c,
+__global__ void __launch_bounds__(256) k_rank_scatter(const uint2* l0, const uint2* l1, const uint2* t0,
+                                                      const uint2* t1, const Ctrl* c,
                                                       const uint2* agg, uint32_t agg_stride, const uint2* tpre,
                                                       int32_t* delta, int G, const int* status) {
     __shared__ SegCnt s_tot[8];
     if (*status) return;
     const int list = blockIdx.y;
-    const uint2* s = list ? s1 : s0;
+    const bool odd = c->sort_passes & 1u;   // an odd number of passes ends in the second buffer
+    const uint2* s = list ? (odd ? t1 : l1) : (odd ? t0 : l0);
     const uint32_t k = list ? c->cnt_min : c->cnt_max;
     const float r = c->r_f;
     const uint32_t ntiles = (uint32_t)cdiv(k, RANK_TILE);
@@ -1254,7 +1302,7 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2*
     if (topo) k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, status);
     else k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, status);
     k_enc_tile_scan<<<1, 1024, 0, st>>>(tcnt, ntiles, c, status);
-    uint32_t cg = hmin<uint32_t>((ntiles + 7) / 8, (uint32_t)sms * 16);
+    uint32_t cg = hmin<uint32_t>(ntiles, (uint32_t)sms * 8);
     k_enc_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, ntiles, reinterpret_cast<uint32_t*>(out + lo.s5),
                                             status);
 }
@@ -1266,22 +1314,23 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
     uint32_t hg = hmin<uint32_t>((uint32_t)cdiv((uint64_t)max_tiles * OS_TILE, 256), (uint32_t)sms * 4);
     if (hg == 0) hg = 1;
     k_os_hist<<<dim3(hg, 2), 256, 0, st>>>(listM, listm, c, sw.hist, sw.desc_a, sw.desc_b, sw.stride, status);
-    k_os_bases<<<8, 256, 0, st>>>(sw.hist, sw.base, status);
+    k_os_bases<<<8, OS_ND, 0, st>>>(c, sw.hist, sw.base, status);
     uint2 *a0 = listM, *a1 = listm, *b0 = tmpM, *b1 = tmpm;
     const uint32_t pg = hmin<uint32_t>(max_tiles, (uint32_t)sms * 4);
     for (int pass = 0; pass < 4; pass++) {
         uint32_t* cur = (pass & 1) ? sw.desc_b : sw.desc_a;
         uint32_t* nxt = (pass & 1) ? sw.desc_a : sw.desc_b;
-        k_os_pass<<<dim3(pg ? pg : 1, 2), 256, 0, st>>>(a0, a1, b0, b1, c, sw.base, cur, nxt, sw.stride,
+        k_os_pass<<<dim3(pg ? pg : 1, 2), OS_WARPS * 32, 0, st>>>(a0, a1, b0, b1, c, sw.base, cur, nxt, sw.stride,
                                                          sw.ctr + 2 * pass, pass, status);
         uint2* t0 = a0; a0 = b0; b0 = t0;
         uint2* t1 = a1; a1 = b1; b1 = t1;
     }
-    // after 4 passes the sorted data is back in listM / listm
+    // the sorted lists are in listM / listm after an even number of passes,
+    // in tmpM / tmpm after an odd one (the kernels read the count)
     dim3 grid(G, 2);
-    k_rank_tiles<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, G, status);
+    k_rank_tiles<<<grid, 256, 0, st>>>(listM, listm, tmpM, tmpm, c, agg, agg_stride, G, status);
     k_rank_scan<<<2, 256, 0, st>>>(agg, agg_stride, c, status);
-    k_rank_scatter<<<grid, 256, 0, st>>>(listM, listm, c, agg, agg_stride, tpre, delta, G, status);
+    k_rank_scatter<<<grid, 256, 0, st>>>(listM, listm, tmpM, tmpm, c, agg, agg_stride, tpre, delta, G, status);
 }
 
 void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* scratch, uint8_t* out,
@@ -1291,7 +1340,7 @@ void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* s
     if (grid == 0) grid = 1;
     k_encode_ranks<<<grid, 256, 0, st>>>(delta, c, tcnt, scratch, out, status);
     k_rank_tile_scan<<<1, 1024, 0, st>>>(tcnt, c, status);
-    uint32_t cg = hmin<uint32_t>((max_tiles + 7) / 8, (uint32_t)sms * 16);
+    uint32_t cg = hmin<uint32_t>(max_tiles, (uint32_t)sms * 8);
     k_rank_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, c, out, status);
 }
 
