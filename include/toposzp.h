@@ -180,7 +180,10 @@ uint64_t toposzp_noalloc_max_points(void);
  *                        neighbourhood into a compact record first (default);
  *                        -1: they read the field directly
  *   dec_split            0: one fused wavefront kernel decodes (default);
- *                        1: its four stages run as separate launches */
+ *                        1: its four stages run as separate launches
+ *   rank_bitmap          0: dense ranks from bitmaps over the key span when
+ *                        they fit the workspace, else a radix sort (default);
+ *                        -1: always the radix sort */
 typedef struct {
     int32_t cd_threads;
     int32_t cd_blocks_per_sm;
@@ -188,6 +191,7 @@ typedef struct {
     int32_t dec_slack_tiles;
     int32_t saddle_records;
     int32_t dec_split;
+    int32_t rank_bitmap;
 } toposzp_tuning;
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
 

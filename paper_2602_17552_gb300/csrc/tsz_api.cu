@@ -258,7 +258,7 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
         sw.stride = w.os_stride;
         sw.max_tiles = w.os_tiles;
         launch_ranks(c, listM, listm, reinterpret_cast<uint2*>(ws + w.tmpM),
-                     reinterpret_cast<uint2*>(ws + w.tmpm), sw, reinterpret_cast<uint2*>(ws + w.agg),
+                     reinterpret_cast<uint2*>(ws + w.tmpm), w.agg - w.tmpM, sw, reinterpret_cast<uint2*>(ws + w.agg),
                      w.agg_stride, tcnt, reinterpret_cast<int32_t*>(ws + w.delta), w.G, sms, status, st);
         // the rank payload slots reuse the sort's buffers (free again by now)
         launch_encode_ranks(reinterpret_cast<int32_t*>(ws + w.delta), c, reinterpret_cast<uint2*>(ws + w.rdesc),
@@ -365,6 +365,7 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     if (t->dec_slack_tiles < 0 || t->dec_slack_tiles > 65536) return TOPOSZP_ERR_INVALID_ARG;
     if (t->saddle_records < -1 || t->saddle_records > 1) return TOPOSZP_ERR_INVALID_ARG;
     if (t->dec_split < 0 || t->dec_split > 1) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->rank_bitmap < -1 || t->rank_bitmap > 0) return TOPOSZP_ERR_INVALID_ARG;
     Tuning u;
     if (t->cd_threads) u.cd_threads = t->cd_threads;
     if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
@@ -372,6 +373,7 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     u.dec_slack_tiles = t->dec_slack_tiles;
     u.saddle_records = t->saddle_records;
     u.dec_split = t->dec_split;
+    u.rank_bitmap = t->rank_bitmap;
     g_tuning = u;
     return TOPOSZP_OK;
 }

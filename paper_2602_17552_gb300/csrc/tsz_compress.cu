@@ -761,7 +761,7 @@ __global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s
                                                  uint32_t* ghist /* [2][4][512] */, uint32_t* desc_a,
                                                  uint32_t* desc_b, uint32_t desc_stride, const int* status) {
     __shared__ uint32_t h[4][4 * OS_ND];
-    if (*status) return;
+    if (*status || c->rank_bitmap) return;
     const SortPlan sp = sort_plan(c);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) c->sort_passes = (uint32_t)sp.passes;
     if (sp.passes == 0) return;
@@ -799,7 +799,7 @@ __global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s
 __global__ void __launch_bounds__(512) k_os_bases(const Ctrl* c, const uint32_t* ghist, uint32_t* base,
                                                   const int* status) {
     __shared__ uint32_t s_w[16];
-    if (*status) return;
+    if (*status || c->rank_bitmap) return;
     const int row = blockIdx.x;   // list * 4 + pass
     if ((row & 3) >= (int)c->sort_passes) return;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -824,7 +824,7 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_os_pass(const uint2* s0, cons
     __shared__ uint32_t s_tile;
     __shared__ uint16_t wcnt[OS_WARPS][OS_ND];
     __shared__ uint32_t gofs[OS_ND];
-    if (*status) return;
+    if (*status || c->rank_bitmap) return;
     const SortPlan sp = sort_plan(c);
     if (pass >= sp.passes) return;
     const int list = blockIdx.y;
@@ -996,7 +996,7 @@ __global__ void __launch_bounds__(256) k_rank_tiles(const uint2* l0, const uint2
                                                     uint2* agg, uint32_t agg_stride, int G,
                                                     const int* status) {
     __shared__ SegCnt s_tot[8];
-    if (*status) return;
+    if (*status || c->rank_bitmap) return;
     const int list = blockIdx.y;
     const bool odd = c->sort_passes & 1u;   // an odd number of passes ends in the second buffer
     const uint2* s = list ? (odd ? t1 : l1) : (odd ? t0 : l0);
@@ -1020,7 +1020,7 @@ __global__ void __launch_bounds__(256) k_rank_tiles(const uint2* l0, const uint2
 __global__ void __launch_bounds__(256) k_rank_scan(uint2* agg, uint32_t agg_stride, const Ctrl* c,
                                                    const int* status) {
     __shared__ SegCnt sh[256];
-    if (*status) return;
+    if (*status || c->rank_bitmap) return;
     const int list = blockIdx.x;
     const uint32_t k = list ? c->cnt_min : c->cnt_max;
     const uint32_t ntiles = (uint32_t)cdiv(k, RANK_TILE);
@@ -1054,7 +1054,7 @@ __global__ void __launch_bounds__(256) k_rank_scatter(const uint2* l0, const uin
                                                       const uint2* agg, uint32_t agg_stride, const uint2* tpre,
                                                       int32_t* delta, int G, const int* status) {
     __shared__ SegCnt s_tot[8];
-    if (*status) return;
+    if (*status || c->rank_bitmap) return;
     const int list = blockIdx.y;
     const bool odd = c->sort_passes & 1u;   // an odd number of passes ends in the second buffer
     const uint2* s = list ? (odd ? t1 : l1) : (odd ? t0 : l0);
@@ -1307,9 +1307,183 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2*
                                             status);
 }
 
-void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, const SortWs& sw,
-                  uint2* agg, uint32_t agg_stride, const uint2* tpre, int32_t* delta, int G, int sms, int* status,
-                  cudaStream_t st) {
+// ====================================================== dense ranks from bitmaps
+//
+// When the keys' span 2^B (bits of key - smallest key, from the range pass)
+// fits the workspace, the dense ranks need no sort.  Per list, a bitmap over
+// the span marks the keys present; an exclusive popcount prefix per word gives
+// P(x) = number of distinct keys below x.  Bins (QZ codes) are contiguous key
+// intervals (quantisation is monotone in the value, ord() in the key), so
+// delta = 1 + P(key) - P(lo), lo = the smallest key of the entry's bin, found
+// by a binary search on the quantiser.  Layout in the region: bitmap 0,
+// prefix 0, bitmap 1, prefix 1 (W words each).  Same deltas as the sort path.
+
+constexpr uint32_t BM_CHUNK = 8192;   // words per prefix chunk (one CTA)
+
+__device__ __forceinline__ int32_t key_bin(uint32_t key, int list, float r) {
+    return quantize(key_float(list ? ~key : key), r);
+}
+
+// Decides the mode and zeroes the two bitmaps.
+__global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsigned long long region_bytes,
+                                                 int force_sort, const int* status) {
+    if (*status) return;
+    const SortPlan sp = sort_plan(c);
+    const uint32_t kmax = c->max_key, kmin = ~c->min_inv;
+    const uint32_t span = kmax > kmin ? kmax - kmin : 0u;
+    const int B = span ? 32 - __clz(span) : 0;
+    const unsigned long long W = B <= 31 ? ((1ull << B) + 31) / 32 + 1 : 0ull;
+    const bool use = !force_sort && sp.passes > 0 && B <= 31 && 16ull * W <= region_bytes;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->rank_bitmap = use ? 1u : 0u;
+        c->bm_words = use ? (uint32_t)W : 0u;
+    }
+    if (!use) return;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < W;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        region[i] = 0u;
+        region[2 * W + i] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_bm_set(const uint2* s0, const uint2* s1, Ctrl* c, uint32_t* region,
+                                                const int* status) {
+    if (*status || !c->rank_bitmap) return;
+    const SortPlan sp = sort_plan(c);
+    const uint32_t W = c->bm_words;
+    const int list = blockIdx.y;
+    const uint2* s = list ? s1 : s0;
+    const uint32_t k = list_count(c, list), base = sp.base[list];
+    uint32_t* bm = region + (size_t)list * 2 * W;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        const uint32_t rel = s[i].x - base;
+        atomicOr(bm + (rel >> 5), 1u << (rel & 31));
+    }
+}
+
+// popcount of every BM_CHUNK-word chunk of both bitmaps
+__global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region, uint32_t* csum,
+                                                 const int* status) {
+    __shared__ uint32_t s_w[8];
+    if (*status || !c->rank_bitmap) return;
+    const uint32_t W = c->bm_words, nch = (W + BM_CHUNK - 1) / BM_CHUNK;
+    for (uint32_t q = blockIdx.x; q < 2 * nch; q += gridDim.x) {
+        const uint32_t list = q / nch, ch = q % nch;
+        const uint32_t* bm = region + (size_t)list * 2 * W + (size_t)ch * BM_CHUNK;
+        const uint32_t nw = min(BM_CHUNK, W - ch * BM_CHUNK);
+        uint32_t a = 0;
+        for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) a += __popc(bm[i]);
+        a = __reduce_add_sync(FULL, a);
+        if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < 8; w++) t += s_w[w];
+            csum[q] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// exclusive popcount prefix of every word (chunk offsets summed from csum)
+__global__ void __launch_bounds__(1024) k_bm_prefix(Ctrl* c, uint32_t* region, const uint32_t* csum,
+                                                    const int* status) {
+    __shared__ uint32_t s_w[32];
+    __shared__ uint32_t s_off;
+    if (*status || !c->rank_bitmap) return;
+    const uint32_t W = c->bm_words, nch = (W + BM_CHUNK - 1) / BM_CHUNK;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t q = blockIdx.x; q < 2 * nch; q += gridDim.x) {
+        const uint32_t list = q / nch, ch = q % nch;
+        // offset: the chunk sums before this one in its list
+        uint32_t o = 0;
+        for (uint32_t i = threadIdx.x; i < ch; i += blockDim.x) o += csum[list * nch + i];
+        o = __reduce_add_sync(FULL, o);
+        if (lane == 0) s_w[warp] = o;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < 32; w++) t += s_w[w];
+            s_off = t;
+        }
+        __syncthreads();
+        uint32_t run = s_off;
+        const uint32_t* bm = region + (size_t)list * 2 * W + (size_t)ch * BM_CHUNK;
+        uint32_t* pre = region + (size_t)list * 2 * W + W + (size_t)ch * BM_CHUNK;
+        const uint32_t nw = min(BM_CHUNK, W - ch * BM_CHUNK);
+        for (uint32_t b0 = 0; b0 < nw; b0 += 1024) {
+            const uint32_t i = b0 + threadIdx.x;
+            const uint32_t v = i < nw ? __popc(bm[i]) : 0u;
+            uint32_t inc = v;
+#pragma unroll
+            for (int of = 1; of < 32; of <<= 1) {
+                const uint32_t t = __shfl_up_sync(FULL, inc, of);
+                if (lane >= (uint32_t)of) inc += t;
+            }
+            __syncthreads();
+            if (lane == 31) s_w[warp] = inc;
+            __syncthreads();
+            uint32_t wp = 0, tot = 0;
+            for (uint32_t w = 0; w < 32; w++) {
+                const uint32_t x = s_w[w];
+                if (w < warp) wp += x;
+                tot += x;
+            }
+            if (i < nw) pre[i] = run + wp + inc - v;
+            run += tot;
+        }
+        __syncthreads();
+    }
+}
+
+// P(x): distinct keys of the list below relative key x
+__device__ __forceinline__ uint32_t bm_rank(const uint32_t* bm, const uint32_t* pre, uint32_t x) {
+    const uint32_t w = x >> 5, b = x & 31;
+    return pre[w] + __popc(bm[w] & ((1u << b) - 1u));
+}
+
+__global__ void __launch_bounds__(256) k_rank_delta(const uint2* s0, const uint2* s1, Ctrl* c,
+                                                    const uint32_t* region, const uint2* tpre, int32_t* delta,
+                                                    const int* status) {
+    if (*status || !c->rank_bitmap) return;
+    const SortPlan sp = sort_plan(c);
+    const uint32_t W = c->bm_words;
+    const float r = c->r_f;
+    const int list = blockIdx.y;
+    const uint2* s = list ? s1 : s0;
+    const uint32_t k = list_count(c, list), base = sp.base[list];
+    const uint32_t* bm = region + (size_t)list * 2 * W;
+    const uint32_t* pre = bm + W;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
+        const uint2 e = s[i];
+        const uint32_t rel = e.x - base;
+        const int32_t q = key_bin(e.x, list, r);
+        // smallest relative key of the bin: the bin is a key interval holding rel
+        uint32_t lo = 0, hi = rel;
+        while (lo < hi) {
+            const uint32_t mid = lo + ((hi - lo) >> 1);
+            const int32_t qm = key_bin(mid + base, list, r);
+            if (list ? qm > q : qm < q) lo = mid + 1;
+            else hi = mid;
+        }
+        const uint32_t d = 1u + bm_rank(bm, pre, rel) - bm_rank(bm, pre, lo);
+        delta[tpre[e.y >> TILE_POS_BITS].y + (e.y & ((1u << TILE_POS_BITS) - 1))] = (int32_t)d;
+    }
+}
+
+void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint64_t tmp_bytes,
+                  const SortWs& sw, uint2* agg, uint32_t agg_stride, const uint2* tpre, int32_t* delta, int G,
+                  int sms, int* status, cudaStream_t st) {
+    // dense ranks from key bitmaps when the key span fits tmpM..tmpm; every
+    // kernel of the other path then returns at once (and the other way round)
+    uint32_t* region = reinterpret_cast<uint32_t*>(tmpM);
+    uint32_t* csum = reinterpret_cast<uint32_t*>(agg);
+    const uint32_t bg = (uint32_t)sms * 8;
+    k_bm_zero<<<bg, 256, 0, st>>>(c, region, tmp_bytes, g_tuning.rank_bitmap < 0 ? 1 : 0, status);
+    k_bm_set<<<dim3(bg, 2), 256, 0, st>>>(listM, listm, c, region, status);
+    k_bm_sums<<<bg, 256, 0, st>>>(c, region, csum, status);
+    k_bm_prefix<<<(uint32_t)sms * 2, 1024, 0, st>>>(c, region, csum, status);
+    k_rank_delta<<<dim3(bg, 2), 256, 0, st>>>(listM, listm, c, region, tpre, delta, status);
     const uint32_t max_tiles = sw.max_tiles;
     uint32_t hg = hmin<uint32_t>((uint32_t)cdiv((uint64_t)max_tiles * OS_TILE, 256), (uint32_t)sms * 4);
     if (hg == 0) hg = 1;

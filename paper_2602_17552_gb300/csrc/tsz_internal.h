@@ -15,6 +15,7 @@ struct Tuning {
     int dec_slack_tiles = 0;        // 0: a quarter of the fused decoder's resident CTAs
     int saddle_records = 0;         // >= 0: neighbourhood records in the saddle rounds; < 0: field reads
     int dec_split = 0;              // > 0: the decoder stages as separate launches instead of fused
+    int rank_bitmap = 0;            // 0: dense ranks from key bitmaps when they fit; < 0: always the sort
 };
 extern Tuning g_tuning;
 
@@ -46,9 +47,9 @@ void launch_qparams(Ctrl* c, int* status, cudaStream_t st);
 void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2* tcnt, uint32_t* scratch,
                          uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo, uint32_t nb,
                          int sms, int* status, cudaStream_t st);
-void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, const SortWs& sw,
-                  uint2* agg, uint32_t agg_stride, const uint2* tpre, int32_t* delta, int G, int sms, int* status,
-                  cudaStream_t st);
+void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint64_t tmp_bytes,
+                  const SortWs& sw, uint2* agg, uint32_t agg_stride, const uint2* tpre, int32_t* delta, int G,
+                  int sms, int* status, cudaStream_t st);
 void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* scratch, uint8_t* out,
                          uint64_t max_k, int sms, int* status, cudaStream_t st);
 void launch_count_saddles(const uint32_t* labels, Ctrl* c, uint32_t n, int sms, int* status,

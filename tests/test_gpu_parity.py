@@ -184,3 +184,21 @@ def test_parity_config3_full():
     a = synth.turbulence_3d(512, seed=3, device="cuda").cpu().numpy()
     for eb in (1e-3, 1e-5):
         assert_parity(a, eb, rel=True)
+
+
+def test_parity_rank_paths_narrow_key_span():
+    """A positive field inside one binade (keys span < 2^23) large enough for
+    the dense ranks to come from key bitmaps; the same stream as the radix-sort
+    path and as the oracle."""
+    from paper_2602_17552_gb300 import autotune
+    g = synth.grf((96, 96, 96), -11 / 3, 21).numpy()
+    a = (384.0 + 100.0 * np.tanh(g / 3.0)).astype(np.float32)   # inside [256, 512)
+    assert a.min() > 256 and a.max() < 512
+    obuf, _ = assert_parity(a, 1e-3, rel=True)
+    f = torch.from_numpy(a).cuda()
+    try:
+        autotune.apply({**autotune.DEFAULT, "rank_bitmap": -1})
+        sorted_path = codec.compress(f, 1e-3, "rel").cpu().numpy().tobytes()
+    finally:
+        autotune.apply(autotune.DEFAULT)
+    assert sorted_path == obuf
