@@ -1388,50 +1388,28 @@ __global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region
 // exclusive popcount prefix of every word (chunk offsets summed from csum)
 __global__ void __launch_bounds__(1024) k_bm_prefix(Ctrl* c, uint32_t* region, const uint32_t* csum,
                                                     const int* status) {
-    __shared__ uint32_t s_w[32];
-    __shared__ uint32_t s_off;
+    __shared__ unsigned long long s_w[33][2];
+    __shared__ uint32_t s_o[32];
     if (*status || !c->rank_bitmap) return;
     const uint32_t W = c->bm_words, nch = (W + BM_CHUNK - 1) / BM_CHUNK;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (uint32_t q = blockIdx.x; q < 2 * nch; q += gridDim.x) {
         const uint32_t list = q / nch, ch = q % nch;
         // offset: the chunk sums before this one in its list
         uint32_t o = 0;
         for (uint32_t i = threadIdx.x; i < ch; i += blockDim.x) o += csum[list * nch + i];
         o = __reduce_add_sync(FULL, o);
-        if (lane == 0) s_w[warp] = o;
+        if ((threadIdx.x & 31) == 0) s_o[threadIdx.x >> 5] = o;
         __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t t = 0;
-            for (int w = 0; w < 32; w++) t += s_w[w];
-            s_off = t;
-        }
-        __syncthreads();
-        uint32_t run = s_off;
+        uint32_t off = 0;
+        for (int w = 0; w < 32; w++) off += s_o[w];
         const uint32_t* bm = region + (size_t)list * 2 * W + (size_t)ch * BM_CHUNK;
         uint32_t* pre = region + (size_t)list * 2 * W + W + (size_t)ch * BM_CHUNK;
         const uint32_t nw = min(BM_CHUNK, W - ch * BM_CHUNK);
-        for (uint32_t b0 = 0; b0 < nw; b0 += 1024) {
-            const uint32_t i = b0 + threadIdx.x;
-            const uint32_t v = i < nw ? __popc(bm[i]) : 0u;
-            uint32_t inc = v;
-#pragma unroll
-            for (int of = 1; of < 32; of <<= 1) {
-                const uint32_t t = __shfl_up_sync(FULL, inc, of);
-                if (lane >= (uint32_t)of) inc += t;
-            }
-            __syncthreads();
-            if (lane == 31) s_w[warp] = inc;
-            __syncthreads();
-            uint32_t wp = 0, tot = 0;
-            for (uint32_t w = 0; w < 32; w++) {
-                const uint32_t x = s_w[w];
-                if (w < warp) wp += x;
-                tot += x;
-            }
-            if (i < nw) pre[i] = run + wp + inc - v;
-            run += tot;
-        }
+        unsigned long long ta, tb;
+        cta_scan_pairs(
+            nw, [&](uint32_t i) { return make_uint2((uint32_t)__popc(bm[i]), 0u); },
+            [&](uint32_t i, unsigned long long pa, unsigned long long) { pre[i] = off + (uint32_t)pa; }, s_w, ta,
+            tb);
         __syncthreads();
     }
 }
@@ -1458,13 +1436,34 @@ __global__ void __launch_bounds__(256) k_rank_delta(const uint2* s0, const uint2
         const uint2 e = s[i];
         const uint32_t rel = e.x - base;
         const int32_t q = key_bin(e.x, list, r);
-        // smallest relative key of the bin: the bin is a key interval holding rel
-        uint32_t lo = 0, hi = rel;
-        while (lo < hi) {
-            const uint32_t mid = lo + ((hi - lo) >> 1);
-            const int32_t qm = key_bin(mid + base, list, r);
-            if (list ? qm > q : qm < q) lo = mid + 1;
-            else hi = mid;
+        // smallest relative key of the bin (the bin is a key interval holding
+        // rel): start from the bin edge (q -+ 0.5) / r in binary32, a few ulps
+        // off at most, and step to the exact edge; a binary search if the
+        // steps do not settle
+        const float edge = __fdiv_rn(list ? (float)q + 0.5f : (float)q - 0.5f, r);
+        const uint32_t gk = list ? ~ord_key(edge) : ord_key(edge);
+        const long long gr = (long long)gk - (long long)base;
+        uint32_t lo = gr < 0 ? 0u : (gr > (long long)rel ? rel : (uint32_t)gr);
+        bool ok = false;
+        for (int it = 0; it < 16; it++) {
+            if (key_bin(lo + base, list, r) != q) {
+                lo++;   // below the bin: its keys are larger
+            } else if (lo > 0 && key_bin(lo - 1 + base, list, r) == q) {
+                lo--;
+            } else {
+                ok = true;
+                break;
+            }
+        }
+        if (!ok) {
+            uint32_t a = 0, hi = rel;
+            while (a < hi) {
+                const uint32_t mid = a + ((hi - a) >> 1);
+                const int32_t qm = key_bin(mid + base, list, r);
+                if (list ? qm > q : qm < q) a = mid + 1;
+                else hi = mid;
+            }
+            lo = a;
         }
         const uint32_t d = 1u + bm_rank(bm, pre, rel) - bm_rank(bm, pre, lo);
         delta[tpre[e.y >> TILE_POS_BITS].y + (e.y & ((1u << TILE_POS_BITS) - 1))] = (int32_t)d;
