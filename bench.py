@@ -35,6 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 NOMINAL_HBM_GBS = 8000.0
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
+# kernel, per field point, from one ncu capture of the 512^3 workload at relative
+# eb 1e-3 (profiles/launches_turb512_rel1e-3.md); reported only for that workload
+# and only while the kernel is unchanged since the capture.
+TRAFFIC_PER_POINT = {"k_decode_fused": 812.1e6 / 512 ** 3}
 
 
 def parse_args():
@@ -294,13 +299,16 @@ def run_ours(args):
     nb = (n + 31) // 32
     lab_bytes = 4 * ((n + 15) // 16) if topo else 0
     field_sections = (h["off_s6"] - h["off_s1"]) + 4 * h["pay_words"]   # S1, S2, S4, S5 (+ padding)
+    # library stages between its stage events (tsz_api.cu): the dominant one
+    # with algorithmic bytes gives the roofline line
     kernels = {
-        "k_range_cd": (stage_ms(0, 1), 4 * n + lab_bytes),
+        "k_range_cd_vec": (stage_ms(0, 1), 4 * n + lab_bytes),
         "k_encode_field": (stage_ms(1, 2), 4 * n + lab_bytes + field_sections + 8 * k),
         "rank_stages": (stage_ms(2, 3), None),
-        "k_decode_field": (stage_ms(5, 6), nb + 4 * nb + 4 * h["pay_words"] + lab_bytes + 4 * n + 4 * k),
-        "k_decode_ranks": (stage_ms(6, 7), None),
-        "k_fixup": (stage_ms(7, 8), None),
+        "finalize": (stage_ms(3, 4), None),
+        "decode_header_offsets_ranks": (stage_ms(5, 6), None),
+        "k_decode_fused": (stage_ms(6, 7), nb + 4 * nb + 4 * h["pay_words"] + lab_bytes + 4 * n + 4 * k),
+        "k_saddle_rounds": (stage_ms(7, 8), None),
     }
     peaks = measured_peaks()
     peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
@@ -314,13 +322,17 @@ def run_ours(args):
                       "frac_nominal_8tbs": round(gbs / NOMINAL_HBM_GBS, 4)})
         kout[name] = d
     dom = max((kname for kname in kout if "alg_bytes" in kout[kname]), key=lambda kk: kout[kk]["ms"])
+    traffic = None
+    if dom in TRAFFIC_PER_POINT and topo and args.workload == "turb512" and args.eb == 1e-3 and args.side == 512:
+        traffic = int(TRAFFIC_PER_POINT[dom] * n)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": kout[dom]["achieved_gbs"], "peak": peak,
-                "unit": "GB/s", "frac": kout[dom]["frac"], "traffic": None,
+                "unit": "GB/s", "frac": kout[dom]["frac"], "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
     nbytes_all = 4 * n * ws_n
     value = nbytes_all * args.steps / (total_ms * 1e-3) / 1e9
-    # kernels per call (tsz_api.cu launch sequences)
-    launches_c = 15 if topo else 5
+    # kernels per call (tsz_api.cu launch sequences; on the key-bitmap path the
+    # radix-sort kernels are launched and return at once)
+    launches_c = 24 if topo else 7
     launches_d = 6
     result = {
         "metric": "compress+decompress throughput (uncompressed bytes / round-trip time)",

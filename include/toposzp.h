@@ -199,8 +199,9 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
  * count > 0, every toposzp_compress records events[0..4] (cudaEvent_t handles
  * owned by the caller) on its stream: before the range + CD kernel, after it,
  * after the field encoder, after the rank stages, at the end; and every
- * toposzp_decompress records events[5..8]: at the start, after the field
- * decoder, after the rank decoder, at the end.  count must be 0 (off) or 9.
+ * toposzp_decompress records events[5..8]: at the start, after the header,
+ * offsets and rank-stream decode, after the fused field decoder, at the end
+ * (after the saddle rounds).  count must be 0 (off) or 9.
  * The setting is process-wide and not thread-safe; it is meant for a
  * single-threaded benchmark. */
 toposzp_status toposzp_set_stage_events(void* const* events, int count);

@@ -326,7 +326,8 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
     Ctrl* c = reinterpret_cast<Ctrl*>(ws + w.ctrl);
     const int sms = sm_count();
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
-    cudaMemsetAsync(ws, 0, w.tile_w, st);   // control block, rank look-back descriptors, stage flags
+    cudaMemsetAsync(ws, 0, w.tile_w, st);   // control block, rank tile sums, stage flags
+    stage(5, st);
     launch_parse_header(src, in_size, n_out, c, status, st);
     // the rank stream's tile sums and prefixes live in the (no longer used) rank descriptor region
     uint32_t* rtile = reinterpret_cast<uint32_t*>(ws + w.rdesc);
@@ -334,13 +335,12 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
                        reinterpret_cast<unsigned long long*>(ws + w.pay_pre), reinterpret_cast<uint32_t*>(ws + w.cp_pre),
                        rtile, w.ntiles, sms, status, st);
     launch_decode_ranks(src, c, rtile, reinterpret_cast<int32_t*>(ws + w.delta), n_out, sms, status, st);
-    stage(5, st);
+    stage(6, st);
     launch_decode_fused(src, c, out, reinterpret_cast<unsigned long long*>(ws + w.pay_pre),
                         reinterpret_cast<uint32_t*>(ws + w.cp_pre), reinterpret_cast<int32_t*>(ws + w.delta),
                         reinterpret_cast<uint32_t*>(ws + w.cp_idx), reinterpret_cast<float*>(ws + w.newv),
                         reinterpret_cast<uint32_t*>(ws + w.flags), reinterpret_cast<uint32_t*>(ws + w.sad),
                         w.sad_cap, w.ntiles, 64u, sms, status, st);
-    stage(6, st);
     stage(7, st);
     // the stencil values are consumed by now: their buffer holds the colour
     // buckets; the extremum positions and ranks (contiguous) hold the records
