@@ -782,7 +782,8 @@ struct FusedArgs {
 // CTA-wide scan of the widths, rebuilds the 32 magnitudes from the planes with
 // register bit operations, applies the signs and the Lorenzo prefix, and
 // writes D0 through a padded shared buffer so that the stores are coalesced.
-// TOPO: the tile's extrema positions, in index order, go to cp_idx.
+// TOPO: the tile's extrema positions, in index order, go to cp_idx (bit 31:
+// the point is a maximum).
 constexpr int DT_ROW = 36;   // shared words per staged output row (conflict-free 16-byte accesses)
 
 template <bool TOPO>
@@ -801,14 +802,16 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
     else corrupt = true;
     for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_pay[i] = __ldg(pay + P0 + i);
     const uint32_t b = t * DT_BLOCKS + threadIdx.x;   // this thread's block
-    uint32_t w = 0, xm = 0;
+    uint32_t w = 0, xm = 0, xM = 0;
     int32_t first = 0;
     if (b < g.nb) {
         w = __ldg(widths + b);
         first = __ldg(firsts + b);
         if (w > 32) w = 0;   // a damaged stream (the offset pre-pass flags it)
         if (TOPO) {   // m = 01, M = 11: the low bit marks an extremum
-            xm = compact16(label_word(labels, 2 * b, g.n)) | compact16(label_word(labels, 2 * b + 1, g.n)) << 16;
+            const uint32_t l0 = label_word(labels, 2 * b, g.n), l1 = label_word(labels, 2 * b + 1, g.n);
+            xm = compact16(l0) | compact16(l1) << 16;
+            xM = compact16(l0 & (l0 >> 1)) | compact16(l1 & (l1 >> 1)) << 16;   // M = 11
         }
     }
     const uint32_t words = w ? 1u + w : 0u, ncp = __popc(xm);
@@ -866,7 +869,8 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
         while (xm) {
             const int e = __ffs(xm) - 1;
             xm &= xm - 1;
-            if (pos < k) A.cp_idx[pos] = b * 32u + (uint32_t)e;
+            // bit 31 carries the type (1: maximum), so the stencil stage needs no label load
+            if (pos < k) A.cp_idx[pos] = (b * 32u + (uint32_t)e) | ((xM >> e) & 1u) << 31;
             else corrupt = true;
             pos++;
         }
@@ -901,11 +905,12 @@ struct ExtIn {
 
 __device__ __forceinline__ void ext_load(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t pos,
                                          ExtIn& e) {
-    const uint32_t p = __ldcg(A.cp_idx + pos);
+    const uint32_t raw = __ldcg(A.cp_idx + pos);
+    const uint32_t p = raw & 0x7FFFFFFFu;
     e.ok = p < g.n;   // only a damaged stream fails this (its checks already failed)
     if (!e.ok) return;
     const uint32_t st[3] = {1u, g.nx, g.nxy};
-    e.lab = label_at(labels, p);
+    e.lab = raw >> 31 ? LAB_MAX : LAB_MIN;
     e.dl = __ldg(A.delta + pos);
     uint32_t x, y, z;
     coords(g, p, x, y, z);
@@ -922,8 +927,7 @@ __device__ __forceinline__ void ext_load(const FusedArgs& A, const Geo& g, const
     }
 }
 
-__device__ __forceinline__ float ext_eval(const ExtIn& e, float h_f, unsigned long long& restored,
-                                          unsigned long long& skipped) {
+__device__ __forceinline__ float ext_eval(const ExtIn& e, float h_f, uint32_t& restored, uint32_t& skipped) {
     float nv = __int_as_float(0x7FC00000);
     if (!e.ok) return nv;
     // type of p in D0: for a labelled extremum only m / M matter (no FT)
@@ -957,7 +961,7 @@ __device__ __forceinline__ float ext_eval(const ExtIn& e, float h_f, unsigned lo
 }
 
 __device__ void stage_extrema(const FusedArgs& A, const Geo& g, const uint32_t* labels, uint32_t s,
-                              unsigned long long& restored, unsigned long long& skipped) {
+                              uint32_t& restored, uint32_t& skipped) {
     const uint32_t P0 = A.cp_pre[s], P1 = A.cp_pre[s + 1];
     const float h_f = A.c->h_f;
     for (uint32_t pos = P0 + threadIdx.x; pos < P1; pos += blockDim.x) {
@@ -971,7 +975,7 @@ __device__ void stage_apply(const FusedArgs& A, const Geo& g, uint32_t s) {
     const uint32_t P0 = A.cp_pre[s], P1 = A.cp_pre[s + 1];
     for (uint32_t pos = P0 + threadIdx.x; pos < P1; pos += blockDim.x) {
         const float v = __ldcg(A.newv + pos);
-        const uint32_t p = __ldcg(A.cp_idx + pos);
+        const uint32_t p = __ldcg(A.cp_idx + pos) & 0x7FFFFFFFu;
         if (!isnan(v) && p < g.n) A.out[p] = v;
     }
 }
@@ -1089,7 +1093,7 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
     const uint32_t Lg = TOPO ? hmin<uint32_t>(H + A.slack, ntiles) : 0u;
     const uint32_t total = ntiles + 3 * Lg;
     bool corrupt = false;
-    unsigned long long restored = 0, skipped = 0;
+    uint32_t restored = 0, skipped = 0;   // per thread: at most the extrema it handled
     while (true) {
     if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_fused, 1u);
     __syncthreads();
@@ -1125,8 +1129,8 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
             skipped += __shfl_xor_sync(FULL, skipped, o);
         }
         if ((threadIdx.x & 31) == 0) {
-            if (restored) atomicAdd(&c->stat_restored, restored);
-            if (skipped) atomicAdd(&c->stat_skipped, skipped);
+            if (restored) atomicAdd(&c->stat_restored, (unsigned long long)restored);
+            if (skipped) atomicAdd(&c->stat_skipped, (unsigned long long)skipped);
         }
     }
 }
@@ -1157,7 +1161,7 @@ __global__ void __launch_bounds__(256, 4) k_decode_stage(FusedArgs A) {
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
     const uint32_t ntiles = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
     bool corrupt = false;
-    unsigned long long restored = 0, skipped = 0;
+    uint32_t restored = 0, skipped = 0;   // per thread: at most the extrema it handled
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         if (K == 1) {
             if (topo) stage_decode<true>(A, g, lo, t, S.pay, S.w, S.cp, corrupt);
@@ -1179,8 +1183,8 @@ __global__ void __launch_bounds__(256, 4) k_decode_stage(FusedArgs A) {
             skipped += __shfl_xor_sync(FULL, skipped, o);
         }
         if ((threadIdx.x & 31) == 0) {
-            if (restored) atomicAdd(&c->stat_restored, restored);
-            if (skipped) atomicAdd(&c->stat_skipped, skipped);
+            if (restored) atomicAdd(&c->stat_restored, (unsigned long long)restored);
+            if (skipped) atomicAdd(&c->stat_skipped, (unsigned long long)skipped);
         }
     }
 }
