@@ -332,7 +332,7 @@ def run_ours(args):
     value = nbytes_all * args.steps / (total_ms * 1e-3) / 1e9
     # kernels per call (tsz_api.cu launch sequences; on the key-bitmap path the
     # radix-sort kernels are launched and return at once)
-    launches_c = 24 if topo else 7
+    launches_c = 23 if topo else 7
     launches_d = 6
     result = {
         "metric": "compress+decompress throughput (uncompressed bytes / round-trip time)",

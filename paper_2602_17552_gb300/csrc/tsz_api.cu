@@ -245,8 +245,8 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     launch_range_cd(field, g, c, labels, topo, sms, st);
     stage(1, st);
     launch_qparams(c, status, st);
-    launch_encode_field(field, labels, c, tcnt, reinterpret_cast<uint32_t*>(ws + w.tmpM), o, lo, listM, listm,
-                        topo, g.nb, sms, status, st);
+    launch_encode_field(field, labels, c, tcnt, reinterpret_cast<uint32_t*>(ws + w.tmpM), w.agg - w.tmpM, o, lo,
+                        listM, listm, topo, g.nb, sms, status, st);
     stage(2, st);
     if (topo) {
         SortWs sw;

@@ -112,7 +112,7 @@ __host__ __device__ inline void make_layout(uint64_t n, uint64_t nb, bool topo, 
 struct Ctrl {
     // range pass
     unsigned int min_inv, max_key, nonfinite, sort_passes;
-    unsigned int rank_bitmap, bm_words, pad_b0, pad_b1;   // dense ranks from key bitmaps (1) or the sort (0)
+    unsigned int rank_bitmap, bm_words, bm_off, pad_b1;   // dense ranks from key bitmaps (1) or the sort (0)
     // quantiser (Section II-C) and geometry, filled by the parameter kernel or
     // by the header parser
     int const_field, rel, rbf_k, rs_sweeps;

@@ -385,7 +385,7 @@ template <bool TOPO>
 __global__ void __launch_bounds__(256, 3) k_encode_field(const float* __restrict__ a,
                                                          const uint32_t* __restrict__ labels, Ctrl* c,
                                                          uint2* tcnt, EncOut o, uint2* listM, uint2* listm,
-                                                         int* status) {
+                                                         uint32_t* region, int* status) {
     __shared__ __align__(16) uint32_t s_buf[ENC_TILE_BLOCKS * ENC_ROW];
     __shared__ uint32_t s_wsum[8][3];
     __shared__ uint32_t s_base[2];
@@ -488,8 +488,19 @@ __global__ void __launch_bounds__(256, 3) k_encode_field(const float* __restrict
     }
     if (TOPO) {
         __syncthreads();
-        // (key, position) pairs of this block's extrema, in index order
+        // (key, position) pairs of this block's extrema, in index order; with
+        // the bitmap ranks also each key's bit in its list's bitmap
         const uint32_t* row = s_buf + t * ENC_ROW;
+        uint32_t* bmM = nullptr;
+        uint32_t* bmm = nullptr;
+        uint32_t baseM = 0, basem = 0;
+        if (c->rank_bitmap) {
+            const uint32_t W = c->bm_words;
+            bmM = region + c->bm_off;
+            bmm = bmM + 2 * (size_t)W;
+            baseM = ~c->min_inv;   // ord(vmin): the smallest maximum key
+            basem = ~c->max_key;   // ~ord(vmax): the smallest minimum key
+        }
         uint32_t oMg = s_base[0] + oM, omg = s_base[1] + om, local = oM + om;
         uint32_t xm = xmM | xmm;
         while (xm) {
@@ -497,8 +508,19 @@ __global__ void __launch_bounds__(256, 3) k_encode_field(const float* __restrict
             xm &= xm - 1;
             const uint32_t key = ord_key(__uint_as_float(row[e]));
             const uint32_t pos = tile << TILE_POS_BITS | local++;
-            if ((xmM >> e) & 1u) listM[oMg++] = make_uint2(key, pos);
-            else listm[omg++] = make_uint2(~key, pos);
+            if ((xmM >> e) & 1u) {
+                listM[oMg++] = make_uint2(key, pos);
+                if (bmM) {
+                    const uint32_t rel = key - baseM;
+                    atomicOr(bmM + (rel >> 5), 1u << (rel & 31));
+                }
+            } else {
+                listm[omg++] = make_uint2(~key, pos);
+                if (bmm) {
+                    const uint32_t rel = ~key - basem;
+                    atomicOr(bmm + (rel >> 5), 1u << (rel & 31));
+                }
+            }
         }
     }
     __syncthreads();   // the staged values are no longer read: the buffer takes the payload
@@ -1293,14 +1315,24 @@ void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsign
 
 void launch_qparams(Ctrl* c, int* status, cudaStream_t st) { k_qparams<<<1, 32, 0, st>>>(c, status); }
 
+__global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsigned long long region_bytes,
+                                                 unsigned long long slot_bytes, int force_sort, const int* status);
+
 void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2* tcnt, uint32_t* scratch,
-                         uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo, uint32_t nb,
-                         int sms, int* status, cudaStream_t st) {
+                         uint64_t region_bytes, uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo,
+                         uint32_t nb, int sms, int* status, cudaStream_t st) {
     EncOut o{reinterpret_cast<uint32_t*>(out + lo.s1), out + lo.s2,
              reinterpret_cast<int32_t*>(out + lo.s4), scratch};
     const uint32_t ntiles = (nb + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;   // one tile per CTA
-    if (topo) k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, status);
-    else k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, status);
+    if (topo) {
+        // the rank mode (key bitmaps or sort) is decided here, so the encoder can set the bits
+        const unsigned long long slot_bytes = 4ull * TILE_PAY * ntiles;
+        k_bm_zero<<<(uint32_t)sms * 8, 256, 0, st>>>(c, scratch, region_bytes, slot_bytes,
+                                                      g_tuning.rank_bitmap < 0 ? 1 : 0, status);
+        k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+    } else {
+        k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+    }
     k_enc_tile_scan<<<1, 1024, 0, st>>>(tcnt, ntiles, c, status);
     uint32_t cg = hmin<uint32_t>(ntiles, (uint32_t)sms * 8);
     k_enc_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, ntiles, reinterpret_cast<uint32_t*>(out + lo.s5),
@@ -1324,40 +1356,30 @@ __device__ __forceinline__ int32_t key_bin(uint32_t key, int list, float r) {
     return quantize(key_float(list ? ~key : key), r);
 }
 
-// Decides the mode and zeroes the two bitmaps.
+// Decides the mode and zeroes the two bitmaps.  They take the end of the
+// region (the field encoder's payload slots use its start while it sets the
+// bits); c->bm_off is their word offset.
 __global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsigned long long region_bytes,
-                                                 int force_sort, const int* status) {
+                                                 unsigned long long slot_bytes, int force_sort, const int* status) {
     if (*status) return;
     const SortPlan sp = sort_plan(c);
     const uint32_t kmax = c->max_key, kmin = ~c->min_inv;
     const uint32_t span = kmax > kmin ? kmax - kmin : 0u;
     const int B = span ? 32 - __clz(span) : 0;
     const unsigned long long W = B <= 31 ? ((1ull << B) + 31) / 32 + 1 : 0ull;
-    const bool use = !force_sort && sp.passes > 0 && B <= 31 && 16ull * W <= region_bytes;
+    const bool use = !force_sort && sp.passes > 0 && B <= 31 && slot_bytes + 16ull * W + 16 <= region_bytes;
+    const unsigned long long off = use ? ((region_bytes - 16ull * W) / 4) & ~3ull : 0ull;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->rank_bitmap = use ? 1u : 0u;
         c->bm_words = use ? (uint32_t)W : 0u;
+        c->bm_off = (uint32_t)off;
     }
     if (!use) return;
+    uint32_t* bm = region + off;
     for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < W;
          i += (unsigned long long)gridDim.x * blockDim.x) {
-        region[i] = 0u;
-        region[2 * W + i] = 0u;
-    }
-}
-
-__global__ void __launch_bounds__(256) k_bm_set(const uint2* s0, const uint2* s1, Ctrl* c, uint32_t* region,
-                                                const int* status) {
-    if (*status || !c->rank_bitmap) return;
-    const SortPlan sp = sort_plan(c);
-    const uint32_t W = c->bm_words;
-    const int list = blockIdx.y;
-    const uint2* s = list ? s1 : s0;
-    const uint32_t k = list_count(c, list), base = sp.base[list];
-    uint32_t* bm = region + (size_t)list * 2 * W;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
-        const uint32_t rel = s[i].x - base;
-        atomicOr(bm + (rel >> 5), 1u << (rel & 31));
+        bm[i] = 0u;
+        bm[2 * W + i] = 0u;
     }
 }
 
@@ -1367,6 +1389,7 @@ __global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region
     __shared__ uint32_t s_w[8];
     if (*status || !c->rank_bitmap) return;
     const uint32_t W = c->bm_words, nch = (W + BM_CHUNK - 1) / BM_CHUNK;
+    region += c->bm_off;
     for (uint32_t q = blockIdx.x; q < 2 * nch; q += gridDim.x) {
         const uint32_t list = q / nch, ch = q % nch;
         const uint32_t* bm = region + (size_t)list * 2 * W + (size_t)ch * BM_CHUNK;
@@ -1392,6 +1415,7 @@ __global__ void __launch_bounds__(1024) k_bm_prefix(Ctrl* c, uint32_t* region, c
     __shared__ uint32_t s_o[32];
     if (*status || !c->rank_bitmap) return;
     const uint32_t W = c->bm_words, nch = (W + BM_CHUNK - 1) / BM_CHUNK;
+    region += c->bm_off;
     for (uint32_t q = blockIdx.x; q < 2 * nch; q += gridDim.x) {
         const uint32_t list = q / nch, ch = q % nch;
         // offset: the chunk sums before this one in its list
@@ -1426,21 +1450,21 @@ __global__ void __launch_bounds__(256) k_rank_delta(const uint2* s0, const uint2
     if (*status || !c->rank_bitmap) return;
     const SortPlan sp = sort_plan(c);
     const uint32_t W = c->bm_words;
-    const float r = c->r_f;
+    const float r = c->r_f, w_f = c->w_f;
     const int list = blockIdx.y;
     const uint2* s = list ? s1 : s0;
     const uint32_t k = list_count(c, list), base = sp.base[list];
-    const uint32_t* bm = region + (size_t)list * 2 * W;
+    const uint32_t* bm = region + c->bm_off + (size_t)list * 2 * W;
     const uint32_t* pre = bm + W;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
         const uint2 e = s[i];
         const uint32_t rel = e.x - base;
         const int32_t q = key_bin(e.x, list, r);
         // smallest relative key of the bin (the bin is a key interval holding
-        // rel): start from the bin edge (q -+ 0.5) / r in binary32, a few ulps
+        // rel): start from the bin edge (q -+ 0.5) * w in binary32, a few ulps
         // off at most, and step to the exact edge; a binary search if the
         // steps do not settle
-        const float edge = __fdiv_rn(list ? (float)q + 0.5f : (float)q - 0.5f, r);
+        const float edge = __fmul_rn(list ? (float)q + 0.5f : (float)q - 0.5f, w_f);
         const uint32_t gk = list ? ~ord_key(edge) : ord_key(edge);
         const long long gr = (long long)gk - (long long)base;
         uint32_t lo = gr < 0 ? 0u : (gr > (long long)rel ? rel : (uint32_t)gr);
@@ -1475,11 +1499,10 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
                   int sms, int* status, cudaStream_t st) {
     // dense ranks from key bitmaps when the key span fits tmpM..tmpm; every
     // kernel of the other path then returns at once (and the other way round)
+    (void)tmp_bytes;   // the mode and the bitmaps were set up with the field encoder
     uint32_t* region = reinterpret_cast<uint32_t*>(tmpM);
     uint32_t* csum = reinterpret_cast<uint32_t*>(agg);
     const uint32_t bg = (uint32_t)sms * 8;
-    k_bm_zero<<<bg, 256, 0, st>>>(c, region, tmp_bytes, g_tuning.rank_bitmap < 0 ? 1 : 0, status);
-    k_bm_set<<<dim3(bg, 2), 256, 0, st>>>(listM, listm, c, region, status);
     k_bm_sums<<<bg, 256, 0, st>>>(c, region, csum, status);
     k_bm_prefix<<<(uint32_t)sms * 2, 1024, 0, st>>>(c, region, csum, status);
     k_rank_delta<<<dim3(bg, 2), 256, 0, st>>>(listM, listm, c, region, tpre, delta, status);

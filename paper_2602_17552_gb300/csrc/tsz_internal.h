@@ -45,8 +45,8 @@ void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsi
                             int sms, cudaStream_t st);
 void launch_qparams(Ctrl* c, int* status, cudaStream_t st);
 void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2* tcnt, uint32_t* scratch,
-                         uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo, uint32_t nb,
-                         int sms, int* status, cudaStream_t st);
+                         uint64_t region_bytes, uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo,
+                         uint32_t nb, int sms, int* status, cudaStream_t st);
 void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint64_t tmp_bytes,
                   const SortWs& sw, uint2* agg, uint32_t agg_stride, const uint2* tpre, int32_t* delta, int G,
                   int sms, int* status, cudaStream_t st);
