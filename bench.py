@@ -13,7 +13,9 @@ HBM).  Prints ONE JSON line (rank 0):
              bandwidth (MEASURED_PEAKS.json)
   e2e        the same metric through the public Python API with host buffers:
              pinned host field -> device -> compress -> compressed bytes to host
-             -> device -> decompress -> field to host, copies inside the timing
+             -> device -> decompress -> field to host, copies inside the timing;
+             a sequence of such round trips with four in flight on separate
+             streams (each step's copies overlap another step's kernels)
   cpu_baseline  the CPU oracle (single thread) on a bounded sample
 
 `--impl reference` times the CPU oracle itself as the reference arm.
@@ -40,6 +42,7 @@ NOMINAL_HBM_GBS = 8000.0
 # eb 1e-3 (profiles/launches_turb512_rel1e-3.md); reported only for that workload
 # and only while the kernel is unchanged since the capture.
 TRAFFIC_PER_POINT = {"k_decode_fused": 812.1e6 / 512 ** 3}
+E2E_IN_FLIGHT = int(os.environ.get("TOPOSZP_E2E_IN_FLIGHT", "4"))   # round trips in flight at once
 
 
 def parse_args():
@@ -57,7 +60,7 @@ def parse_args():
     ap.add_argument("--eb", type=float, default=1e-3)
     ap.add_argument("--side", type=int, default=512, help="edge of the 3D turbulence field")
     ap.add_argument("--no-topo", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=9)
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU-baseline work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -351,31 +354,85 @@ def run_ours(args):
         "kernels": kout, "roofline": roofline, "gpu_launches": (launches_c + launches_d) * args.steps,
         "clocks": clk.summary(),
     }
-    # ---- end to end through the public API with host buffers (every rank)
+    # ---- end to end through the public API with host buffers (every rank).
+    # Every step is a full round trip through host memory: the field from pinned
+    # host memory to the device, compression, the stream's bytes to the host
+    # (their count read back first), the stream back to the device,
+    # decompression, the field to the host.  Steps are independent fields of a
+    # sequence, so E2E_IN_FLIGHT of them are in flight on their own streams and
+    # buffers: one step's copies overlap another's kernels and the link runs
+    # both directions at once.
     if args.e2e_steps > 0:
         host = field.cpu().pin_memory()
-        hout = torch.empty(csize, dtype=torch.uint8).pin_memory()
-        hrec = torch.empty(field.shape, dtype=torch.float32).pin_memory()
-        times = []
-        for i in range(args.e2e_steps + 1):
+        shape = tuple(field.shape)
+        bound = codec.compress_bound(shape)
+        slots = []
+        for _ in range(E2E_IN_FLIGHT):
+            slots.append({
+                "stream": torch.cuda.Stream(dev),
+                "d_in": torch.empty_like(field),
+                "out": torch.empty(bound, dtype=torch.uint8, device=dev),
+                "back": torch.empty(bound, dtype=torch.uint8, device=dev),
+                "size": torch.zeros(1, dtype=torch.int64, device=dev),
+                "size_h": torch.zeros(1, dtype=torch.int64).pin_memory(),
+                "st_c": torch.zeros(1, dtype=torch.int32, device=dev),
+                "st_d": torch.zeros(1, dtype=torch.int32, device=dev),
+                "cws": torch.empty(codec.compress_workspace_size(shape), dtype=torch.uint8, device=dev),
+                "dws": torch.empty(codec.decompress_workspace_size(shape), dtype=torch.uint8, device=dev),
+                "rec": torch.empty_like(field),
+                "hout": torch.empty(bound, dtype=torch.uint8).pin_memory(),
+                "hrec": torch.empty(shape, dtype=torch.float32).pin_memory(),
+                "ev": torch.cuda.Event(),
+            })
+
+        def phase_a(i):
+            sl = slots[i % E2E_IN_FLIGHT]
+            with torch.cuda.stream(sl["stream"]):
+                sl["d_in"].copy_(host, non_blocking=True)
+                codec.compress_async(sl["d_in"], eb, mode, params=params, out=sl["out"], ws=sl["cws"],
+                                     size=sl["size"], status=sl["st_c"], stream=sl["stream"])
+                sl["size_h"].copy_(sl["size"], non_blocking=True)
+                sl["ev"].record(sl["stream"])
+
+        def phase_b(i):
+            sl = slots[i % E2E_IN_FLIGHT]
+            sl["ev"].synchronize()
+            cs = int(sl["size_h"][0])
+            with torch.cuda.stream(sl["stream"]):
+                sl["hout"][:cs].copy_(sl["out"][:cs], non_blocking=True)
+                sl["back"][:cs].copy_(sl["hout"][:cs], non_blocking=True)
+                codec.decompress_async(sl["back"][:cs], shape, out=sl["rec"], ws=sl["dws"], status=sl["st_d"],
+                                       stream=sl["stream"])
+                sl["hrec"].copy_(sl["rec"], non_blocking=True)
+
+        def run(steps):
+            for i in range(min(E2E_IN_FLIGHT, steps)):
+                phase_a(i)
+            for i in range(steps):
+                phase_b(i)
+                if i + E2E_IN_FLIGHT < steps:
+                    phase_a(i + E2E_IN_FLIGHT)
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            d_in = host.to(dev, non_blocking=True)
-            buf = codec.compress(d_in, eb, mode, no_topo=args.no_topo)
-            hout[:buf.numel()].copy_(buf, non_blocking=True)
-            d_buf = hout[:buf.numel()].to(dev, non_blocking=True)
-            r = codec.decompress(d_buf, tuple(field.shape))
-            hrec.copy_(r, non_blocking=True)
-            torch.cuda.synchronize()
-            if i:
-                times.append(time.perf_counter() - t0)
-        e2e_s = statistics.mean(times)
+
+        run(E2E_IN_FLIGHT)   # warm-up
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(args.e2e_steps)
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        for sl in slots:
+            if int(sl["st_c"].item()) or int(sl["st_d"].item()):
+                raise RuntimeError("device status set during the end-to-end steps")
+        if not torch.equal(slots[0]["hrec"], rec.cpu()):
+            raise RuntimeError("end-to-end round trip differs from the device-timed one")
         if pg:
             t = torch.tensor([e2e_s], device=dev)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             e2e_s = float(t.item())
         result["e2e"] = {"value": round(4 * n * ws_n / e2e_s / 1e9, 3), "unit": "GB/s",
-                         "h2d_bytes_per_step": int(4 * n + csize), "d2h_bytes_per_step": int(csize + 4 * n)}
+                         "h2d_bytes_per_step": int(4 * n + csize), "d2h_bytes_per_step": int(csize + 4 * n),
+                         "in_flight": E2E_IN_FLIGHT}
     if rank == 0 and not args.no_cpu_baseline:
         gbs, desc, _ = cpu_sample(spec, field.cpu(), eb, args.cpu_seconds)
         result["cpu_baseline"] = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
