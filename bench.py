@@ -41,7 +41,7 @@ NOMINAL_HBM_GBS = 8000.0
 # kernel, per field point, from one ncu capture of the 512^3 workload at relative
 # eb 1e-3 (profiles/launches_turb512_rel1e-3.md); reported only for that workload
 # and only while the kernel is unchanged since the capture.
-TRAFFIC_PER_POINT = {"k_decode_fused": 812.1e6 / 512 ** 3}
+TRAFFIC_PER_POINT = {"k_decode_fused": 811.6e6 / 512 ** 3}
 E2E_IN_FLIGHT = int(os.environ.get("TOPOSZP_E2E_IN_FLIGHT", "4"))   # round trips in flight at once
 
 
