@@ -795,24 +795,42 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
     const uint32_t* pay = reinterpret_cast<const uint32_t*>(A.in + lo.s5);
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
     const float w_f = A.c->w_f;
+    // this thread's block: width, first code, labels (issued before the payload
+    // loads, so that both are in flight together)
+    const uint32_t b = t * DT_BLOCKS + threadIdx.x;
+    uint32_t w = 0, l0 = 0, l1 = 0;
+    int32_t first = 0;
+    if (b < g.nb) {
+        w = __ldg(widths + b);
+        first = __ldg(firsts + b);
+        if (TOPO) {
+            l0 = label_word(labels, 2 * b, g.n);
+            l1 = label_word(labels, 2 * b + 1, g.n);
+        }
+    }
     // the tile's payload is one contiguous word range: stage it with coalesced loads
     const unsigned long long P0 = A.pay_pre[t], P1 = A.pay_pre[t + 1];
     uint32_t len = 0;
     if (P1 >= P0 && P1 - P0 <= (unsigned long long)DT_BLOCKS * 33 && P1 <= A.c->pay_words) len = (uint32_t)(P1 - P0);
     else corrupt = true;
-    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_pay[i] = __ldg(pay + P0 + i);
-    const uint32_t b = t * DT_BLOCKS + threadIdx.x;   // this thread's block
-    uint32_t w = 0, xm = 0, xM = 0;
-    int32_t first = 0;
-    if (b < g.nb) {
-        w = __ldg(widths + b);
-        first = __ldg(firsts + b);
-        if (w > 32) w = 0;   // a damaged stream (the offset pre-pass flags it)
-        if (TOPO) {   // m = 01, M = 11: the low bit marks an extremum
-            const uint32_t l0 = label_word(labels, 2 * b, g.n), l1 = label_word(labels, 2 * b + 1, g.n);
-            xm = compact16(l0) | compact16(l1) << 16;
-            xM = compact16(l0 & (l0 >> 1)) | compact16(l1 & (l1 >> 1)) << 16;   // M = 11
+    for (uint32_t i0 = 0; i0 < len; i0 += 4 * DT_BLOCKS) {   // four loads in flight per thread
+        uint32_t v4[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t i = i0 + j * DT_BLOCKS + threadIdx.x;
+            v4[j] = i < len ? __ldg(pay + P0 + i) : 0u;
         }
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t i = i0 + j * DT_BLOCKS + threadIdx.x;
+            if (i < len) s_pay[i] = v4[j];
+        }
+    }
+    if (w > 32) w = 0;   // a damaged stream (the offset pre-pass flags it)
+    uint32_t xm = 0, xM = 0;
+    if (TOPO) {   // m = 01, M = 11: the low bit marks an extremum
+        xm = compact16(l0) | compact16(l1) << 16;
+        xM = compact16(l0 & (l0 >> 1)) | compact16(l1 & (l1 >> 1)) << 16;
     }
     const uint32_t words = w ? 1u + w : 0u, ncp = __popc(xm);
     uint32_t iw = words, ic = ncp;
