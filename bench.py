@@ -305,7 +305,7 @@ def run_ours(args):
     # library stages between its stage events (tsz_api.cu): the dominant one
     # with algorithmic bytes gives the roofline line
     kernels = {
-        "k_range_cd_vec": (stage_ms(0, 1), 4 * n + lab_bytes),
+        "k_range_cd": (stage_ms(0, 1), 4 * n + lab_bytes),   # k_range_cd_col / _vec / generic
         "k_encode_field": (stage_ms(1, 2), 4 * n + lab_bytes + field_sections + 8 * k),
         "rank_stages": (stage_ms(2, 3), None),
         "finalize": (stage_ms(3, 4), None),

@@ -183,7 +183,10 @@ uint64_t toposzp_noalloc_max_points(void);
  *                        1: its four stages run as separate launches
  *   rank_bitmap          0: dense ranks from bitmaps over the key span when
  *                        they fit the workspace, else a radix sort (default);
- *                        -1: always the radix sort */
+ *                        -1: always the radix sort
+ *   cd_columns           0: the range + CD pass of 3D fields walks z-columns
+ *                        when each plane is a whole number of 128-point
+ *                        chunks (default); -1: never */
 typedef struct {
     int32_t cd_threads;
     int32_t cd_blocks_per_sm;
@@ -192,6 +195,7 @@ typedef struct {
     int32_t saddle_records;
     int32_t dec_split;
     int32_t rank_bitmap;
+    int32_t cd_columns;
 } toposzp_tuning;
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
 

@@ -36,7 +36,7 @@ class Tuning(ctypes.Structure):
     _fields_ = [("cd_threads", ctypes.c_int32), ("cd_blocks_per_sm", ctypes.c_int32),
                 ("rounds_blocks_per_sm", ctypes.c_int32), ("dec_slack_tiles", ctypes.c_int32),
                 ("saddle_records", ctypes.c_int32), ("dec_split", ctypes.c_int32),
-                ("rank_bitmap", ctypes.c_int32)]
+                ("rank_bitmap", ctypes.c_int32), ("cd_columns", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):

@@ -27,7 +27,7 @@ def apply(cfg: dict) -> None:
     t = _lib.Tuning(int(cfg.get("cd_threads", 0)), int(cfg.get("cd_blocks_per_sm", 0)),
                     int(cfg.get("rounds_blocks_per_sm", 0)), int(cfg.get("dec_slack_tiles", 0)),
                     int(cfg.get("saddle_records", 0)), int(cfg.get("dec_split", 0)),
-                    int(cfg.get("rank_bitmap", 0)))
+                    int(cfg.get("rank_bitmap", 0)), int(cfg.get("cd_columns", 0)))
     st = _lib.load().toposzp_set_tuning(t)
     if st:
         raise _lib.TopoSZpError(st, "toposzp_set_tuning")

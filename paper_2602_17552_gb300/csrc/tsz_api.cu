@@ -366,6 +366,7 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     if (t->saddle_records < -1 || t->saddle_records > 1) return TOPOSZP_ERR_INVALID_ARG;
     if (t->dec_split < 0 || t->dec_split > 1) return TOPOSZP_ERR_INVALID_ARG;
     if (t->rank_bitmap < -1 || t->rank_bitmap > 0) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->cd_columns < -1 || t->cd_columns > 0) return TOPOSZP_ERR_INVALID_ARG;
     Tuning u;
     if (t->cd_threads) u.cd_threads = t->cd_threads;
     if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
@@ -374,6 +375,7 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     u.saddle_records = t->saddle_records;
     u.dec_split = t->dec_split;
     u.rank_bitmap = t->rank_bitmap;
+    u.cd_columns = t->cd_columns;
     g_tuning = u;
     return TOPOSZP_OK;
 }

@@ -296,6 +296,90 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
     }
 }
 
+// The compression pass for 3D fields whose planes hold a whole number of
+// 128-point chunks: a warp walks one chunk position down z (a segment of
+// CD_ZSEG planes) and keeps the rows z-1, z, z+1 in registers, so each value
+// comes from DRAM about once (the y-neighbour rows are the neighbouring
+// warps' rows, read from L2).  Same results as k_range_cd_vec.
+constexpr uint32_t CD_ZSEG = 32;
+
+__global__ void __launch_bounds__(256) k_range_cd_col(const float* __restrict__ a, const Geo g, Ctrl* c,
+                                                      uint32_t* __restrict__ labels) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t ncols = g.nxy / 128, nsegs = (g.nz + CD_ZSEG - 1) / CD_ZSEG;
+    float vmin = __int_as_float(0x7F800000), vmax = __int_as_float(0xFF800000);
+    float fin = 0.0f;   // sum of (v - v): +0 while every value is finite, NaN after an inf or NaN
+    uint32_t cs = 0;
+    GlobalVal val{a};
+    for (uint32_t wi = gw; wi < ncols * nsegs; wi += nw) {
+        const uint32_t col = wi % ncols, seg = wi / ncols;
+        const uint32_t p0 = col * 128u + 4u * lane;   // this lane's quad within a plane
+        const uint32_t t = fdiv(p0, g.fx);
+        const uint32_t x = p0 - t * g.nx, y = t;       // one plane: t < ny
+        const bool xl = x > 0, xr = x + 4 < g.nx, yin = y > 0 && y + 1 < g.ny;
+        const uint32_t z0 = seg * CD_ZSEG, z1 = min(g.nz, z0 + CD_ZSEG);
+        const float4* a4 = reinterpret_cast<const float4*>(a);
+        float4 prev = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (z0 > 0) prev = __ldg(a4 + ((size_t)(z0 - 1) * g.nxy + p0) / 4);
+        float4 cur = __ldg(a4 + ((size_t)z0 * g.nxy + p0) / 4);
+        for (uint32_t z = z0; z < z1; z++) {
+            const uint32_t i0 = z * g.nxy + p0;
+            float4 next = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (z + 1 < g.nz) next = __ldg(a4 + (i0 + g.nxy) / 4);
+            const float4 v = cur;
+            vmin = fminf(fminf(vmin, v.x), fminf(v.y, fminf(v.z, v.w)));
+            vmax = fmaxf(fmaxf(vmax, v.x), fmaxf(v.y, fmaxf(v.z, v.w)));
+            fin = __fadd_rn(fin, __fadd_rn(__fadd_rn(__fsub_rn(v.x, v.x), __fsub_rn(v.y, v.y)),
+                                           __fadd_rn(__fsub_rn(v.z, v.z), __fsub_rn(v.w, v.w))));
+            float left = __shfl_up_sync(FULL, v.w, 1);
+            float right = __shfl_down_sync(FULL, v.x, 1);
+            if (lane == 0 && xl) left = __ldg(a + i0 - 1);
+            if (lane == 31 && xr) right = __ldg(a + i0 + 4);
+            uint32_t bits = 0;
+            if (yin && z > 0 && z + 1 < g.nz) {
+                const float4 ym = __ldg(a4 + (i0 - g.nx) / 4);
+                const float4 yp = __ldg(a4 + (i0 + g.nx) / 4);
+                // -0 - (+0) = -0 would read as "less": fold every -0 to +0 first
+                const float4 cv = cz4(v), cym = cz4(ym), cyp = cz4(yp), czm = cz4(prev), czp = cz4(next);
+                const float cl = __fadd_rn(left, 0.0f), cr = __fadd_rn(right, 0.0f);
+                bits = cd_sign<true>(cv.x, cl, cv.y, xl, true, cym.x, cyp.x, czm.x, czp.x) |
+                       cd_sign<true>(cv.y, cv.x, cv.z, true, true, cym.y, cyp.y, czm.y, czp.y) << 2 |
+                       cd_sign<true>(cv.z, cv.y, cv.w, true, true, cym.z, cyp.z, czm.z, czp.z) << 4 |
+                       cd_sign<true>(cv.w, cv.z, cr, true, xr, cym.w, cyp.w, czm.w, czp.w) << 6;
+            } else {
+                const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int j = 0; j < 4; j++) bits |= (uint32_t)classify(val, g, i0 + j, x + j, y, z, vv[j]) << (2 * j);
+            }
+            // four lanes make one 16-point label word
+            const uint32_t b1 = __shfl_down_sync(FULL, bits, 1);
+            const uint32_t b2 = __shfl_down_sync(FULL, bits, 2);
+            const uint32_t b3 = __shfl_down_sync(FULL, bits, 3);
+            if ((lane & 3) == 0) {
+                const uint32_t word = bits | (b1 << 8) | (b2 << 16) | (b3 << 24);
+                labels[i0 >> 4] = word;
+                cs += __popc((word >> 1) & ~word & 0x55555555u);
+            }
+            prev = cur;
+            cur = next;
+        }
+    }
+    uint32_t kmax = vmax >= vmin ? ord_key(vmax) : 0u;
+    uint32_t kmin = vmax >= vmin ? ~ord_key(vmin) : 0u;
+    kmax = __reduce_max_sync(FULL, kmax);
+    kmin = __reduce_max_sync(FULL, kmin);
+    const bool anybad = __any_sync(FULL, isnan(fin));
+    const uint32_t sad = __reduce_add_sync(FULL, cs);
+    if (lane == 0) {
+        if (kmax) atomicMax(&c->max_key, kmax);
+        if (kmin) atomicMax(&c->min_inv, kmin);
+        if (anybad) atomicExch(&c->nonfinite, 1u);
+        if (sad) atomicAdd(&c->k_sad, (unsigned long long)sad);
+    }
+}
+
 // counts[0] = n - (m + s + M)
 __global__ void k_count_regular(uint32_t n, unsigned long long* counts) {
     counts[0] = (unsigned long long)n - counts[1] - counts[2] - counts[3];
@@ -1240,6 +1324,12 @@ void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bo
         uint32_t blocks = hmin<uint32_t>((g.n / 128 + per_cta_chunks - 1) / per_cta_chunks + 1,
                                          (uint32_t)sms * (uint32_t)g_tuning.cd_blocks_per_sm);
         const bool three = g.ndim == 3;
+        if (topo && three && g.nxy % 128 == 0 && g_tuning.cd_columns >= 0) {
+            const uint32_t work = (g.nxy / 128) * ((g.nz + CD_ZSEG - 1) / CD_ZSEG);   // warps
+            const uint32_t cb = hmin<uint32_t>((work + 7) / 8, (uint32_t)sms * 8);
+            k_range_cd_col<<<cb ? cb : 1, 256, 0, st>>>(a, g, c, labels);
+            return;
+        }
         if (topo && three) k_range_cd_vec<true, false, true, true><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
         else if (topo) k_range_cd_vec<true, false, true, false><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
         else k_range_cd_vec<false, false, true, false><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);

@@ -54,6 +54,7 @@ SMALL = [
     ("mixed3d_45x37x29", lambda: synth.grf((29, 37, 45), -11 / 3, 4).numpy(), None),
     ("adv2d_133x71", lambda: synth.adversarial_small(1, (133, 71)).numpy(), None),
     ("adv3d_17x9x13", lambda: synth.adversarial_small(2, (17, 9, 13)).numpy(), None),
+    ("turb_cols_45x32x64", lambda: np.exp(synth.grf((45, 32, 64), -11 / 3, 6).numpy()), None),
 ]
 
 
@@ -78,7 +79,9 @@ def test_parity_config1_abs_bound():
                                    (3, 3, 3), (1, 33), (4, 8, 1), (2, 1025),
                                    # nx % 4 == 0: the vectorised CD path and its boundary rows
                                    (1, 4), (2, 8), (3, 4, 4), (5, 3, 12), (9, 16), (4, 1, 8), (2, 2, 4),
-                                   (1, 1, 128), (3, 260)])
+                                   (1, 1, 128), (3, 260),
+                                   # planes of whole 128-point chunks: the z-column pass, one and two segments
+                                   (5, 8, 16), (40, 16, 32), (70, 4, 64)])
 def test_parity_degenerate_shapes(shape):
     rng = np.random.default_rng(sum(shape))
     a = rng.integers(-4, 5, size=shape).astype(np.float32) * np.float32(0.25)
