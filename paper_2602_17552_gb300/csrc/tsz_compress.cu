@@ -1528,12 +1528,32 @@ __global__ void __launch_bounds__(1024) k_bm_prefix(Ctrl* c, uint32_t* region, c
     }
 }
 
-// P(x): distinct keys of the list below relative key x
-__device__ __forceinline__ uint32_t bm_rank(const uint32_t* bm, const uint32_t* pre, uint32_t x) {
-    const uint32_t w = x >> 5, b = x & 31;
-    return pre[w] + __popc(bm[w] & ((1u << b) - 1u));
+// Smallest relative key of the bin of `key` (the bin is a key interval holding
+// rel): start from the bin edge (q -+ 0.5) * w in binary32, a few ulps off at
+// most, and step to the exact edge; a binary search if the steps do not settle.
+__device__ __forceinline__ uint32_t bin_lo(uint32_t key, uint32_t rel, uint32_t base, int list, float r, float w_f) {
+    const int32_t q = key_bin(key, list, r);
+    const float edge = __fmul_rn(list ? (float)q + 0.5f : (float)q - 0.5f, w_f);
+    const uint32_t gk = list ? ~ord_key(edge) : ord_key(edge);
+    const long long gr = (long long)gk - (long long)base;
+    uint32_t lo = gr < 0 ? 0u : (gr > (long long)rel ? rel : (uint32_t)gr);
+    for (int it = 0; it < 16; it++) {
+        if (key_bin(lo + base, list, r) != q) lo++;   // below the bin: its keys are larger
+        else if (lo > 0 && key_bin(lo - 1 + base, list, r) == q) lo--;
+        else return lo;
+    }
+    uint32_t a = 0, hi = rel;
+    while (a < hi) {
+        const uint32_t mid = a + ((hi - a) >> 1);
+        const int32_t qm = key_bin(mid + base, list, r);
+        if (list ? qm > q : qm < q) a = mid + 1;
+        else hi = mid;
+    }
+    return a;
 }
 
+// delta of every list entry; four entries per thread at a time, their table
+// lookups in flight together
 __global__ void __launch_bounds__(256) k_rank_delta(const uint2* s0, const uint2* s1, Ctrl* c,
                                                     const uint32_t* region, const uint2* tpre, int32_t* delta,
                                                     const int* status) {
@@ -1546,41 +1566,34 @@ __global__ void __launch_bounds__(256) k_rank_delta(const uint2* s0, const uint2
     const uint32_t k = list_count(c, list), base = sp.base[list];
     const uint32_t* bm = region + c->bm_off + (size_t)list * 2 * W;
     const uint32_t* pre = bm + W;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < k; i += gridDim.x * blockDim.x) {
-        const uint2 e = s[i];
-        const uint32_t rel = e.x - base;
-        const int32_t q = key_bin(e.x, list, r);
-        // smallest relative key of the bin (the bin is a key interval holding
-        // rel): start from the bin edge (q -+ 0.5) * w in binary32, a few ulps
-        // off at most, and step to the exact edge; a binary search if the
-        // steps do not settle
-        const float edge = __fmul_rn(list ? (float)q + 0.5f : (float)q - 0.5f, w_f);
-        const uint32_t gk = list ? ~ord_key(edge) : ord_key(edge);
-        const long long gr = (long long)gk - (long long)base;
-        uint32_t lo = gr < 0 ? 0u : (gr > (long long)rel ? rel : (uint32_t)gr);
-        bool ok = false;
-        for (int it = 0; it < 16; it++) {
-            if (key_bin(lo + base, list, r) != q) {
-                lo++;   // below the bin: its keys are larger
-            } else if (lo > 0 && key_bin(lo - 1 + base, list, r) == q) {
-                lo--;
-            } else {
-                ok = true;
-                break;
-            }
+    const uint32_t stride = gridDim.x * blockDim.x;
+    constexpr uint32_t TMASK = (1u << TILE_POS_BITS) - 1;
+    for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < k; i0 += 4 * stride) {
+        uint2 e[4];
+        uint32_t rel[4], lo[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) e[j] = i0 + j * stride < k ? s[i0 + j * stride] : make_uint2(base, 0u);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            rel[j] = e[j].x - base;
+            lo[j] = bin_lo(e[j].x, rel[j], base, list, r, w_f);
         }
-        if (!ok) {
-            uint32_t a = 0, hi = rel;
-            while (a < hi) {
-                const uint32_t mid = a + ((hi - a) >> 1);
-                const int32_t qm = key_bin(mid + base, list, r);
-                if (list ? qm > q : qm < q) a = mid + 1;
-                else hi = mid;
-            }
-            lo = a;
+        uint32_t pr[4], br[4], pl[4], bl[4], tp[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            pr[j] = pre[rel[j] >> 5];
+            br[j] = bm[rel[j] >> 5];
+            pl[j] = pre[lo[j] >> 5];
+            bl[j] = bm[lo[j] >> 5];
+            tp[j] = tpre[e[j].y >> TILE_POS_BITS].y;
         }
-        const uint32_t d = 1u + bm_rank(bm, pre, rel) - bm_rank(bm, pre, lo);
-        delta[tpre[e.y >> TILE_POS_BITS].y + (e.y & ((1u << TILE_POS_BITS) - 1))] = (int32_t)d;
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            if (i0 + j * stride >= k) continue;
+            const uint32_t below_rel = pr[j] + __popc(br[j] & ((1u << (rel[j] & 31)) - 1u));
+            const uint32_t below_lo = pl[j] + __popc(bl[j] & ((1u << (lo[j] & 31)) - 1u));
+            delta[tp[j] + (e[j].y & TMASK)] = (int32_t)(1u + below_rel - below_lo);
+        }
     }
 }
 
