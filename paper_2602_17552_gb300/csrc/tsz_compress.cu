@@ -703,7 +703,19 @@ __global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restri
         const uint64_t p0 = (uint64_t)tile * (ENC_TILE_BLOCKS * 32);
         const uint64_t left = k - p0;
         const uint32_t np = left < (uint64_t)(ENC_TILE_BLOCKS * 32) ? (uint32_t)left : (uint32_t)(ENC_TILE_BLOCKS * 32);
-        for (uint32_t i = t; i < np; i += 256) s_buf[(i >> 5) * ENC_ROW + (i & 31)] = (uint32_t)__ldcs(delta + p0 + i);
+        for (uint32_t i0 = 0; i0 < np; i0 += 4 * 256) {   // four loads in flight per thread
+            uint32_t v4[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t i = i0 + j * 256 + t;
+                v4[j] = i < np ? (uint32_t)__ldcs(delta + p0 + i) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t i = i0 + j * 256 + t;
+                if (i < np) s_buf[(i >> 5) * ENC_ROW + (i & 31)] = v4[j];
+            }
+        }
         __syncthreads();
         const uint32_t b = tile * ENC_TILE_BLOCKS + t;
         uint32_t m[32];

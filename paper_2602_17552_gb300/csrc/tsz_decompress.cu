@@ -151,15 +151,27 @@ __global__ void __launch_bounds__(256, 3) k_decode_ranks(const uint8_t* __restri
         uint32_t len = 0;
         if (P1 >= P0 && P1 - P0 <= DT_BLOCKS * 33u && P1 <= rwords) len = P1 - P0;
         else corrupt = true;
-        for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_buf[i] = __ldg(pay + P0 + i);
         const uint32_t b = t * DT_BLOCKS + threadIdx.x;
         uint32_t w = 0;
         int32_t f = 0;
-        if (b < nbd) {
+        if (b < nbd) {   // issued before the payload loads: both in flight together
             w = __ldg(widths + b);
             f = __ldg(firsts + b);
-            if (w > 32) w = 0;
         }
+        for (uint32_t i0 = 0; i0 < len; i0 += 4 * DT_BLOCKS) {   // four loads in flight per thread
+            uint32_t v4[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t i = i0 + j * DT_BLOCKS + threadIdx.x;
+                v4[j] = i < len ? __ldg(pay + P0 + i) : 0u;
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t i = i0 + j * DT_BLOCKS + threadIdx.x;
+                if (i < len) s_buf[i] = v4[j];
+            }
+        }
+        if (w > 32) w = 0;
         const uint32_t words = w ? 1u + w : 0u;
         uint32_t iw = words;
 #pragma unroll
