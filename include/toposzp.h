@@ -199,6 +199,41 @@ typedef struct {
 } toposzp_tuning;
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
 
+/* ---- Batched form (no counterpart in the paper).  Many uneven fields in one
+ * CUDA-graph replay: a plan fixes the fields' shapes, bounds and parameters and
+ * spreads them over parallel branch streams (longest first onto the
+ * least-loaded branch); a call forks the branches from `stream`, runs every
+ * field's ordinary compress / decompress launch sequence on its branch, and
+ * joins them.  The first call with a given set of pointers is captured into a
+ * CUDA graph, later calls with the same pointers replay it; inside a caller's
+ * own stream capture the launches are issued directly.  Outputs are
+ * bit-identical to per-field toposzp_compress / toposzp_decompress.
+ *
+ * toposzp_batch_plan_create (host): nfields >= 1; ndims[i] in {2, 3};
+ *   dims3[3i..3i+2] the field's dims (x fastest); modes / ebs per field;
+ *   params (host, NULL = defaults) shared by all fields; tune_json (host, may
+ *   be NULL) a JSON object whose "branches" member sets the branch count
+ *   (default 8, at most nfields).  *plan receives an opaque handle.
+ * toposzp_batch_workspace_size (host): bytes of workspace a call needs.
+ * toposzp_batch_compress: fields[i] (host array of device pointers) in,
+ *   outs[i] device buffers of at least toposzp_compress_bound bytes,
+ *   out_sizes device uint64[nfields], statuses device int32[nfields].
+ * toposzp_batch_decompress: ins[i] device buffers holding the streams (at least
+ *   toposzp_compress_bound bytes each, e.g. the outs of a batch compress),
+ *   outs[i] device float32[n_i], statuses device int32[nfields].
+ * A plan serialises its own calls (one at a time, any thread); it must not be
+ * destroyed while a call of it may still run on the device. */
+toposzp_status toposzp_batch_plan_create(int nfields, const int* ndims, const uint64_t* dims3,
+                                         const toposzp_eb_mode* modes, const double* ebs,
+                                         const toposzp_params* params, const char* tune_json, void** plan);
+uint64_t toposzp_batch_workspace_size(const void* plan);
+int toposzp_batch_branches(const void* plan);
+toposzp_status toposzp_batch_compress(void* plan, const float* const* fields, void* const* outs, uint64_t* out_sizes,
+                                      void* workspace, uint64_t ws_bytes, int32_t* statuses, toposzp_stream stream);
+toposzp_status toposzp_batch_decompress(void* plan, const void* const* ins, float* const* outs, void* workspace,
+                                        uint64_t ws_bytes, int32_t* statuses, toposzp_stream stream);
+void toposzp_batch_plan_destroy(void* plan);
+
 /* Host.  Profiling hook (no counterpart in the paper).  After a call with
  * count > 0, every toposzp_compress records events[0..4] (cudaEvent_t handles
  * owned by the caller) on its stream: before the range + CD kernel, after it,

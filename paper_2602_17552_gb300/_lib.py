@@ -49,7 +49,9 @@ class Info(ctypes.Structure):
 EXPORTS = ("toposzp_default_params", "toposzp_status_string", "toposzp_compress_bound",
            "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size", "toposzp_compress",
            "toposzp_inspect", "toposzp_decompress", "toposzp_critical_points", "toposzp_topo_errors",
-           "toposzp_set_stage_events", "toposzp_compress_noalloc", "toposzp_noalloc_max_points", "toposzp_set_tuning")
+           "toposzp_set_stage_events", "toposzp_compress_noalloc", "toposzp_noalloc_max_points", "toposzp_set_tuning",
+           "toposzp_batch_plan_create", "toposzp_batch_workspace_size", "toposzp_batch_branches",
+           "toposzp_batch_compress", "toposzp_batch_decompress", "toposzp_batch_plan_destroy")
 
 _lib = None
 
@@ -92,6 +94,20 @@ def load() -> ctypes.CDLL:
     L.toposzp_set_tuning.restype = c_int
     L.toposzp_noalloc_max_points.argtypes = []
     L.toposzp_noalloc_max_points.restype = u64
+    L.toposzp_batch_plan_create.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_uint64),
+                                            ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(Params), ctypes.c_char_p, ctypes.POINTER(vp)]
+    L.toposzp_batch_plan_create.restype = c_int
+    L.toposzp_batch_workspace_size.argtypes = [vp]
+    L.toposzp_batch_workspace_size.restype = u64
+    L.toposzp_batch_branches.argtypes = [vp]
+    L.toposzp_batch_branches.restype = c_int
+    L.toposzp_batch_compress.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, vp, u64, vp, vp]
+    L.toposzp_batch_compress.restype = c_int
+    L.toposzp_batch_decompress.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, u64, vp, vp]
+    L.toposzp_batch_decompress.restype = c_int
+    L.toposzp_batch_plan_destroy.argtypes = [vp]
+    L.toposzp_batch_plan_destroy.restype = None
     _lib = L
     return L
 

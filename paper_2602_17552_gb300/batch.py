@@ -1,21 +1,23 @@
 """Batched compression / decompression of many uneven fields in one launch.
 
-A :class:`BatchPlan` owns device buffers for every field of a batch and
-captures the whole batch -- the library's kernel sequence for each field -- as
-one CUDA graph.  Fields are spread over ``branches`` parallel graph branches
-(longest-first onto the least-loaded branch), so small fields that leave most
-SMs idle overlap on the device; each branch reuses one workspace sized for its
-largest field.  Replaying the batch is a single ``cudaGraphLaunch``.
+A thin binding of the library's native batch plan (``toposzp_batch_*`` in
+``include/toposzp.h``): the plan spreads the fields over parallel branch
+streams (longest first onto the least-loaded branch) and replays the whole
+batch -- every field's ordinary kernel sequence -- as one CUDA graph.  This
+module only allocates the device buffers (torch) and marshals the pointers.
 
 Every field goes through exactly the same kernels as a plain call, so the
 compressed bytes and decoded values are identical to per-field runs (checked in
-the tests).  ``branches`` and the library's launch geometry come from the
-autotuner (:mod:`paper_2602_17552_gb300.autotune`).
+the tests).  ``branches`` comes from the autotuner
+(:mod:`paper_2602_17552_gb300.autotune`).  ``run_eager`` issues the same fields
+as plain per-field calls, one after another on the current stream: the
+baseline the batched form is measured against.
 """
 from __future__ import annotations
 
 import ctypes
-from dataclasses import dataclass, field
+import json
+from dataclasses import dataclass
 
 import torch
 
@@ -28,133 +30,125 @@ class Item:
     shape: tuple
     eb: float
     mode: str
-    src: torch.Tensor                 # input field (compress) / decoded output (decompress)
+    src: torch.Tensor                 # input field
     out: torch.Tensor = None          # compressed stream buffer (capacity = bound)
     size: torch.Tensor = None         # int64 stream length, written on the device
     st_c: torch.Tensor = None
     st_d: torch.Tensor = None
     dec: torch.Tensor = None          # decoded field
-    branch: int = 0
 
 
-@dataclass
 class BatchPlan:
-    items: list
-    branches: int
-    params: object
-    device: torch.device
-    ws_c: list = field(default_factory=list)
-    ws_d: list = field(default_factory=list)
-    streams: list = field(default_factory=list)
-    graph_c: torch.cuda.CUDAGraph = None
-    graph_d: torch.cuda.CUDAGraph = None
+    def __init__(self, items, branches, params, device, handle):
+        self.items = items
+        self.params = params
+        self.device = device
+        self._h = handle
+        self.branches = int(_lib.load().toposzp_batch_branches(handle))
+        n = len(items)
+        self.sizes = torch.zeros(n, dtype=torch.int64, device=device)
+        self.st_c = torch.zeros(n, dtype=torch.int32, device=device)
+        self.st_d = torch.zeros(n, dtype=torch.int32, device=device)
+        for i, it in enumerate(items):
+            it.size, it.st_c, it.st_d = self.sizes[i:i + 1], self.st_c[i:i + 1], self.st_d[i:i + 1]
+        wsb = int(_lib.load().toposzp_batch_workspace_size(handle))
+        self.ws = torch.empty(max(wsb, 256), dtype=torch.uint8, device=device)
+        P = ctypes.c_void_p * n
+        self._src = P(*[it.src.data_ptr() for it in items])
+        self._out = P(*[it.out.data_ptr() for it in items])
+        self._dec = P(*[it.dec.data_ptr() for it in items])
+        self._ws_eager = None
 
     @property
     def nbytes(self) -> int:
         return sum(it.src.numel() * 4 for it in self.items)
 
-    # ------------------------------------------------------------ building
     @staticmethod
-    def create(fields, ebs, modes="rel", branches: int = 4, no_topo=False, device=None) -> "BatchPlan":
+    def create(fields, ebs, modes="rel", branches: int = 8, no_topo=False, device=None) -> "BatchPlan":
         """fields: list of float32 CUDA tensors (2D or 3D); ebs / modes: per field or scalar."""
         dev = torch.device(device) if device is not None else fields[0].device
         n = len(fields)
         ebs = list(ebs) if isinstance(ebs, (list, tuple)) else [ebs] * n
         modes = list(modes) if isinstance(modes, (list, tuple)) else [modes] * n
         params = codec.make_params(no_topo=no_topo)
-        items = []
+        items, ndims, dims, mcodes = [], [], [], []
         for f, eb, md in zip(fields, ebs, modes):
             if not (f.is_cuda and f.dtype == torch.float32 and f.is_contiguous()):
                 raise ValueError("batch fields must be contiguous float32 CUDA tensors")
-            items.append(Item(tuple(f.shape), float(eb), md, f))
-        branches = max(1, min(int(branches), n))
-        # longest first onto the least-loaded branch
-        load = [0] * branches
-        for it in sorted(items, key=lambda it: -it.src.numel()):
-            b = min(range(branches), key=lambda j: load[j])
-            it.branch = b
-            load[b] += it.src.numel()
-        plan = BatchPlan(items, branches, params, dev)
-        for b in range(branches):
-            mine = [it for it in items if it.branch == b]
-            wc = max((codec.compress_workspace_size(it.shape) for it in mine), default=256)
-            wd = max((codec.decompress_workspace_size(it.shape) for it in mine), default=256)
-            plan.ws_c.append(torch.empty(wc, dtype=torch.uint8, device=dev))
-            plan.ws_d.append(torch.empty(wd, dtype=torch.uint8, device=dev))
-            plan.streams.append(torch.cuda.Stream(device=dev))
-        for it in items:
+            nd, d = codec.field_dims(f.shape)
+            ndims.append(nd)
+            dims.extend(list(_lib.dims3(nd, d)))
+            mcodes.append(_lib.EB_REL if md == "rel" else _lib.EB_ABS)
+            it = Item(tuple(f.shape), float(eb), md, f)
             it.out = torch.empty(codec.compress_bound(it.shape), dtype=torch.uint8, device=dev)
-            it.size = torch.zeros(1, dtype=torch.int64, device=dev)
-            it.st_c = torch.zeros(1, dtype=torch.int32, device=dev)
-            it.st_d = torch.zeros(1, dtype=torch.int32, device=dev)
             it.dec = torch.empty(it.shape, dtype=torch.float32, device=dev)
-        return plan
+            items.append(it)
+        h = ctypes.c_void_p()
+        L = _lib.load()
+        st = L.toposzp_batch_plan_create(n, (ctypes.c_int * n)(*ndims), (ctypes.c_uint64 * (3 * n))(*dims),
+                                         (ctypes.c_int * n)(*mcodes), (ctypes.c_double * n)(*[it.eb for it in items]),
+                                         ctypes.byref(params), json.dumps({"branches": int(branches)}).encode(),
+                                         ctypes.byref(h))
+        if st:
+            raise _lib.TopoSZpError(st, "toposzp_batch_plan_create")
+        return BatchPlan(items, branches, params, dev, h)
 
-    def _enqueue(self, op: str):
-        """Issue the batch on the branch streams, forked from and joined into the
-        current stream (works eagerly and under graph capture)."""
-        main = torch.cuda.current_stream(self.device)
-        fork = torch.cuda.Event()
-        fork.record(main)
-        joins = []
-        for b, s in enumerate(self.streams):
-            s.wait_event(fork)
-            with torch.cuda.stream(s):
-                for it in self.items:
-                    if it.branch != b:
-                        continue
-                    if op == "compress":
-                        codec.compress_async(it.src, it.eb, it.mode, params=self.params, out=it.out,
-                                             ws=self.ws_c[b], size=it.size, status=it.st_c, stream=s)
-                    else:
-                        codec.decompress_async(it.out, it.shape, out=it.dec, ws=self.ws_d[b],
-                                               status=it.st_d, stream=s)
-            ev = torch.cuda.Event()
-            ev.record(s)
-            joins.append(ev)
-        for ev in joins:
-            main.wait_event(ev)
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h:
+            torch.cuda.synchronize(self.device)
+            _lib.load().toposzp_batch_plan_destroy(h)
+            self._h = None
 
-    def capture(self):
-        """Capture compress and decompress of the whole batch as two CUDA graphs."""
-        self.run_eager("compress")       # warm-up outside capture (lazy init, occupancy queries)
-        self.run_eager("decompress")
-        torch.cuda.synchronize(self.device)
-        self.graph_c = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph_c):
-            self._enqueue("compress")
-        self.graph_d = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(self.graph_d):
-            self._enqueue("decompress")
-        return self
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
 
     # ------------------------------------------------------------- running
-    def run_eager(self, op: str):
-        self._enqueue(op)
+    def capture(self):
+        """Run both directions once: the library captures each direction's CUDA
+        graph on its first call with these buffers (later calls replay it)."""
+        self.compress()
+        self.decompress()
+        torch.cuda.synchronize(self.device)
+        return self
 
     def compress(self):
-        """Replay the compress graph (one launch) on the current stream."""
-        if self.graph_c is None:
-            self.run_eager("compress")
-        else:
-            self.graph_c.replay()
+        st = _lib.load().toposzp_batch_compress(self._h, self._src, self._out, self.sizes.data_ptr(),
+                                                self.ws.data_ptr(), self.ws.numel(), self.st_c.data_ptr(),
+                                                self._stream())
+        if st:
+            raise _lib.TopoSZpError(st, "toposzp_batch_compress")
 
     def decompress(self):
-        if self.graph_d is None:
-            self.run_eager("decompress")
-        else:
-            self.graph_d.replay()
+        st = _lib.load().toposzp_batch_decompress(self._h, self._out, self._dec, self.ws.data_ptr(),
+                                                  self.ws.numel(), self.st_d.data_ptr(), self._stream())
+        if st:
+            raise _lib.TopoSZpError(st, "toposzp_batch_decompress")
+
+    def run_eager(self, op: str):
+        """The same fields as plain per-field calls on the current stream, one
+        after another (one workspace shared by all)."""
+        if self._ws_eager is None:
+            wmax = max(max(codec.compress_workspace_size(it.shape), codec.decompress_workspace_size(it.shape))
+                       for it in self.items)
+            self._ws_eager = torch.empty(wmax, dtype=torch.uint8, device=self.device)
+        for it in self.items:
+            if op == "compress":
+                codec.compress_async(it.src, it.eb, it.mode, params=self.params, out=it.out, ws=self._ws_eager,
+                                     size=it.size, status=it.st_c)
+            else:
+                codec.decompress_async(it.out, it.shape, out=it.dec, ws=self._ws_eager, status=it.st_d)
 
     def check(self):
         """Raise if any field's device status is set (synchronises)."""
         torch.cuda.synchronize(self.device)
-        for i, it in enumerate(self.items):
-            for st, what in ((it.st_c, "compress"), (it.st_d, "decompress")):
-                v = int(st.item())
-                if v:
-                    raise _lib.TopoSZpError(v, f"batch item {i} {what}")
+        for i, (c, d) in enumerate(zip(self.st_c.tolist(), self.st_d.tolist())):
+            if c:
+                raise _lib.TopoSZpError(c, f"batch item {i} compress")
+            if d:
+                raise _lib.TopoSZpError(d, f"batch item {i} decompress")
 
     def streams_bytes(self):
         """Per field: the compressed stream (uint8 CUDA tensor views, exact length)."""
         torch.cuda.synchronize(self.device)
-        return [it.out[:int(it.size.item())] for it in self.items]
+        return [it.out[:int(s)] for it, s in zip(self.items, self.sizes.tolist())]

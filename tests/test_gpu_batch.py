@@ -1,5 +1,6 @@
-"""Batched form: many uneven fields through one CUDA-graph launch give exactly
-the bytes and values of per-field plain calls."""
+"""Batched form (the native batch plan of the C ABI): many uneven fields
+through one CUDA-graph replay give exactly the bytes and values of per-field
+plain calls."""
 import numpy as np
 import pytest
 import torch
@@ -27,8 +28,8 @@ def test_batch_equals_plain(branches, graph):
             plan.compress()
             plan.decompress()
     else:
-        plan.compress()
-        plan.decompress()
+        plan.run_eager("compress")
+        plan.run_eager("decompress")
     plan.check()
     streams = plan.streams_bytes()
     for f, eb, s, it in zip(fs, ebs, streams, plan.items):
@@ -67,3 +68,24 @@ def test_launch_tuning_never_changes_bits():
                 assert torch.equal(codec.decompress(got, tuple(f.shape)), codec.decompress(w, tuple(f.shape)))
     finally:
         autotune.apply(autotune.DEFAULT)
+
+
+def test_batch_inside_a_callers_capture():
+    """Under the caller's own stream capture the plan issues its launches
+    directly into the caller's graph; replaying that graph gives the same
+    streams as plain calls."""
+    fs, ebs = _fields()
+    plan = batch.BatchPlan.create(fs, ebs, "rel", branches=3).capture()   # warm-up outside capture
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.compress()
+            plan.decompress()
+    plan.sizes.zero_()
+    g.replay()
+    plan.check()
+    for f, eb, st, it in zip(fs, ebs, plan.streams_bytes(), plan.items):
+        want = codec.compress(f, eb, "rel")
+        assert torch.equal(st, want)
+        assert torch.equal(it.dec, codec.decompress(want, tuple(f.shape)))
