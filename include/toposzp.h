@@ -79,6 +79,8 @@ uint64_t toposzp_compress_bound(int ndim, const uint64_t dims[3]);
  * it covers fields where every other point is an extremum. */
 uint64_t toposzp_compress_workspace_size(int ndim, const uint64_t dims[3]);
 uint64_t toposzp_decompress_workspace_size(int ndim, const uint64_t dims[3]);
+/* Host.  The larger of the two: one workspace that serves both calls. */
+uint64_t toposzp_workspace_size(int ndim, const uint64_t dims[3]);
 
 /* Compress one field (Section IV-A: CD + RP, QZ, B + LZ, BE).
  *   field        device float32[n], read only

@@ -47,7 +47,8 @@ class Info(ctypes.Structure):
 
 
 EXPORTS = ("toposzp_default_params", "toposzp_status_string", "toposzp_compress_bound",
-           "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size", "toposzp_compress",
+           "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size", "toposzp_workspace_size",
+           "toposzp_compress",
            "toposzp_inspect", "toposzp_decompress", "toposzp_critical_points", "toposzp_topo_errors",
            "toposzp_set_stage_events", "toposzp_compress_noalloc", "toposzp_noalloc_max_points", "toposzp_set_tuning",
            "toposzp_batch_plan_create", "toposzp_batch_workspace_size", "toposzp_batch_branches",
@@ -71,7 +72,8 @@ def load() -> ctypes.CDLL:
     L.toposzp_default_params.restype = None
     L.toposzp_status_string.argtypes = [c_int]
     L.toposzp_status_string.restype = ctypes.c_char_p
-    for f in ("toposzp_compress_bound", "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size"):
+    for f in ("toposzp_compress_bound", "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size",
+              "toposzp_workspace_size"):
         getattr(L, f).argtypes = [c_int, dims_t]
         getattr(L, f).restype = u64
     L.toposzp_compress.argtypes = [vp, c_int, dims_t, c_int, ctypes.c_double, ctypes.POINTER(Params),

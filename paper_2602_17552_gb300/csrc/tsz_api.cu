@@ -198,6 +198,11 @@ uint64_t toposzp_decompress_workspace_size(int ndim, const uint64_t dims[3]) {
     return decompress_ws(g.n).end;
 }
 
+uint64_t toposzp_workspace_size(int ndim, const uint64_t dims[3]) {
+    const uint64_t a = toposzp_compress_workspace_size(ndim, dims), b = toposzp_decompress_workspace_size(ndim, dims);
+    return a > b ? a : b;
+}
+
 toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dims[3],
                                 toposzp_eb_mode mode, double eb, const toposzp_params* params,
                                 void* out, uint64_t out_capacity, uint64_t* out_size, void* workspace,
