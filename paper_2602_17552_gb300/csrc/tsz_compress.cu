@@ -466,7 +466,7 @@ static_assert(ENC_TILE_BLOCKS * 32 == (1 << TILE_POS_BITS), "tile size");
 static_assert(ENC_TILE_BLOCKS * ENC_ROW >= TILE_PAY, "payload staging");
 
 template <bool TOPO>
-__global__ void __launch_bounds__(256, 3) k_encode_field(const float* __restrict__ a,
+__global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict__ a,
                                                          const uint32_t* __restrict__ labels, Ctrl* c,
                                                          uint2* tcnt, EncOut o, uint2* listM, uint2* listm,
                                                          uint32_t* region, int* status) {
