@@ -183,20 +183,27 @@ __device__ __forceinline__ uint32_t compact16(uint32_t x) {
 }
 
 // Exclusive scan of pairs (a_i, b_i), i < cnt, by one CTA of 1024 threads:
-// coalesced chunks of 1024 entries, a shuffle scan per warp, one shared step
-// per chunk, running 64-bit carries.  load(i) -> uint2; store(i, pa, pb).
-// Returns the totals.  Shared scratch: s_w[33] pairs.
+// chunks of 4096 entries, four consecutive entries per thread, a shuffle scan
+// of the threads' sums per warp, one shared step per chunk, running 64-bit
+// carries.  load(i) -> uint2; store(i, pa, pb).  Returns the totals.  Shared
+// scratch: s_w[33] pairs.
 template <class Load, class Store>
 __device__ void cta_scan_pairs(uint32_t cnt, Load load, Store store, unsigned long long (*s_w)[2],
                                unsigned long long& tot_a, unsigned long long& tot_b) {
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr uint32_t PER = 4, CHUNK = 1024 * PER;
     unsigned long long ca = 0, cb = 0;
-    uint2 nxt = threadIdx.x < cnt ? load(threadIdx.x) : make_uint2(0u, 0u);
-    for (uint32_t base = 0; base < cnt; base += 1024) {
-        const uint32_t i = base + threadIdx.x;
-        const uint2 v = nxt;
-        nxt = i + 1024 < cnt ? load(i + 1024) : make_uint2(0u, 0u);   // next chunk in flight
-        unsigned long long ia = v.x, ib = v.y;
+    for (uint32_t base = 0; base < cnt; base += CHUNK) {
+        const uint32_t i0 = base + threadIdx.x * PER;
+        uint2 v[PER];
+        unsigned long long sa = 0, sb = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < PER; j++) {
+            v[j] = i0 + j < cnt ? load(i0 + j) : make_uint2(0u, 0u);
+            sa += v[j].x;
+            sb += v[j].y;
+        }
+        unsigned long long ia = sa, ib = sb;
 #pragma unroll
         for (int of = 1; of < 32; of <<= 1) {
             const unsigned long long ta = __shfl_up_sync(0xFFFFFFFFu, ia, of), tb = __shfl_up_sync(0xFFFFFFFFu, ib, of);
@@ -206,18 +213,24 @@ __device__ void cta_scan_pairs(uint32_t cnt, Load load, Store store, unsigned lo
         __syncthreads();
         if (warp == 0) {   // exclusive prefixes of the 32 warp totals, and the chunk total
             const unsigned long long xa = s_w[lane][0], xb = s_w[lane][1];
-            unsigned long long sa = xa, sb = xb;
+            unsigned long long ra = xa, rb = xb;
 #pragma unroll
             for (int of = 1; of < 32; of <<= 1) {
-                const unsigned long long ta = __shfl_up_sync(0xFFFFFFFFu, sa, of), tb = __shfl_up_sync(0xFFFFFFFFu, sb, of);
-                if (lane >= (uint32_t)of) { sa += ta; sb += tb; }
+                const unsigned long long ta = __shfl_up_sync(0xFFFFFFFFu, ra, of), tb = __shfl_up_sync(0xFFFFFFFFu, rb, of);
+                if (lane >= (uint32_t)of) { ra += ta; rb += tb; }
             }
-            s_w[lane][0] = sa - xa;
-            s_w[lane][1] = sb - xb;
-            if (lane == 31) { s_w[32][0] = sa; s_w[32][1] = sb; }
+            s_w[lane][0] = ra - xa;
+            s_w[lane][1] = rb - xb;
+            if (lane == 31) { s_w[32][0] = ra; s_w[32][1] = rb; }
         }
         __syncthreads();
-        if (i < cnt) store(i, ca + s_w[warp][0] + ia - v.x, cb + s_w[warp][1] + ib - v.y);
+        unsigned long long pa = ca + s_w[warp][0] + ia - sa, pb = cb + s_w[warp][1] + ib - sb;
+#pragma unroll
+        for (uint32_t j = 0; j < PER; j++) {
+            if (i0 + j < cnt) store(i0 + j, pa, pb);
+            pa += v[j].x;
+            pb += v[j].y;
+        }
         ca += s_w[32][0];
         cb += s_w[32][1];
         __syncthreads();
