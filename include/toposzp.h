@@ -184,8 +184,10 @@ uint64_t toposzp_noalloc_max_points(void);
  *   dec_split            0: one fused wavefront kernel decodes (default);
  *                        1: its four stages run as separate launches
  *   rank_bitmap          0: dense ranks from bitmaps over the key span when
- *                        they fit the workspace, else a radix sort (default);
- *                        -1: always the radix sort
+ *                        they fit the workspace, else a radix sort, with a
+ *                        table of each QZ bin's first rank when the bins of
+ *                        the field's range fit (default); 1: the bitmaps
+ *                        without that table; -1: always the radix sort
  *   cd_columns           0: the range + CD pass of 3D fields walks z-columns
  *                        when each plane is a whole number of 128-point
  *                        chunks (default); -1: never */

@@ -370,7 +370,7 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     if (t->dec_slack_tiles < 0 || t->dec_slack_tiles > 65536) return TOPOSZP_ERR_INVALID_ARG;
     if (t->saddle_records < -1 || t->saddle_records > 1) return TOPOSZP_ERR_INVALID_ARG;
     if (t->dec_split < 0 || t->dec_split > 1) return TOPOSZP_ERR_INVALID_ARG;
-    if (t->rank_bitmap < -1 || t->rank_bitmap > 0) return TOPOSZP_ERR_INVALID_ARG;
+    if (t->rank_bitmap < -1 || t->rank_bitmap > 1) return TOPOSZP_ERR_INVALID_ARG;
     if (t->cd_columns < -1 || t->cd_columns > 0) return TOPOSZP_ERR_INVALID_ARG;
     Tuning u;
     if (t->cd_threads) u.cd_threads = t->cd_threads;

@@ -112,7 +112,7 @@ __host__ __device__ inline void make_layout(uint64_t n, uint64_t nb, bool topo, 
 struct Ctrl {
     // range pass
     unsigned int min_inv, max_key, nonfinite, sort_passes;
-    unsigned int rank_bitmap, bm_words, bm_off, pad_b1;   // dense ranks from key bitmaps (1) or the sort (0)
+    unsigned int rank_bitmap, bm_words, bm_off, bin_n;   // dense ranks from key bitmaps (1) or the sort (0)
     // quantiser (Section II-C) and geometry, filled by the parameter kernel or
     // by the header parser
     int const_field, rel, rbf_k, rs_sweeps;
@@ -123,7 +123,9 @@ struct Ctrl {
     Geo g;
     // tile allocators of the persistent codec kernels
     // extrema lists (compress) and counts
-    unsigned int cnt_max, cnt_min, pad2, pad3;
+    unsigned int cnt_max, cnt_min;
+    int bin_q0;   // first QZ bin of the per-bin rank table (bin_n bins, 0: no table)
+    unsigned int pad3;
     unsigned long long sum_abs;
     unsigned long long pay_words, k_total, rank_words, k_sad;
     unsigned long long counts[4];

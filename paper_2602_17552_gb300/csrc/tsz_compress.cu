@@ -581,7 +581,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
         if (c->rank_bitmap) {
             const uint32_t W = c->bm_words;
             bmM = region + c->bm_off;
-            bmm = bmM + 2 * (size_t)W;
+            bmm = bmM + (size_t)W;
             baseM = ~c->min_inv;   // ord(vmin): the smallest maximum key
             basem = ~c->max_key;   // ~ord(vmax): the smallest minimum key
         }
@@ -1418,7 +1418,7 @@ void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsign
 void launch_qparams(Ctrl* c, int* status, cudaStream_t st) { k_qparams<<<1, 32, 0, st>>>(c, status); }
 
 __global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsigned long long region_bytes,
-                                                 unsigned long long slot_bytes, int force_sort, const int* status);
+                                                 unsigned long long slot_bytes, int mode, const int* status);
 
 void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2* tcnt, uint32_t* scratch,
                          uint64_t region_bytes, uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo,
@@ -1429,8 +1429,8 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2*
     if (topo) {
         // the rank mode (key bitmaps or sort) is decided here, so the encoder can set the bits
         const unsigned long long slot_bytes = 4ull * TILE_PAY * ntiles;
-        k_bm_zero<<<(uint32_t)sms * 8, 256, 0, st>>>(c, scratch, region_bytes, slot_bytes,
-                                                      g_tuning.rank_bitmap < 0 ? 1 : 0, status);
+        k_bm_zero<<<(uint32_t)sms * 8, 256, 0, st>>>(c, scratch, region_bytes, slot_bytes, g_tuning.rank_bitmap,
+                                                      status);
         k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
     } else {
         k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
@@ -1448,9 +1448,12 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2*
 // the span marks the keys present; an exclusive popcount prefix per word gives
 // P(x) = number of distinct keys below x.  Bins (QZ codes) are contiguous key
 // intervals (quantisation is monotone in the value, ord() in the key), so
-// delta = 1 + P(key) - P(lo), lo = the smallest key of the entry's bin, found
-// by a binary search on the quantiser.  Layout in the region: bitmap 0,
-// prefix 0, bitmap 1, prefix 1 (W words each).  Same deltas as the sort path.
+// delta = 1 + P(key) - P(lo), lo = the smallest key of the entry's bin.
+// Layout at the end of the region (W words, a multiple of 4): bitmap 0,
+// bitmap 1, then per list W pairs (prefix, bitmap word), so that P(x) takes one
+// 8-byte load.  P(lo) comes from a table over the bins of the field's range
+// (the region's start, free once the field payload is copied out) when it
+// fits; otherwise each entry finds lo itself.  Same deltas as the sort path.
 
 constexpr uint32_t BM_CHUNK = 8192;   // words per prefix chunk (one CTA)
 
@@ -1458,31 +1461,37 @@ __device__ __forceinline__ int32_t key_bin(uint32_t key, int list, float r) {
     return quantize(key_float(list ? ~key : key), r);
 }
 
-// Decides the mode and zeroes the two bitmaps.  They take the end of the
-// region (the field encoder's payload slots use its start while it sets the
-// bits); c->bm_off is their word offset.
+// Decides the mode, sizes the bin table and zeroes the two bitmaps.  The
+// bitmaps and pairs take the end of the region (the field encoder's payload
+// slots use its start while it sets the bits); c->bm_off is their word offset.
+// mode: < 0 the sort, 0 bitmaps and bin table when they fit, 1 no bin table.
 __global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsigned long long region_bytes,
-                                                 unsigned long long slot_bytes, int force_sort, const int* status) {
+                                                 unsigned long long slot_bytes, int mode, const int* status) {
     if (*status) return;
     const SortPlan sp = sort_plan(c);
     const uint32_t kmax = c->max_key, kmin = ~c->min_inv;
     const uint32_t span = kmax > kmin ? kmax - kmin : 0u;
     const int B = span ? 32 - __clz(span) : 0;
-    const unsigned long long W = B <= 31 ? ((1ull << B) + 31) / 32 + 1 : 0ull;
-    const bool use = !force_sort && sp.passes > 0 && B <= 31 && slot_bytes + 16ull * W + 16 <= region_bytes;
-    const unsigned long long off = use ? ((region_bytes - 16ull * W) / 4) & ~3ull : 0ull;
+    const unsigned long long W = B <= 31 ? (((1ull << B) + 31) / 32 + 1 + 3) & ~3ull : 0ull;
+    const bool use = mode >= 0 && sp.passes > 0 && B <= 31 && slot_bytes + 24ull * W + 16 <= region_bytes;
+    const unsigned long long off = use ? ((region_bytes - 24ull * W) / 4) & ~3ull : 0ull;
+    // QZ bins of the range [vmin, vmax]: both lists' entries fall inside
+    const float r = c->r_f;
+    const long long q0 = quantize(key_float(kmin), r), q1 = quantize(key_float(kmax), r);
+    const long long nbins = q1 - q0 + 1;
+    const bool tab = use && mode == 0 && nbins > 0 && 8ull * (unsigned long long)nbins <= slot_bytes;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         c->rank_bitmap = use ? 1u : 0u;
         c->bm_words = use ? (uint32_t)W : 0u;
         c->bm_off = (uint32_t)off;
+        c->bin_n = tab ? (uint32_t)nbins : 0u;
+        c->bin_q0 = (int32_t)q0;
     }
     if (!use) return;
     uint32_t* bm = region + off;
-    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < W;
-         i += (unsigned long long)gridDim.x * blockDim.x) {
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < 2 * W;
+         i += (unsigned long long)gridDim.x * blockDim.x)
         bm[i] = 0u;
-        bm[2 * W + i] = 0u;
-    }
 }
 
 // popcount of every BM_CHUNK-word chunk of both bitmaps
@@ -1494,7 +1503,7 @@ __global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region
     region += c->bm_off;
     for (uint32_t q = blockIdx.x; q < 2 * nch; q += gridDim.x) {
         const uint32_t list = q / nch, ch = q % nch;
-        const uint32_t* bm = region + (size_t)list * 2 * W + (size_t)ch * BM_CHUNK;
+        const uint32_t* bm = region + (size_t)list * W + (size_t)ch * BM_CHUNK;
         const uint32_t nw = min(BM_CHUNK, W - ch * BM_CHUNK);
         uint32_t a = 0;
         for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) a += __popc(bm[i]);
@@ -1510,7 +1519,8 @@ __global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region
     }
 }
 
-// exclusive popcount prefix of every word (chunk offsets summed from csum)
+// (exclusive popcount prefix, word) of every bitmap word (chunk offsets summed
+// from csum)
 __global__ void __launch_bounds__(1024) k_bm_prefix(Ctrl* c, uint32_t* region, const uint32_t* csum,
                                                     const int* status) {
     __shared__ unsigned long long s_w[33][2];
@@ -1528,40 +1538,71 @@ __global__ void __launch_bounds__(1024) k_bm_prefix(Ctrl* c, uint32_t* region, c
         __syncthreads();
         uint32_t off = 0;
         for (int w = 0; w < 32; w++) off += s_o[w];
-        const uint32_t* bm = region + (size_t)list * 2 * W + (size_t)ch * BM_CHUNK;
-        uint32_t* pre = region + (size_t)list * 2 * W + W + (size_t)ch * BM_CHUNK;
+        const uint32_t* bm = region + (size_t)list * W + (size_t)ch * BM_CHUNK;
+        uint2* pr = reinterpret_cast<uint2*>(region + 2 * (size_t)W) + (size_t)list * W + (size_t)ch * BM_CHUNK;
         const uint32_t nw = min(BM_CHUNK, W - ch * BM_CHUNK);
         unsigned long long ta, tb;
         cta_scan_pairs(
             nw, [&](uint32_t i) { return make_uint2((uint32_t)__popc(bm[i]), 0u); },
-            [&](uint32_t i, unsigned long long pa, unsigned long long) { pre[i] = off + (uint32_t)pa; }, s_w, ta,
-            tb);
+            [&](uint32_t i, unsigned long long pa, unsigned long long) { pr[i] = make_uint2(off + (uint32_t)pa, bm[i]); },
+            s_w, ta, tb);
         __syncthreads();
     }
 }
 
-// Smallest relative key of the bin of `key` (the bin is a key interval holding
-// rel): start from the bin edge (q -+ 0.5) * w in binary32, a few ulps off at
-// most, and step to the exact edge; a binary search if the steps do not settle.
-__device__ __forceinline__ uint32_t bin_lo(uint32_t key, uint32_t rel, uint32_t base, int list, float r, float w_f) {
-    const int32_t q = key_bin(key, list, r);
+// P(x): distinct keys of the list below relative key x
+__device__ __forceinline__ uint32_t bm_below(const uint2* pr, uint32_t x) {
+    const uint2 p = pr[x >> 5];
+    return p.x + __popc(p.y & ((1u << (x & 31)) - 1u));
+}
+
+// Smallest relative key x in [0, hi] whose bin is not before q in the list's
+// key order (hi + 1 if none): start from the bin edge (q -+ 0.5) * w in
+// binary32, a few ulps off at most, and step to the exact edge; a binary
+// search if the steps do not settle.  For a key of bin q and hi = its relative
+// key this is the smallest relative key of that bin.
+__device__ __forceinline__ uint32_t bin_first(int32_t q, uint32_t hi, uint32_t base, int list, float r, float w_f) {
+    auto before = [&](uint32_t x) {
+        const int32_t qx = key_bin(x + base, list, r);
+        return list ? qx > q : qx < q;
+    };
     const float edge = __fmul_rn(list ? (float)q + 0.5f : (float)q - 0.5f, w_f);
     const uint32_t gk = list ? ~ord_key(edge) : ord_key(edge);
     const long long gr = (long long)gk - (long long)base;
-    uint32_t lo = gr < 0 ? 0u : (gr > (long long)rel ? rel : (uint32_t)gr);
+    uint32_t x = gr < 0 ? 0u : (gr > (long long)hi ? hi : (uint32_t)gr);
     for (int it = 0; it < 16; it++) {
-        if (key_bin(lo + base, list, r) != q) lo++;   // below the bin: its keys are larger
-        else if (lo > 0 && key_bin(lo - 1 + base, list, r) == q) lo--;
-        else return lo;
+        if (before(x)) {
+            if (x == hi) return hi + 1;
+            x++;
+        } else if (x > 0 && !before(x - 1)) {
+            x--;
+        } else {
+            return x;
+        }
     }
-    uint32_t a = 0, hi = rel;
-    while (a < hi) {
-        const uint32_t mid = a + ((hi - a) >> 1);
-        const int32_t qm = key_bin(mid + base, list, r);
-        if (list ? qm > q : qm < q) a = mid + 1;
-        else hi = mid;
+    uint32_t a = 0, b = hi + 1;
+    while (a < b) {
+        const uint32_t mid = a + ((b - a) >> 1);
+        if (before(mid)) a = mid + 1;
+        else b = mid;
     }
     return a;
+}
+
+// P(lo) of every bin of the field's range, both lists: table[list * bin_n + q - bin_q0]
+__global__ void __launch_bounds__(256) k_bin_table(Ctrl* c, uint32_t* region, const int* status) {
+    if (*status || !c->rank_bitmap || !c->bin_n) return;
+    const SortPlan sp = sort_plan(c);
+    const uint32_t W = c->bm_words, nb = c->bin_n;
+    const uint32_t span = c->max_key - ~c->min_inv;
+    const float r = c->r_f, w_f = c->w_f;
+    const uint2* pr0 = reinterpret_cast<const uint2*>(region + c->bm_off + 2 * (size_t)W);
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < 2 * nb; i += gridDim.x * blockDim.x) {
+        const int list = i >= nb;
+        const int32_t q = c->bin_q0 + (int32_t)(i - (list ? nb : 0u));
+        const uint32_t lo = bin_first(q, span, sp.base[list], list, r, w_f);
+        region[i] = bm_below(pr0 + (size_t)list * W, lo);
+    }
 }
 
 // delta of every list entry; four entries per thread at a time, their table
@@ -1571,41 +1612,43 @@ __global__ void __launch_bounds__(256) k_rank_delta(const uint2* s0, const uint2
                                                     const int* status) {
     if (*status || !c->rank_bitmap) return;
     const SortPlan sp = sort_plan(c);
-    const uint32_t W = c->bm_words;
+    const uint32_t W = c->bm_words, nb = c->bin_n;
+    const int32_t q0 = c->bin_q0;
     const float r = c->r_f, w_f = c->w_f;
     const int list = blockIdx.y;
     const uint2* s = list ? s1 : s0;
     const uint32_t k = list_count(c, list), base = sp.base[list];
-    const uint32_t* bm = region + c->bm_off + (size_t)list * 2 * W;
-    const uint32_t* pre = bm + W;
+    const uint2* pr = reinterpret_cast<const uint2*>(region + c->bm_off + 2 * (size_t)W) + (size_t)list * W;
+    const uint32_t* tab = region + (size_t)list * nb;
     const uint32_t stride = gridDim.x * blockDim.x;
     constexpr uint32_t TMASK = (1u << TILE_POS_BITS) - 1;
     for (uint32_t i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < k; i0 += 4 * stride) {
         uint2 e[4];
-        uint32_t rel[4], lo[4];
+        uint32_t rel[4], blo[4], bk[4], tp[4];
 #pragma unroll
         for (int j = 0; j < 4; j++) e[j] = i0 + j * stride < k ? s[i0 + j * stride] : make_uint2(base, 0u);
+        if (nb) {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            rel[j] = e[j].x - base;
-            lo[j] = bin_lo(e[j].x, rel[j], base, list, r, w_f);
-        }
-        uint32_t pr[4], br[4], pl[4], bl[4], tp[4];
+            for (int j = 0; j < 4; j++) {
+                rel[j] = e[j].x - base;
+                const int32_t q = key_bin(e[j].x, list, r);
+                blo[j] = tab[min((uint32_t)(q - q0), nb - 1)];
+                bk[j] = bm_below(pr, rel[j]);
+                tp[j] = tpre[e[j].y >> TILE_POS_BITS].y;
+            }
+        } else {
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            pr[j] = pre[rel[j] >> 5];
-            br[j] = bm[rel[j] >> 5];
-            pl[j] = pre[lo[j] >> 5];
-            bl[j] = bm[lo[j] >> 5];
-            tp[j] = tpre[e[j].y >> TILE_POS_BITS].y;
+            for (int j = 0; j < 4; j++) {
+                rel[j] = e[j].x - base;
+                const uint32_t lo = bin_first(key_bin(e[j].x, list, r), rel[j], base, list, r, w_f);
+                blo[j] = bm_below(pr, lo);
+                bk[j] = bm_below(pr, rel[j]);
+                tp[j] = tpre[e[j].y >> TILE_POS_BITS].y;
+            }
         }
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
-            if (i0 + j * stride >= k) continue;
-            const uint32_t below_rel = pr[j] + __popc(br[j] & ((1u << (rel[j] & 31)) - 1u));
-            const uint32_t below_lo = pl[j] + __popc(bl[j] & ((1u << (lo[j] & 31)) - 1u));
-            delta[tp[j] + (e[j].y & TMASK)] = (int32_t)(1u + below_rel - below_lo);
-        }
+        for (int j = 0; j < 4; j++)
+            if (i0 + j * stride < k) delta[tp[j] + (e[j].y & TMASK)] = (int32_t)(1u + bk[j] - blo[j]);
     }
 }
 
@@ -1620,6 +1663,7 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
     const uint32_t bg = (uint32_t)sms * 8;
     k_bm_sums<<<bg, 256, 0, st>>>(c, region, csum, status);
     k_bm_prefix<<<(uint32_t)sms * 2, 1024, 0, st>>>(c, region, csum, status);
+    k_bin_table<<<(uint32_t)sms * 2, 256, 0, st>>>(c, region, status);
     k_rank_delta<<<dim3(bg, 2), 256, 0, st>>>(listM, listm, c, region, tpre, delta, status);
     const uint32_t max_tiles = sw.max_tiles;
     uint32_t hg = hmin<uint32_t>((uint32_t)cdiv((uint64_t)max_tiles * OS_TILE, 256), (uint32_t)sms * 4);

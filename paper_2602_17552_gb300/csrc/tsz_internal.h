@@ -15,7 +15,7 @@ struct Tuning {
     int dec_slack_tiles = 0;        // 0: a quarter of the fused decoder's resident CTAs
     int saddle_records = 0;         // >= 0: neighbourhood records in the saddle rounds; < 0: field reads
     int dec_split = 0;              // > 0: the decoder stages as separate launches instead of fused
-    int rank_bitmap = 0;            // 0: dense ranks from key bitmaps when they fit; < 0: always the sort
+    int rank_bitmap = 0;            // 0: key bitmaps (+ bin table) when they fit; 1: no bin table; < 0: the sort
     int cd_columns = 0;             // 0: z-column pass for 3D fields when the planes allow; < 0: never
 };
 extern Tuning g_tuning;

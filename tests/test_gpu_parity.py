@@ -190,18 +190,32 @@ def test_parity_config3_full():
 
 
 def test_parity_rank_paths_narrow_key_span():
-    """A positive field inside one binade (keys span < 2^23) large enough for
-    the dense ranks to come from key bitmaps; the same stream as the radix-sort
-    path and as the oracle."""
+    """A positive field inside [256, 272) (keys span < 2^19), small enough in
+    key span for the dense ranks to come from key bitmaps: the stream is the
+    oracle's on the bitmap path with the per-bin rank table, on the bitmap path
+    without it, and on the radix-sort path.  Which path ran is read from the
+    workspace's control block (its first words: min_inv, max_key, nonfinite,
+    sort_passes, rank_bitmap, bm_words, bm_off, bin_n)."""
     from paper_2602_17552_gb300 import autotune
     g = synth.grf((96, 96, 96), -11 / 3, 21).numpy()
-    a = (384.0 + 100.0 * np.tanh(g / 3.0)).astype(np.float32)   # inside [256, 512)
-    assert a.min() > 256 and a.max() < 512
+    a = (264.0 + 7.0 * np.tanh(g / 3.0)).astype(np.float32)
+    assert a.min() > 256 and a.max() < 272
     obuf, _ = assert_parity(a, 1e-3, rel=True)
     f = torch.from_numpy(a).cuda()
+    ws = torch.empty(codec.compress_workspace_size(a.shape), dtype=torch.uint8, device="cuda")
+    seen = {}
     try:
-        autotune.apply({**autotune.DEFAULT, "rank_bitmap": -1})
-        sorted_path = codec.compress(f, 1e-3, "rel").cpu().numpy().tobytes()
+        for mode in (0, 1, -1):
+            autotune.apply({**autotune.DEFAULT, "rank_bitmap": mode})
+            call = codec.compress_async(f, 1e-3, "rel", ws=ws)
+            torch.cuda.synchronize()
+            assert int(call.status.item()) == 0
+            got = call.out[: int(call.size.item())].cpu().numpy().tobytes()
+            ctrl = ws[:32].cpu().numpy().view(np.uint32)
+            seen[mode] = (int(ctrl[4]), int(ctrl[7]))
+            assert got == obuf, f"rank_bitmap={mode}: " + section_report(got, obuf)
     finally:
         autotune.apply(autotune.DEFAULT)
-    assert sorted_path == obuf
+    assert seen[0][0] == 1 and seen[0][1] > 0, seen     # bitmaps + bin table
+    assert seen[1][0] == 1 and seen[1][1] == 0, seen    # bitmaps, no table
+    assert seen[-1][0] == 0, seen                      # radix sort
