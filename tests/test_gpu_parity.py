@@ -104,10 +104,11 @@ def test_parity_constant_and_tiny_range():
     assert eo.value.status == eg.value.status == _lib.EB_TOO_SMALL
 
 
-@pytest.mark.parametrize("shape", [(50, 60), (12, 16, 20)])
+@pytest.mark.parametrize("shape", [(50, 60), (12, 16, 20), (6, 8, 16), (40, 4, 64)])
 def test_parity_negative_zero_and_denormals(shape):
     """Signed zeros compare equal and subnormal differences keep their sign
-    (nx % 4 == 0: the vectorised critical-point pass, 2D and 3D)."""
+    (nx % 4 == 0: the vectorised critical-point pass, 2D and 3D; 128-point
+    planes: the z-column pass)."""
     rng = np.random.default_rng(3)
     a = rng.choice(np.array([-0.0, 0.0, 1e-40, -1e-40, 1e-38, -2e-38], np.float32), size=shape)
     assert_parity(a.astype(np.float32), 0.25, rel=True)
