@@ -38,10 +38,11 @@ sys.path.insert(0, ROOT)
 
 NOMINAL_HBM_GBS = 8000.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
-# kernel, per field point, from one ncu capture of the 512^3 workload at relative
-# eb 1e-3 (profiles/launches_turb512_rel1e-3.md); reported only for that workload
-# and only while the kernel is unchanged since the capture.
-TRAFFIC_PER_POINT = {"k_decode_fused": 811.6e6 / 512 ** 3}
+# kernel, per field point, from one ncu capture of the 384^3 case of the same
+# turbulence workload at relative eb 1e-3 (profiles/launches_turb512_rel1e-3.md),
+# scaled to the 512^3 launch by points; reported only for that workload and only
+# while the kernel is unchanged since the capture.
+TRAFFIC_PER_POINT = {"k_decode_fused": (85322496 + 230360832) / 384 ** 3}
 E2E_IN_FLIGHT = int(os.environ.get("TOPOSZP_E2E_IN_FLIGHT", "4"))   # round trips in flight at once
 
 
@@ -335,7 +336,7 @@ def run_ours(args):
     value = nbytes_all * args.steps / (total_ms * 1e-3) / 1e9
     # kernels per call (tsz_api.cu launch sequences; on the key-bitmap path the
     # radix-sort kernels are launched and return at once)
-    launches_c = 23 if topo else 7
+    launches_c = 24 if topo else 7
     launches_d = 6
     result = {
         "metric": "compress+decompress throughput (uncompressed bytes / round-trip time)",
@@ -344,7 +345,7 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": describe(spec), "n": n, "field_bytes": 4 * n, "eb_mode": mode, "eb": args.eb,
-                   "topology": topo, "l2": "inputs larger than L2 (field 537 MB > 129 MB)" if n * 4 > 129e6
+                   "topology": topo, "l2": f"inputs larger than L2 (field {4 * n / 1e6:.0f} MB > 129 MB)" if n * 4 > 129e6
                    else "field fits in L2: no flush between steps", "parallelism": f"replicas x{ws_n}"},
         "compress_gbs": round(4 * n / (comp_ms * 1e-3) / 1e9, 2),
         "decompress_gbs": round(4 * n / (dec_ms * 1e-3) / 1e9, 2),

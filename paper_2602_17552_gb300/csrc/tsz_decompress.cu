@@ -2,7 +2,7 @@
 //
 //   k_parse_header   one thread: validate the stream header against the call
 //                    and the buffer size, fill the control block
-//   k_dec_tile_*     offset pre-pass: per 2048-point tile, payload words and
+//   k_dec_tile_*     offset pre-pass: per 8192-point tile, payload words and
 //                    extremum counts -> exclusive prefixes (MD^ bookkeeping)
 //   k_decode_ranks   the inverse codec on the rank stream (delta sequence)
 //   k_decode_fused   persistent wavefront over tiles: BE^, LZ^ + B^, QZ^ (planes
@@ -602,7 +602,7 @@ __device__ __forceinline__ bool saddle_candidate_rec_any(int ndim, int r, const 
 
 // ---------------------------------------------------------- offset pre-pass
 //
-// Per decode tile (64 blocks): payload words from the widths and the number of
+// Per decode tile (256 blocks): payload words from the widths and the number of
 // extrema (m/M labels) -> exclusive prefixes.  With every tile's offsets known
 // up front the fused decoder needs no look-back.
 
@@ -664,8 +664,6 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
 }
 
 // exclusive scans of the tile sums (one CTA); totals must match the header.
-// Each thread owns a contiguous run of tiles and reads it in unrolled groups of
-// 16 independent loads.
 __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t* tile_w, const uint32_t* tile_c,
                                                         unsigned long long* pay_pre, uint32_t* cp_pre,
                                                         uint32_t* rtile_w, int* status) {
@@ -702,7 +700,7 @@ __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t*
 
 // ------------------------------------------------------- fused wavefront decode
 //
-// One persistent kernel over linear tiles of 2048 points.  The CTA that takes
+// One persistent kernel over linear tiles of 8192 points.  The CTA that takes
 // tile t runs
 //   S1(t)       decode: BE^, LZ^ + B^, QZ^ -> out = D0; positions of extrema
 //   S2(t - H)   CP^ + RP^ evaluation of that tile's extrema on the D0 snapshot
