@@ -52,7 +52,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256", "batch", "serve"])
+    ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256", "batch", "serve", "tradeoff"])
     ap.add_argument("--fields", type=int, default=96, help="batch workload: number of fields")
     ap.add_argument("--branches", type=int, default=0, help="batch workload: graph branches (0 = tuned)")
     ap.add_argument("--requests", type=int, default=400, help="serve workload: number of requests")
@@ -538,6 +538,31 @@ def run_serve(args):
         "served": a, "serial_plain": b}), flush=True)
 
 
+def run_tradeoff(args):
+    """Bit rate against FN / FP / FT (Section III-B), TopoSZp and its SZp-only
+    mode (no topology sections), relative bounds 1e-3, 1e-4, 1e-5, on the
+    1800x3600 and 512^3 fields: the synthetic analogue of Table II / Fig. 8.
+    One JSON line; not a throughput measurement."""
+    import torch
+    from paper_2602_17552_gb300 import codec
+    torch.cuda.set_device(0)
+    rows = []
+    for wl in ("climate", "turb512"):
+        spec = workload_spec(wl, 1e-3, args.side)
+        f = spec.make("cuda")
+        labels, cnt = codec.critical_points(f)
+        counts = cnt.cpu().tolist()
+        for eb in (1e-3, 1e-4, 1e-5):
+            for no_topo in (False, True):
+                r = codec.tradeoff(f, eb, "rel", no_topo=no_topo, labels=labels)
+                rows.append({"field": describe(spec).split(", relative")[0], "eb_rel": eb,
+                             "mode": "SZp only" if no_topo else "TopoSZp", "counts_rmsM": counts,
+                             **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}})
+        del f, labels
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "tradeoff", "data": "synthetic", "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -546,6 +571,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "tradeoff":
+        run_tradeoff(args)
     else:
         run_ours(args)
 

@@ -202,6 +202,29 @@ def topo_errors(labels_a: torch.Tensor, labels_b: torch.Tensor, n: int, *, strea
     return out.view(3, 4)
 
 
+def tradeoff(field: torch.Tensor, eb: float, mode: str = "rel", *, no_topo=False, labels=None,
+             stream=None) -> dict:
+    """One point of the bit-rate / topology-error trade-off (Section III-B,
+    Table II): compress and decompress ``field`` and count the false
+    negatives, false positives and false types of the decompressed field's
+    critical points against the original's (Section IV-A(1) labels), per type
+    in the order r, m, s, M (FN and FT by the original type, FP by the new).
+    ``labels``: the original's packed labels, if already computed.
+    Returns bytes, bit_rate (bits per value), ratio, max_err_over_eps (the
+    largest |decoded - input| over the stream's absolute bound), fn, fp, ft."""
+    n = field.numel()
+    if labels is None:
+        labels, _ = critical_points(field, counts=False, stream=stream)
+    buf = compress(field, eb, mode, no_topo=no_topo, stream=stream)
+    info = inspect(buf)
+    dec = decompress(buf, tuple(field.shape), stream=stream)
+    lab_d, _ = critical_points(dec, counts=False, stream=stream)
+    e = topo_errors(labels, lab_d, n, stream=stream).cpu().tolist()
+    err = float((dec.double() - field.double()).abs().max())
+    return {"bytes": int(buf.numel()), "bit_rate": 8.0 * buf.numel() / n, "ratio": 4.0 * n / buf.numel(),
+            "max_err_over_eps": err / info.eps, "fn": e[0], "fp": e[1], "ft": e[2]}
+
+
 def unpack_labels(words: torch.Tensor, n: int) -> torch.Tensor:
     """Packed 2-bit labels -> one uint8 per point (any device)."""
     w = words.to(torch.int64) & 0xFFFFFFFF

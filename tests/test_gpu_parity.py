@@ -220,3 +220,28 @@ def test_parity_rank_paths_narrow_key_span():
     assert seen[0][0] == 1 and seen[0][1] > 0, seen     # bitmaps + bin table
     assert seen[1][0] == 1 and seen[1][1] == 0, seen    # bitmaps, no table
     assert seen[-1][0] == 0, seen                      # radix sort
+
+
+@pytest.mark.parametrize("shape", [(96, 96, 96), (600, 700)])
+def test_parity_saddle_rounds_many_tiles(shape):
+    """RS^ rounds on a field of many decode tiles (RBF radius 3, two sweeps):
+    with neighbourhood records and with direct field reads, the oracle's field."""
+    from paper_2602_17552_gb300 import autotune
+    if len(shape) == 3:
+        a = synth.turbulence_3d(shape[0], seed=11).numpy()
+    else:
+        a = synth.climate_2d(*shape, seed=11).numpy()
+    opts = dict(rbf_k=7, rs_sweeps=2)
+    obuf = oracle.compress(a, 1e-3, rel=True, **opts)
+    oout = oracle.decompress(obuf, a.shape)
+    f = torch.from_numpy(a).cuda()
+    try:
+        for cfg in ({}, {"saddle_records": -1}):
+            autotune.apply({**autotune.DEFAULT, **cfg})
+            buf = codec.compress(f, 1e-3, "rel", **opts)
+            assert buf.cpu().numpy().tobytes() == obuf, cfg
+            out = codec.decompress(buf, a.shape).cpu().numpy()
+            assert np.array_equal(out.view(np.uint32), oout.view(np.uint32)), \
+                (cfg, int(np.count_nonzero(out.view(np.uint32) != oout.view(np.uint32))))
+    finally:
+        autotune.apply(autotune.DEFAULT)
