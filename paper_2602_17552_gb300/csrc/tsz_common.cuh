@@ -135,6 +135,9 @@ struct Ctrl {
     unsigned int front[4];    // per-stage frontiers of the fused decoder
     unsigned int tile_fused, pad5[3];
     unsigned int sad_col[8], sad_fill[8];   // lost saddles per colour (RS^ rounds)
+    // per-slice sums of the tile counts (field tiles, rank-stream tiles), added
+    // by the kernels that count, read by the slice-parallel scans
+    unsigned long long sl_tile[32][2], sl_rank[32][2];
     unsigned int sad_next[8];               // work counters of the rounds' evaluation
     Layout lo;
     float g_rbf[9];
@@ -239,6 +242,53 @@ __device__ void cta_scan_pairs(uint32_t cnt, Load load, Store store, unsigned lo
     }
     tot_a = ca;
     tot_b = cb;
+}
+
+// Slice-parallel form: SCAN_SLICES CTAs, CTA j scans entries [j * len, (j +
+// 1) * len) of [0, cnt), len = slice_len(cnt), offset by the sums of the
+// slices before it; the sums (sl[j] = {sum a, sum b} of slice j) were added
+// up by the kernel that wrote the entries.  No CTA waits on another.  Returns
+// the totals over all slices.
+constexpr uint32_t SCAN_SLICES = 32;
+__host__ __device__ inline uint32_t slice_len(uint32_t cnt) {
+    const uint32_t l = (cnt + SCAN_SLICES - 1) / SCAN_SLICES;
+    return l ? l : 1u;
+}
+template <class Load, class Store>
+__device__ void slice_scan_pairs(uint32_t cnt, const unsigned long long (*sl)[2], Load load, Store store,
+                                 unsigned long long (*s_w)[2], unsigned long long& tot_a,
+                                 unsigned long long& tot_b) {
+    __shared__ unsigned long long s_off[4];
+    const uint32_t j = blockIdx.x;
+    if (threadIdx.x < 32) {
+        const unsigned long long xa = sl[threadIdx.x][0], xb = sl[threadIdx.x][1];
+        unsigned long long oa = 0, ob = 0, ta = 0, tb = 0;
+        for (uint32_t i = 0; i < SCAN_SLICES; i++) {
+            const unsigned long long ya = __shfl_sync(FULL, xa, i), yb = __shfl_sync(FULL, xb, i);
+            if (i < j) { oa += ya; ob += yb; }
+            ta += ya;
+            tb += yb;
+        }
+        if (threadIdx.x == 0) {
+            s_off[0] = oa;
+            s_off[1] = ob;
+            s_off[2] = ta;
+            s_off[3] = tb;
+        }
+    }
+    __syncthreads();
+    const unsigned long long oa = s_off[0], ob = s_off[1];
+    tot_a = s_off[2];
+    tot_b = s_off[3];
+    const uint32_t len = slice_len(cnt);
+    const uint32_t lo = j * len < cnt ? j * len : cnt;
+    const uint32_t hi = cnt - lo < len ? cnt : lo + len;
+    unsigned long long sa, sb;
+    cta_scan_pairs(
+        hi - lo, [&](uint32_t i) { return load(lo + i); },
+        [&](uint32_t i, unsigned long long pa, unsigned long long pb) { store(lo + i, oa + pa, ob + pb); }, s_w, sa,
+        sb);
+    __syncthreads();   // s_off and s_w are free again
 }
 
 // spread the low 16 bits of x to the even bit positions

@@ -564,6 +564,9 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
     om += im - __popc(xmm);
     if (t == 0) {
         tcnt[tile] = make_uint2(tw, tM + tm);
+        unsigned long long* sl = c->sl_tile[tile / slice_len(gridDim.x)];
+        if (tw) atomicAdd(sl, (unsigned long long)tw);
+        if (tM + tm) atomicAdd(sl + 1, (unsigned long long)(tM + tm));
         if (TOPO) {
             s_base[0] = tM ? atomicAdd(&c->cnt_max, tM) : 0u;
             s_base[1] = tm ? atomicAdd(&c->cnt_min, tm) : 0u;
@@ -639,13 +642,13 @@ __global__ void __launch_bounds__(1024) k_enc_tile_scan(uint2* tcnt, uint32_t nt
     __shared__ unsigned long long s_w[33][2];
     if (*status) return;
     unsigned long long tw, tc;
-    cta_scan_pairs(
-        ntiles, [&](uint32_t i) { return tcnt[i]; },
+    slice_scan_pairs(
+        ntiles, c->sl_tile, [&](uint32_t i) { return tcnt[i]; },
         [&](uint32_t i, unsigned long long pw, unsigned long long pc) {
             tcnt[i] = make_uint2((uint32_t)pw, (uint32_t)pc);
         },
         s_w, tw, tc);
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         tcnt[ntiles] = make_uint2((uint32_t)tw, (uint32_t)tc);
         c->pay_words = tw;
         c->k_total = tc;
@@ -755,7 +758,10 @@ __global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restri
             if (q < (int)warp) ow += v;
             tw += v;
         }
-        if (t == 0) tcnt[tile] = make_uint2(tw, 0u);
+        if (t == 0) {
+            tcnt[tile] = make_uint2(tw, 0u);
+            if (tw) atomicAdd(&c->sl_rank[tile / slice_len(ntiles)][0], (unsigned long long)tw);
+        }
         if (words) {
             uint32_t* dst = s_buf + ow;
             dst[0] = sgn;
@@ -788,11 +794,11 @@ __global__ void __launch_bounds__(1024) k_rank_tile_scan(uint2* tcnt, Ctrl* c, c
     const uint32_t nbd = (uint32_t)cdiv(c->k_total, L);
     const uint32_t ntiles = (nbd + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;
     unsigned long long tw, tz;
-    cta_scan_pairs(
-        ntiles, [&](uint32_t i) { return tcnt[i]; },
+    slice_scan_pairs(
+        ntiles, c->sl_rank, [&](uint32_t i) { return tcnt[i]; },
         [&](uint32_t i, unsigned long long pw, unsigned long long) { tcnt[i] = make_uint2((uint32_t)pw, 0u); },
         s_w, tw, tz);
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
         tcnt[ntiles] = make_uint2((uint32_t)tw, 0u);
         c->rank_words = tw;
     }
@@ -1435,7 +1441,7 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2*
     } else {
         k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
     }
-    k_enc_tile_scan<<<1, 1024, 0, st>>>(tcnt, ntiles, c, status);
+    k_enc_tile_scan<<<SCAN_SLICES, 1024, 0, st>>>(tcnt, ntiles, c, status);
     uint32_t cg = hmin<uint32_t>(ntiles, (uint32_t)sms * 8);
     k_enc_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, ntiles, reinterpret_cast<uint32_t*>(out + lo.s5),
                                             status);
@@ -1694,7 +1700,7 @@ void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* s
     uint32_t grid = hmin<uint32_t>(max_tiles, (uint32_t)sms * 3);
     if (grid == 0) grid = 1;
     k_encode_ranks<<<grid, 256, 0, st>>>(delta, c, tcnt, scratch, out, status);
-    k_rank_tile_scan<<<1, 1024, 0, st>>>(tcnt, c, status);
+    k_rank_tile_scan<<<SCAN_SLICES, 1024, 0, st>>>(tcnt, c, status);
     uint32_t cg = hmin<uint32_t>(max_tiles, (uint32_t)sms * 8);
     k_rank_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, c, out, status);
 }

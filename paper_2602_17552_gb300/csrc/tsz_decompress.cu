@@ -639,6 +639,9 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
         if (lane == 0) {
             tile_w[t] = words;
             tile_c[t] = cps;
+            unsigned long long* sl = c->sl_tile[t / slice_len(ntiles)];
+            if (words) atomicAdd(sl, (unsigned long long)words);
+            if (cps) atomicAdd(sl + 1, (unsigned long long)cps);
         }
     }
     if (topo) {   // payload words of the rank stream's tiles (8192 deltas each)
@@ -657,40 +660,45 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
                 }
             }
             words = __reduce_add_sync(FULL, words);
-            if (lane == 0) rtile_w[t] = words;
+            if (lane == 0) {
+                rtile_w[t] = words;
+                if (words) atomicAdd(&c->sl_rank[t / slice_len(nrt)][0], (unsigned long long)words);
+            }
         }
     }
     if (corrupt) set_status(status, ST_CORRUPT);
 }
 
-// exclusive scans of the tile sums (one CTA); totals must match the header.
+// exclusive scans of the tile sums (slice-parallel: the sums of each slice
+// were added up by k_dec_tile_sums); totals must match the header.
 __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t* tile_w, const uint32_t* tile_c,
                                                         unsigned long long* pay_pre, uint32_t* cp_pre,
                                                         uint32_t* rtile_w, int* status) {
     __shared__ unsigned long long s_w[33][2];
     if (*status) return;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
     if (!(c->flags & FLAG_NO_TOPO)) {   // the rank stream's tile prefixes, in place
         const uint32_t nbd = (uint32_t)cdiv(c->k_total, L);
         const uint32_t nrt = (nbd + DT_BLOCKS - 1) / DT_BLOCKS;
         unsigned long long rw, rz;
-        cta_scan_pairs(
-            nrt, [&](uint32_t i) { return make_uint2(rtile_w[i], 0u); },
+        slice_scan_pairs(
+            nrt, c->sl_rank, [&](uint32_t i) { return make_uint2(rtile_w[i], 0u); },
             [&](uint32_t i, unsigned long long pw, unsigned long long) { rtile_w[i] = (uint32_t)pw; }, s_w, rw, rz);
-        if (threadIdx.x == 0) {
+        if (lead) {
             rtile_w[nrt] = (uint32_t)rw;
             if (rw != c->rank_words) set_status(status, ST_CORRUPT);
         }
     }
     const uint32_t ntiles = (c->g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
     unsigned long long tw, tc;
-    cta_scan_pairs(
-        ntiles, [&](uint32_t i) { return make_uint2(tile_w[i], tile_c[i]); },
+    slice_scan_pairs(
+        ntiles, c->sl_tile, [&](uint32_t i) { return make_uint2(tile_w[i], tile_c[i]); },
         [&](uint32_t i, unsigned long long pw, unsigned long long pc) {
             pay_pre[i] = pw;
             cp_pre[i] = (uint32_t)pc;
         },
         s_w, tw, tc);
-    if (threadIdx.x == 0) {
+    if (lead) {
         pay_pre[ntiles] = tw;
         cp_pre[ntiles] = (uint32_t)tc;
         const bool topo = !(c->flags & FLAG_NO_TOPO);
@@ -1334,7 +1342,7 @@ void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* 
     uint32_t blocks = hmin<uint32_t>((ntiles + 7) / 8, (uint32_t)sms * 8);
     if (blocks == 0) blocks = 1;
     k_dec_tile_sums<<<blocks, 256, 0, st>>>(in, c, tile_w, tile_c, rtile_w, status);
-    k_dec_tile_scan<<<1, 1024, 0, st>>>(c, tile_w, tile_c, pay_pre, cp_pre, rtile_w, status);
+    k_dec_tile_scan<<<SCAN_SLICES, 1024, 0, st>>>(c, tile_w, tile_c, pay_pre, cp_pre, rtile_w, status);
 }
 
 void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
