@@ -609,6 +609,11 @@ __device__ __forceinline__ bool saddle_candidate_rec_any(int ndim, int r, const 
 __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict__ in, Ctrl* c,
                                                        uint32_t* tile_w, uint32_t* tile_c, uint32_t* rtile_w,
                                                        int* status) {
+    // per-slice sums of this CTA's tiles (field words, extrema; rank words),
+    // added to the control block once per slice at the end
+    __shared__ unsigned long long s_sl[SCAN_SLICES][3];
+    for (uint32_t i = threadIdx.x; i < SCAN_SLICES * 3; i += blockDim.x) s_sl[i / 3][i % 3] = 0;
+    __syncthreads();
     if (*status) return;
     const Geo g = c->g;
     const Layout lo = c->lo;
@@ -639,7 +644,7 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
         if (lane == 0) {
             tile_w[t] = words;
             tile_c[t] = cps;
-            unsigned long long* sl = c->sl_tile[t / slice_len(ntiles)];
+            unsigned long long* sl = s_sl[t / slice_len(ntiles)];
             if (words) atomicAdd(sl, (unsigned long long)words);
             if (cps) atomicAdd(sl + 1, (unsigned long long)cps);
         }
@@ -662,11 +667,16 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
             words = __reduce_add_sync(FULL, words);
             if (lane == 0) {
                 rtile_w[t] = words;
-                if (words) atomicAdd(&c->sl_rank[t / slice_len(nrt)][0], (unsigned long long)words);
+                if (words) atomicAdd(&s_sl[t / slice_len(nrt)][2], (unsigned long long)words);
             }
         }
     }
     if (corrupt) set_status(status, ST_CORRUPT);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < SCAN_SLICES * 3; i += blockDim.x) {
+        const unsigned long long v = s_sl[i / 3][i % 3];
+        if (v) atomicAdd(i % 3 < 2 ? &c->sl_tile[i / 3][i % 3] : &c->sl_rank[i / 3][0], v);
+    }
 }
 
 // exclusive scans of the tile sums (slice-parallel: the sums of each slice
