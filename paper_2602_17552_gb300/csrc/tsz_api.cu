@@ -244,7 +244,7 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     uint32_t* labels = reinterpret_cast<uint32_t*>(o + lo.s6);
 
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
-    cudaMemsetAsync(ws, 0, w.os_desc_a, st);   // control block, look-back descriptors, sort counters
+    cudaMemsetAsync(ws, 0, w.os_desc_a, st);   // control block, per-tile counts, sort histograms and counters
     k_init_ctrl<<<1, 1, 0, st>>>(c, g, mode == TOPOSZP_EB_REL ? 1 : 0, eb, p.flags, (int)p.rs_sweeps);
     stage(0, st);
     launch_range_cd(field, g, c, labels, topo, sms, st);

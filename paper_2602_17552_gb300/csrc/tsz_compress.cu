@@ -1,15 +1,24 @@
 // tsz_compress.cu -- compression kernels (Section IV-A of arXiv 2602.17552).
 //
 // Pipeline on one stream:
-//   k_range_cd      one read of the field: value range (min, max) and, unless
-//                   NO_TOPO, the CD labels written straight into section (6)
+//   k_range_cd_col / _vec / k_range_cd
+//                   one read of the field: value range (min, max), finite
+//                   check and, unless NO_TOPO, the CD labels written straight
+//                   into section (6) (the column form walks z with rows
+//                   z - 1, z, z + 1 in registers)
 //   k_qparams       one thread: eps, bin width w, its reciprocal r, half-width h
-//   k_encode<Field> one read of field + labels: QZ, B + LZ, BE with a
-//                   single-pass decoupled look-back for the payload offsets and
-//                   the positions of extrema; extrema keys go to two lists
-//   radix sort      per list, LSD 8-bit digits on order-preserving keys
-//   k_rank_*        dense rank per (type, bin) segment = RP's delta
-//   k_encode<Rank>  the same codec on the delta sequence (no QZ)
+//   k_bm_zero       the rank mode (key bitmaps or radix sort) and zeroed bitmaps
+//   k_encode_field  one read of field + labels per 8192-point tile: QZ, B + LZ,
+//                   BE into the tile's payload slot; extrema keys to two lists
+//                   (and their bits to the key bitmaps)
+//   k_enc_tile_scan, k_enc_copy
+//                   slice-parallel scan of the tile counts, slots to the stream
+//   k_bm_sums, k_bm_prefix, k_bin_table, k_rank_delta
+//                   dense rank per (type, bin) = RP's delta from the bitmaps,
+//                   or, when the key span does not fit, the radix sort
+//                   (k_os_*: LSD passes of <= 9-bit digits) and k_rank_*
+//   k_encode_ranks, k_rank_tile_scan, k_rank_copy
+//                   the same codec on the delta sequence (no QZ)
 //   k_finalize      header, section padding, stream size
 #include "tsz_internal.h"
 
