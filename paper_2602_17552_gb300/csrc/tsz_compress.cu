@@ -1534,34 +1534,70 @@ __global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region
     }
 }
 
-// (exclusive popcount prefix, word) of every bitmap word (chunk offsets summed
-// from csum)
+// (exclusive popcount prefix, word) of every bitmap word.  A CTA per chunk of
+// BM_CHUNK words: 8 consecutive words per thread (16-byte loads and stores;
+// W, the region offset and every chunk are 16-byte aligned), a shuffle scan
+// per warp, one barrier for the warp totals; the chunk's offset is the sum of
+// the chunk sums (csum) before it.
 __global__ void __launch_bounds__(1024) k_bm_prefix(Ctrl* c, uint32_t* region, const uint32_t* csum,
                                                     const int* status) {
-    __shared__ unsigned long long s_w[33][2];
-    __shared__ uint32_t s_o[32];
+    __shared__ uint32_t s_o[32], s_wt[32];
     if (*status || !c->rank_bitmap) return;
     const uint32_t W = c->bm_words, nch = (W + BM_CHUNK - 1) / BM_CHUNK;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     region += c->bm_off;
+    static_assert(BM_CHUNK == 1024 * 8, "one pass of 8 words per thread");
     for (uint32_t q = blockIdx.x; q < 2 * nch; q += gridDim.x) {
         const uint32_t list = q / nch, ch = q % nch;
-        // offset: the chunk sums before this one in its list
         uint32_t o = 0;
         for (uint32_t i = threadIdx.x; i < ch; i += blockDim.x) o += csum[list * nch + i];
         o = __reduce_add_sync(FULL, o);
-        if ((threadIdx.x & 31) == 0) s_o[threadIdx.x >> 5] = o;
-        __syncthreads();
-        uint32_t off = 0;
-        for (int w = 0; w < 32; w++) off += s_o[w];
+        if (lane == 0) s_o[warp] = o;
         const uint32_t* bm = region + (size_t)list * W + (size_t)ch * BM_CHUNK;
         uint2* pr = reinterpret_cast<uint2*>(region + 2 * (size_t)W) + (size_t)list * W + (size_t)ch * BM_CHUNK;
         const uint32_t nw = min(BM_CHUNK, W - ch * BM_CHUNK);
-        unsigned long long ta, tb;
-        cta_scan_pairs(
-            nw, [&](uint32_t i) { return make_uint2((uint32_t)__popc(bm[i]), 0u); },
-            [&](uint32_t i, unsigned long long pa, unsigned long long) { pr[i] = make_uint2(off + (uint32_t)pa, bm[i]); },
-            s_w, ta, tb);
+        const uint32_t i0 = threadIdx.x * 8;
+        const bool full = i0 + 8 <= nw;
+        uint32_t w[8];
+        if (full) {
+            const uint4 x = *reinterpret_cast<const uint4*>(bm + i0);
+            const uint4 y = *reinterpret_cast<const uint4*>(bm + i0 + 4);
+            w[0] = x.x, w[1] = x.y, w[2] = x.z, w[3] = x.w, w[4] = y.x, w[5] = y.y, w[6] = y.z, w[7] = y.w;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++) w[j] = i0 + j < nw ? bm[i0 + j] : 0u;
+        }
+        uint32_t pre[8], run = 0;
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            pre[j] = run;
+            run += __popc(w[j]);
+        }
+        uint32_t incl = run;
+#pragma unroll
+        for (int of = 1; of < 32; of <<= 1) {
+            const uint32_t t = __shfl_up_sync(FULL, incl, of);
+            if (lane >= (uint32_t)of) incl += t;
+        }
+        if (lane == 31) s_wt[warp] = incl;
         __syncthreads();
+        uint32_t base = incl - run;
+#pragma unroll
+        for (int k = 0; k < 32; k++) {
+            base += s_o[k];
+            if (k < (int)warp) base += s_wt[k];
+        }
+        if (full) {
+            uint4* d = reinterpret_cast<uint4*>(pr + i0);
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                d[j] = make_uint4(base + pre[2 * j], w[2 * j], base + pre[2 * j + 1], w[2 * j + 1]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if (i0 + j < nw) pr[i0 + j] = make_uint2(base + pre[j], w[j]);
+        }
+        __syncthreads();   // s_o and s_wt are reused by the next chunk
     }
 }
 
