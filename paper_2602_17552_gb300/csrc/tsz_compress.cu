@@ -1519,9 +1519,13 @@ __global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region
     for (uint32_t q = blockIdx.x; q < 2 * nch; q += gridDim.x) {
         const uint32_t list = q / nch, ch = q % nch;
         const uint32_t* bm = region + (size_t)list * W + (size_t)ch * BM_CHUNK;
-        const uint32_t nw = min(BM_CHUNK, W - ch * BM_CHUNK);
+        const uint32_t nw = min(BM_CHUNK, W - ch * BM_CHUNK);   // a multiple of 4, like W
+        const uint4* b4 = reinterpret_cast<const uint4*>(bm);
         uint32_t a = 0;
-        for (uint32_t i = threadIdx.x; i < nw; i += blockDim.x) a += __popc(bm[i]);
+        for (uint32_t i = threadIdx.x; i < nw / 4; i += blockDim.x) {
+            const uint4 v = b4[i];
+            a += __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+        }
         a = __reduce_add_sync(FULL, a);
         if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = a;
         __syncthreads();
