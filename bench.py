@@ -187,6 +187,29 @@ def dist_setup(args):
     return ws, rank, local
 
 
+def rank_spec(name, eb, side, rank):
+    """Rank r's workload: the same configuration with its own seed (the ranks
+    are independent replicas; no data crosses between them)."""
+    from dataclasses import replace
+    spec = workload_spec(name, eb, side)
+    return replace(spec, seed=spec.seed + 1000 * rank)
+
+
+def rank_max(x, pg, device):
+    """x of the slowest rank (an all-reduce MAX over the job); x itself on one rank."""
+    if not pg:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_gbs(bytes_per_rank_step, world, steps, seconds):
+    """Uncompressed bytes of every rank and step over the job's time, in GB/s."""
+    return bytes_per_rank_step * world * steps / seconds / 1e9
+
+
 def run_reference(args):
     import torch
     ws, rank, local = dist_setup(args)
@@ -229,9 +252,7 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    spec = workload_spec(args.workload, args.eb, args.side)
-    from dataclasses import replace
-    spec = replace(spec, seed=spec.seed + 1000 * rank)
+    spec = rank_spec(args.workload, args.eb, args.side, rank)
     field = spec.make(dev)
     rel = spec.eb_mode == "rel"
     eb = args.eb if rel else 1e-3 * float(field.max() - field.min())
@@ -283,11 +304,8 @@ def run_ours(args):
             outer[s + 1].record(stream)
         torch.cuda.synchronize()
     L.toposzp_set_stage_events(None, 0)
-    total_ms = outer[0].elapsed_time(outer[-1])
+    total_ms = rank_max(outer[0].elapsed_time(outer[-1]), pg, dev)
     if pg:
-        t = torch.tensor([total_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_ms = float(t.item())
         pg.barrier()
     if int(st_c.item()) or int(st_d.item()):
         raise RuntimeError("device status set during the timed region")
@@ -332,8 +350,7 @@ def run_ours(args):
     roofline = {"kernel": dom, "bound": "hbm", "achieved": kout[dom]["achieved_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kout[dom]["frac"], "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}
-    nbytes_all = 4 * n * ws_n
-    value = nbytes_all * args.steps / (total_ms * 1e-3) / 1e9
+    value = whole_job_gbs(4 * n, ws_n, args.steps, total_ms * 1e-3)
     # kernels per call (tsz_api.cu launch sequences; on the key-bitmap path the
     # radix-sort kernels are launched and return at once)
     launches_c = 24 if topo else 7
@@ -430,11 +447,8 @@ def run_ours(args):
                 raise RuntimeError("device status set during the end-to-end steps")
         if not torch.equal(slots[0]["hrec"], rec.cpu()):
             raise RuntimeError("end-to-end round trip differs from the device-timed one")
-        if pg:
-            t = torch.tensor([e2e_s], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        result["e2e"] = {"value": round(4 * n * ws_n / e2e_s / 1e9, 3), "unit": "GB/s",
+        e2e_s = rank_max(e2e_s, pg, dev)
+        result["e2e"] = {"value": round(whole_job_gbs(4 * n, ws_n, 1, e2e_s), 3), "unit": "GB/s",
                          "h2d_bytes_per_step": int(4 * n + csize), "d2h_bytes_per_step": int(csize + 4 * n),
                          "in_flight": E2E_IN_FLIGHT}
     if rank == 0 and not args.no_cpu_baseline:
