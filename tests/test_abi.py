@@ -91,3 +91,36 @@ def test_inspect_reads_oracle_header(lib):
     assert info.total_size == len(buf) and info.k_min == h["k_min"] and info.k_max == h["k_max"]
     bad = ctypes.create_string_buffer(b"XXXX" + buf[4:256], 256)
     assert lib.toposzp_inspect(bad, 256, ctypes.byref(info)) == _lib.CORRUPT_STREAM
+
+
+@pytest.mark.parametrize("shape", [(33, 65), (9, 10, 11)])
+def test_bound_covers_the_worst_case_stream(lib, shape):
+    """Every point an extremum (a checkerboard of random magnitudes: each face
+    neighbour has the other sign) and wide residuals (a tight bound): the rank
+    stream and the payload are as large as they get, still within the bound."""
+    rng = np.random.default_rng(5)
+    parity = np.indices(shape).sum(axis=0) % 2
+    a = ((1.0 + rng.random(shape)) * np.where(parity == 0, 1.0, -1.0)).astype(np.float32)
+    buf = oracle.compress(a, 1e-5, rel=True)
+    h = oracle.header(buf)
+    assert h["k_min"] + h["k_max"] == a.size
+    nd = len(shape)
+    assert len(buf) <= lib.toposzp_compress_bound(nd, _lib.dims3(nd, tuple(reversed(shape))))
+
+
+def test_size_limits_on_host(lib):
+    """Fields of up to 2^31 - 1 points are sized; 2^31 points are not; a zero
+    extent is an invalid argument (all decided on the host)."""
+    largest, too_big = _lib.dims3(2, (2 ** 31 - 1, 1)), _lib.dims3(2, (2 ** 16, 2 ** 15))
+    for f in (lib.toposzp_compress_bound, lib.toposzp_compress_workspace_size,
+              lib.toposzp_decompress_workspace_size, lib.toposzp_workspace_size):
+        assert f(2, largest) > 0
+        assert f(2, too_big) == 0
+    p = _lib.Params()
+    lib.toposzp_default_params(ctypes.byref(p))
+    fake = ctypes.c_void_p(256)
+    for dims in ((0, 8), (8, 0)):
+        assert lib.toposzp_compress(fake, 2, _lib.dims3(2, dims), 1, 1e-3, ctypes.byref(p), fake, 1 << 20, fake,
+                                    fake, 1 << 20, fake, None) == _lib.INVALID_ARG
+    assert lib.toposzp_compress(fake, 2, too_big, 1, 1e-3, ctypes.byref(p), fake, 1 << 20, fake, fake,
+                                1 << 20, fake, None) == _lib.UNSUPPORTED

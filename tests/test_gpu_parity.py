@@ -245,3 +245,14 @@ def test_parity_saddle_rounds_many_tiles(shape):
                 (cfg, int(np.count_nonzero(out.view(np.uint32) != oout.view(np.uint32))))
     finally:
         autotune.apply(autotune.DEFAULT)
+
+
+@pytest.mark.parametrize("shape", [(33, 65), (9, 10, 11), (100, 300), (20, 30, 40)])
+def test_parity_every_point_an_extremum(shape):
+    """A checkerboard of random magnitudes: every point is a minimum or a
+    maximum (the largest extremum lists and rank stream a field can have)."""
+    rng = np.random.default_rng(5)
+    parity = np.indices(shape).sum(axis=0) % 2
+    a = ((1.0 + rng.random(shape)) * np.where(parity == 0, 1.0, -1.0)).astype(np.float32)
+    for eb in (1e-5, 1e-2):
+        assert_parity(a, eb, rel=True)
