@@ -249,6 +249,17 @@ void toposzp_batch_plan_destroy(void* plan);
  * single-threaded benchmark. */
 toposzp_status toposzp_set_stage_events(void* const* events, int count);
 
+/* Failure-path test hook (Section IV-B decoder; no effect unless set).  With
+ * tile >= 0, the fused decoder of later toposzp_decompress calls never
+ * publishes that 8192-point tile's decode stage: the stage waits that depend
+ * on it run out their bounded spin, the call finishes with
+ * TOPOSZP_ERR_TIMEOUT in its status word, and the context stays usable.  No
+ * access leaves its buffer on that path (every position read from the
+ * workspace is checked against n).  tile = -1 (the default) turns it off.
+ * The decoder's split form (tuning dec_split = 1) has no waits and ignores it.
+ * Process-wide and not thread-safe: for tests only. */
+toposzp_status toposzp_set_test_hold(int32_t tile);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,7 +50,7 @@ EXPORTS = ("toposzp_default_params", "toposzp_status_string", "toposzp_compress_
            "toposzp_compress_workspace_size", "toposzp_decompress_workspace_size", "toposzp_workspace_size",
            "toposzp_compress",
            "toposzp_inspect", "toposzp_decompress", "toposzp_critical_points", "toposzp_topo_errors",
-           "toposzp_set_stage_events", "toposzp_compress_noalloc", "toposzp_noalloc_max_points", "toposzp_set_tuning",
+           "toposzp_set_stage_events", "toposzp_set_test_hold", "toposzp_compress_noalloc", "toposzp_noalloc_max_points", "toposzp_set_tuning",
            "toposzp_batch_plan_create", "toposzp_batch_workspace_size", "toposzp_batch_branches",
            "toposzp_batch_compress", "toposzp_batch_decompress", "toposzp_batch_plan_destroy")
 
@@ -88,6 +88,8 @@ def load() -> ctypes.CDLL:
     L.toposzp_topo_errors.argtypes = [vp, vp, u64, vp, vp]
     L.toposzp_topo_errors.restype = c_int
     L.toposzp_set_stage_events.argtypes = [ctypes.POINTER(ctypes.c_void_p), c_int]
+    L.toposzp_set_test_hold.argtypes = [ctypes.c_int32]
+    L.toposzp_set_test_hold.restype = c_int
     L.toposzp_set_stage_events.restype = c_int
     L.toposzp_compress_noalloc.argtypes = [vp, c_int, dims_t, c_int, ctypes.c_double, ctypes.POINTER(Params),
                                            vp, u64, vp, i32p, vp]

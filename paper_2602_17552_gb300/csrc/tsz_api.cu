@@ -115,6 +115,7 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 static cudaEvent_t g_stage_ev[9];
 static bool g_stage_on = false;
+static int32_t g_test_hold = -1;   // toposzp_set_test_hold: the decode tile never published
 static void stage(int i, cudaStream_t st) {
     if (g_stage_on) cudaEventRecord(g_stage_ev[i], st);
 }
@@ -333,7 +334,7 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     cudaMemsetAsync(ws, 0, w.tile_w, st);   // control block, rank tile sums, stage flags
     stage(5, st);
-    launch_parse_header(src, in_size, n_out, c, status, st);
+    launch_parse_header(src, in_size, n_out, c, status, (uint32_t)(g_test_hold + 1), st);
     // the rank stream's tile sums and prefixes live in the (no longer used) rank descriptor region
     uint32_t* rtile = reinterpret_cast<uint32_t*>(ws + w.rdesc);
     launch_dec_offsets(src, c, reinterpret_cast<uint32_t*>(ws + w.tile_w), reinterpret_cast<uint32_t*>(ws + w.tile_c),
@@ -382,6 +383,12 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     u.rank_bitmap = t->rank_bitmap;
     u.cd_columns = t->cd_columns;
     g_tuning = u;
+    return TOPOSZP_OK;
+}
+
+toposzp_status toposzp_set_test_hold(int32_t tile) {
+    if (tile < -1) return TOPOSZP_ERR_INVALID_ARG;
+    g_test_hold = tile;
     return TOPOSZP_OK;
 }
 

@@ -133,7 +133,7 @@ struct Ctrl {
     unsigned long long stat_restored, stat_skipped, stat_saddle;
     unsigned int sad_cnt[8];
     unsigned int front[4];    // per-stage frontiers of the fused decoder
-    unsigned int tile_fused, pad5[3];
+    unsigned int tile_fused, test_hold, pad5[2];   // test_hold: tile + 1 never published (0: none)
     unsigned int sad_col[8], sad_fill[8];   // lost saddles per colour (RS^ rounds)
     // per-slice sums of the tile counts (field tiles, rank-stream tiles), added
     // by the kernels that count, read by the slice-parallel scans

@@ -60,7 +60,7 @@ void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, f
 
 // ---- decompression launchers (tsz_decompress.cu)
 void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c, int* status,
-                         cudaStream_t st);
+                         uint32_t test_hold, cudaStream_t st);
 void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* tile_c,
                         unsigned long long* pay_pre, uint32_t* cp_pre, uint32_t* rtile_w, uint32_t ntiles, int sms,
                         int* status, cudaStream_t st);

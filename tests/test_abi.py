@@ -124,3 +124,9 @@ def test_size_limits_on_host(lib):
                                     fake, 1 << 20, fake, None) == _lib.INVALID_ARG
     assert lib.toposzp_compress(fake, 2, too_big, 1, 1e-3, ctypes.byref(p), fake, 1 << 20, fake, fake,
                                 1 << 20, fake, None) == _lib.UNSUPPORTED
+
+
+def test_test_hold_arguments(lib):
+    assert lib.toposzp_set_test_hold(-2) == _lib.INVALID_ARG
+    assert lib.toposzp_set_test_hold(3) == _lib.OK
+    assert lib.toposzp_set_test_hold(-1) == _lib.OK
