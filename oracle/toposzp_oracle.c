@@ -522,8 +522,19 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
     if (ndim == 2 && dims[2] != 1) return ORC_CORRUPT;
     if (n != dims[0] * dims[1] * dims[2] || n != n_out || nblk != cdiv(n, L)) return ORC_CORRUPT;
     if (kk != 3 && kk != 5 && kk != 7) return ORC_CORRUPT;
+    /* a header this writer cannot produce marks a damaged stream (R7): every
+     * field within the range compression gives it, every section offset equal
+     * to the layout recomputed from the counts */
+    if (flags > 1u || sweeps < 1u || sweeps > 16u) return ORC_CORRUPT;
+    if (!(isfinite(qp.w_f) && qp.w_f > 0.0f) || !(isfinite(qp.h_f) && qp.h_f >= 0.0f)) return ORC_CORRUPT;
+    if (dims[0] > n_out || dims[1] > n_out || dims[2] > n_out) return ORC_CORRUPT;
+    if (kmin > cdiv(n, 2) || kmax > cdiv(n, 2) || (!topo && (kmin || kmax))) return ORC_CORRUPT;
+    if (pay_words > nblk * (L + 1) || rpay > cdiv(kmin + kmax, L) * (L + 1)) return ORC_CORRUPT;
     layout_t lo;
     field_layout(n, nblk, topo, pay_words, &lo);
+    if (get64(in + 152) != lo.s1 || get64(in + 160) != lo.s2 || get64(in + 168) != lo.s4 ||
+        get64(in + 176) != lo.s6 || get64(in + 184) != lo.s5 || get64(in + 192) != (topo ? lo.s7 : lo.end))
+        return ORC_CORRUPT;
     uint64_t sub[5];
     uint64_t k = kmin + kmax;
     uint64_t end = lo.end;
@@ -619,6 +630,12 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
                 uint64_t c[3] = {i % dims[0], (i / dims[0]) % dims[1], i / (dims[0] * dims[1])};
                 int nc;
                 if (orc_colour(ndim, c[0], c[1], c[2], &nc) != col) continue;
+                /* a saddle label is valid at interior points only (R8/R9); a
+                 * damaged stream may carry one elsewhere: never refined */
+                int inside = 1;
+                for (int ax = 0; ax < ndim; ax++)
+                    if (c[ax] == 0 || c[ax] + 1 >= d3[ax]) inside = 0;
+                if (!inside) continue;
                 if (orc_classify(F, ndim, d3, i) == ORC_SAD) continue;   /* not lost */
                 float Fp = F[i];
                 /* tolerance eps_RBF = min(0.1 h, half the smallest nonzero local gap) (R15) */

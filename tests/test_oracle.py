@@ -479,3 +479,26 @@ def test_corrupt_stream_rejected():
             oracle.decompress(bad, a.shape)
     with pytest.raises(oracle.OracleError):
         oracle.decompress(bytes(buf), (a.shape[0] + 1, a.shape[1]))
+
+
+@pytest.mark.parametrize("offset,value", [
+    (40, 2),                  # flags: only NO_TOPO is defined
+    (96, 0), (96, 17),        # RS^ sweeps outside 1..16
+    (64, 0x7F800000),         # bin width w = +inf
+    (72, 0xBF800000),         # half-width h < 0
+    (120, 10 ** 6),           # more minima than half the points
+    (160, 0),                 # section (2) offset off the layout
+    (192, 7),                 # section (7) offset off the layout
+])
+def test_header_outside_what_compression_writes_is_corrupt(offset, value):
+    """A header field outside the range compression gives it marks a damaged
+    stream (stream layout, Section IV-A): the decoder refuses it rather than
+    running e.g. 2^31 sweeps."""
+    import struct
+    a = synth.gaussian_bumps_2d(20, 24, count=4, seed=1).numpy()
+    buf = bytearray(oracle.compress(a, 1e-3, rel=True))
+    width = 8 if offset in (120, 160, 192) else 4
+    buf[offset:offset + width] = struct.pack("<Q" if width == 8 else "<I", value)
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.decompress(bytes(buf), a.shape)
+    assert ei.value.status == oracle.CORRUPT
