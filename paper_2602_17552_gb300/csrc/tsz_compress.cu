@@ -1324,19 +1324,6 @@ __global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rb
     *out_size = lo.end;
 }
 
-// saddle count for the header (labels already written)
-__global__ void k_count_saddles(const uint32_t* labels, Ctrl* c, const int* status) {
-    if (*status) return;
-    const uint32_t nwords = (c->g.n + 15) / 16;
-    unsigned long long s = 0;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += gridDim.x * blockDim.x) {
-        uint32_t w = labels[i];
-        s += __popc(((w >> 1) & 0x55555555u) & ~w & 0x55555555u);
-    }
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
-    if ((threadIdx.x & 31) == 0 && s) atomicAdd(&c->k_sad, s);
-}
-
 // ============================================================ host launchers
 
 static bool vec_ok(const float* a, const Geo& g) {
@@ -1752,14 +1739,6 @@ void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* s
     k_rank_tile_scan<<<SCAN_SLICES, 1024, 0, st>>>(tcnt, c, status);
     uint32_t cg = hmin<uint32_t>(max_tiles, (uint32_t)sms * 8);
     k_rank_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, c, out, status);
-}
-
-void launch_count_saddles(const uint32_t* labels, Ctrl* c, uint32_t n, int sms, int* status,
-                          cudaStream_t st) {
-    uint32_t nwords = (n + 15) / 16;
-    uint32_t blocks = hmin<uint32_t>((nwords + 255) / 256, (uint32_t)sms * 4);
-    if (blocks == 0) blocks = 1;
-    k_count_saddles<<<blocks, 256, 0, st>>>(labels, c, status);
 }
 
 void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, float rbf_sigma,

@@ -53,8 +53,6 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
                   int sms, int* status, cudaStream_t st);
 void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* scratch, uint8_t* out,
                          uint64_t max_k, int sms, int* status, cudaStream_t st);
-void launch_count_saddles(const uint32_t* labels, Ctrl* c, uint32_t n, int sms, int* status,
-                          cudaStream_t st);
 void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, float rbf_sigma,
                      int* status, cudaStream_t st);
 
