@@ -92,8 +92,17 @@ uint64_t toposzp_workspace_size(int ndim, const uint64_t dims[3]);
  *   workspace    device scratch of ws_bytes >= toposzp_compress_workspace_size;
  *                its contents on entry do not matter and are clobbered
  *   status       device int32, set to 0 then to the first device error
- * The stream layout (header and sections) is described in the design notes;
- * sections follow the paper's order with the fixed-size ones first. */
+ * Stream format v1 (little-endian): a 256-byte header -- magic "TSZP",
+ * version, ndim, block length L = 32, dims, flags, bound mode and eb, eps, the
+ * quantiser's w, 1/w and h, a constant-field flag, the value range, RBF k and
+ * sigma, sweeps, n, block count, extremum and saddle counts, the sum of the
+ * absolute residuals, section offsets, total size, payload word counts, RBF
+ * weights -- then the sections, each 16-byte aligned: (1) the
+ * constant-block bitmap, (2) block widths (1 byte each), (4) first codes
+ * (int32 each), (6) critical-point labels (2 bits per point), (5) the blocks'
+ * sign and magnitude planes, (7) the rank stream coded the same way.  (6) and
+ * (7) are absent with TOPOSZP_NO_TOPO.  The paper's section order (Section
+ * IV-A, Fig. 6), with the fixed-size sections first. */
 toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dims[3],
                                 toposzp_eb_mode mode, double eb, const toposzp_params* params,
                                 void* out, uint64_t out_capacity, uint64_t* out_size,

@@ -4,7 +4,7 @@
  * every float operation below is one IEEE-754 binary32/binary64 operation,
  * rounded to nearest, with no fused multiply-add.  Written from the paper's
  * text; where the paper is silent or garbled the reading taken is stated at the
- * spot (R-numbers match the readings listed in the design notes).
+ * spot, labelled with an R-number.
  */
 #include "toposzp_oracle.h"
 

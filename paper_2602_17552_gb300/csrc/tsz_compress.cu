@@ -396,7 +396,7 @@ __global__ void k_count_regular(uint32_t n, unsigned long long* counts) {
 
 // ============================================================ quantiser setup
 
-// Section II-C with the readings of the design notes: eps from the bound mode;
+// Section II-C, with a quantiser provable in binary32: eps from the bound mode;
 // bins of width w = 2h, h = eps - (M + eps) 2^-21 so the binary32 round trip
 // stays within eps; constant fields are coded exactly.
 __global__ void k_qparams(Ctrl* c, int* status) {
