@@ -111,7 +111,10 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
 
 /* Host.  Parse the first 256 bytes of a stream (a host copy) and report its
  * shape and sizes.  Returns CORRUPT_STREAM if the header is not a valid
- * TopoSZp v1 header. */
+ * TopoSZp v1 header: a field outside the range compression writes, or a
+ * section offset other than the layout its counts give (the same rules the
+ * decompressor applies on the device); UNSUPPORTED if the field has 2^31
+ * points or more. */
 typedef struct {
     int ndim;
     uint64_t dims[3];

@@ -305,8 +305,34 @@ toposzp_status toposzp_inspect(const void* header_host, uint64_t header_bytes, t
     info->dims[2] = u64(32);
     if ((info->ndim != 2 && info->ndim != 3) || !info->dims[0] || !info->dims[1] || !info->dims[2])
         return TOPOSZP_ERR_CORRUPT_STREAM;
+    if (info->ndim == 2 && info->dims[2] != 1) return TOPOSZP_ERR_CORRUPT_STREAM;
+    for (int d = 0; d < 3; d++)
+        if (info->dims[d] >= (1ull << 31)) return TOPOSZP_ERR_UNSUPPORTED;
     info->n = u64(104);
     if (info->n != info->dims[0] * info->dims[1] * info->dims[2]) return TOPOSZP_ERR_CORRUPT_STREAM;
+    if (info->n >= (1ull << 31)) return TOPOSZP_ERR_UNSUPPORTED;
+    // every other field within the range compression writes, and the section
+    // offsets equal to the layout recomputed from the counts (the same rules
+    // as the device-side header check)
+    const uint64_t n = info->n, nb = u64(112), kmin = u64(120), kmax = u64(128);
+    const uint64_t pay = u64(208), rpay = u32(216);
+    const uint32_t flags = u32(40), sweeps = u32(96);
+    const int32_t rk = (int32_t)u32(88);
+    float w_f, h_f;
+    std::memcpy(&w_f, h + 64, 4);
+    std::memcpy(&h_f, h + 72, 4);
+    const bool topo = !(flags & TOPOSZP_NO_TOPO);
+    bool ok = nb == cdiv(n, L) && flags <= 1u && sweeps >= 1u && sweeps <= 16u;
+    ok = ok && (rk == 3 || rk == 5 || rk == 7) && std::isfinite(w_f) && w_f > 0.0f && std::isfinite(h_f) &&
+         h_f >= 0.0f;
+    ok = ok && kmin <= cdiv(n, 2) && kmax <= cdiv(n, 2) && (topo || (kmin == 0 && kmax == 0));
+    ok = ok && pay <= nb * (L + 1) && rpay <= cdiv(kmin + kmax, L) * (L + 1);
+    if (!ok) return TOPOSZP_ERR_CORRUPT_STREAM;
+    Layout lo;
+    make_layout(n, nb, topo, pay, kmin + kmax, rpay, lo);
+    if (lo.end != u64(200) || lo.s1 != u64(152) || lo.s2 != u64(160) || lo.s4 != u64(168) ||
+        lo.s6 != u64(176) || lo.s5 != u64(184) || (topo ? lo.s7 : lo.end) != u64(192))
+        return TOPOSZP_ERR_CORRUPT_STREAM;
     info->total_size = u64(200);
     std::memcpy(&info->eps, h + 56, 8);
     info->flags = u32(40);

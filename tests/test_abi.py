@@ -130,3 +130,33 @@ def test_test_hold_arguments(lib):
     assert lib.toposzp_set_test_hold(-2) == _lib.INVALID_ARG
     assert lib.toposzp_set_test_hold(3) == _lib.OK
     assert lib.toposzp_set_test_hold(-1) == _lib.OK
+
+
+@pytest.mark.parametrize("offset,value", [
+    (40, 2), (96, 0), (96, 17), (64, 0x7F800000), (72, 0xBF800000), (88, 4), (112, 1),
+    (120, 10 ** 6), (160, 0), (192, 7), (200, 1 << 40),
+])
+def test_inspect_refuses_what_the_oracle_refuses(lib, offset, value):
+    """The host header parser holds every field to the range compression writes,
+    like the oracle's decoder: each damaged header is CORRUPT_STREAM for both."""
+    import struct
+    a = np.random.default_rng(2).normal(size=(20, 24)).astype(np.float32)
+    buf = bytearray(oracle.compress(a, 1e-3, rel=True))
+    width = 8 if offset in (112, 120, 160, 192, 200) else 4
+    buf[offset:offset + width] = struct.pack("<Q" if width == 8 else "<I", value)
+    info = _lib.Info()
+    cbuf = ctypes.create_string_buffer(bytes(buf[:256]), 256)
+    assert lib.toposzp_inspect(cbuf, 256, ctypes.byref(info)) == _lib.CORRUPT_STREAM
+    with pytest.raises(oracle.OracleError):
+        oracle.decompress(bytes(buf), a.shape)
+
+
+@pytest.mark.parametrize("shape,opts", [((6, 10, 12), {}), ((33, 65), {"no_topo": True}), ((1, 1), {}),
+                                        ((9, 10, 11), {"rbf_k": 7, "rs_sweeps": 16})])
+def test_inspect_accepts_every_oracle_header(lib, shape, opts):
+    a = np.random.default_rng(4).normal(size=shape).astype(np.float32)
+    buf = oracle.compress(a, 1e-3, rel=True, **opts)
+    info = _lib.Info()
+    cbuf = ctypes.create_string_buffer(buf[:256], 256)
+    assert lib.toposzp_inspect(cbuf, 256, ctypes.byref(info)) == _lib.OK
+    assert info.total_size == len(buf)
