@@ -12,9 +12,12 @@
  * follows Section IV-B: BE^, LZ^+B^, QZ^, MD^ (metadata), CP^+RP^ (extrema
  * stencils), RS^ (RBF saddle refinement).
  *
- * Parity unpinned: the adaptive RBF parameter thresholds (sigma and kernel size
- * from the neighbour variation) are a reading of Section IV-B(3) with constants
- * the paper does not give; the tests pin their stated properties only.
+ * Parity unpinned: two constants of the RS^ reading, which the paper does not
+ * give -- the step limit 0.1 h of eps_RBF, and the neighbour-variation
+ * thresholds that pick sigma and the kernel size (Section IV-B(3)).  The tests
+ * pin their stated properties and direction only; the kernel value, the
+ * neighbourhood, its cut at the boundary and the acceptance rules are pinned
+ * by hand-worked fixtures.
  */
 #ifndef TOPOSZP_ORACLE_H
 #define TOPOSZP_ORACLE_H

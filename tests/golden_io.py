@@ -36,3 +36,12 @@ def grid(rows, dtype):
 
 def ints(s: str):
     return [int(x, 0) for x in s.split()]
+
+
+def field(g: dict) -> np.ndarray:
+    """A fixture's input field as float32: 2D from 'field', 3D from the planes
+    'field_z0', 'field_z1', ..."""
+    if "field" in g:
+        return grid(g["field"], np.float32).astype(np.float32)
+    nz = sum(1 for k in g if k.startswith("field_z"))
+    return np.stack([grid(g[f"field_z{z}"], np.float32) for z in range(nz)]).astype(np.float32)

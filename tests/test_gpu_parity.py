@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import oracle
+from golden_io import field, load
 from paper_2602_17552_gb300 import _lib, codec, synth
 
 pytestmark = pytest.mark.gpu
@@ -256,3 +257,15 @@ def test_parity_every_point_an_extremum(shape):
     a = ((1.0 + rng.random(shape)) * np.where(parity == 0, 1.0, -1.0)).astype(np.float32)
     for eb in (1e-5, 1e-2):
         assert_parity(a, eb, rel=True)
+
+
+@pytest.mark.parametrize("name", ["h4_saddle.txt", "rs_shepard_2d_k5.txt", "rs_shepard_2d_k5_edge.txt",
+                                  "rs_clamp_3d_k3.txt", "rs_reject_new_type_3d.txt"])
+def test_parity_rs_hand_cases(name):
+    """The hand-worked RS^ fixtures (Section IV-B(3)): the kernel value with
+    r = 2, the cut ball at the boundary, the 3D clamp, and the refusal of a
+    correction that would create a new critical point."""
+    g = load(name)
+    k = int(g.get("rbf_k", 3))
+    s = float(g.get("rbf_sigma", 1.0))
+    assert_parity(field(g), float(g["eps"]), rel=False, rbf_k=k, rbf_sigma=s)

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
-from golden_io import grid, ints, load
+from golden_io import field, grid, ints, load
 from paper_2602_17552_gb300 import synth
 
 R, MIN, SAD, MAX = 0, 1, 2, 3
@@ -371,6 +371,87 @@ def test_saddle_refinement_hand_case():
     assert stats[2] == 1
 
 
+def _run_golden(name):
+    g = load(name)
+    a = field(g)
+    p = tuple(int(v) for v in g["p"].split())
+    buf = oracle.compress(a, float(g["eps"]), rel=False, rbf_k=int(g["rbf_k"]),
+                          rbf_sigma=float(g["rbf_sigma"]))
+    h, w, hf = header_q(buf)
+    assert h["rbf_k"] == int(g["rbf_k"]) and np.float32(h["rbf_sigma"]) == np.float32(g["rbf_sigma"])
+    out, d0, d1, stats = oracle.decompress(buf, a.shape, stages=True)
+    return g, a, p, buf, w, hf, out, d0, d1, stats
+
+
+@pytest.mark.parametrize("name", ["rs_shepard_2d_k5.txt", "rs_shepard_2d_k5_edge.txt"])
+def test_saddle_shepard_value_hand_cases(name):
+    """Section IV-B(3): the refined value is the normalised Gaussian kernel
+    sum over N_r(p) minus p, restricted to the grid, with weights
+    exp(-d^2 / 2 sigma^2) by squared distance; the fixtures give its offset
+    from p in bin units, worked by hand.  The clamp does not bind there, so
+    the output value of p is the kernel sum itself."""
+    g, a, p, buf, w, hf, out, d0, d1, stats = _run_golden(name)
+    labels = grid(g["labels"], int)
+    assert (oracle.critical_points(a) == labels).all() and labels[p] == SAD
+    assert (bin_codes(a, buf) == grid(g["bins"], int)).all()
+    assert oracle.critical_points(d0)[p] == R                      # lost by QZ^
+    r = int(g["rbf_k"]) // 2
+    ball = np.sum((np.indices(a.shape) - np.array(p).reshape(-1, 1, 1)) ** 2, axis=0) <= r * r
+    assert (d1[ball] == d0[ball]).all()                            # no stencil inside the ball
+    # binary32 rounding: 12 products and sums of values ~0.13 (each within
+    # 2^-24 relative) plus the final add, over w ~ 0.02: below 5e-6 of w
+    step = (float(out[p]) - float(d0[p])) / float(w)
+    assert abs(step - float(g["step_over_w"])) <= 5e-6, step
+    changed = np.argwhere(out != d1)
+    assert [tuple(c) for c in changed] == [p]
+    assert (oracle.critical_points(out) == labels).all()
+    assert stats[2] == 1
+
+
+def test_saddle_clamp_3d_hand_case():
+    """3D, k_size = 3: the kernel mean lies w/6 below p, the step limit
+    0.1 h binds, and the move down makes p a saddle again (fixture)."""
+    g, a, p, buf, w, hf, out, d0, d1, stats = _run_golden("rs_clamp_3d_k3.txt")
+    lab = oracle.critical_points(a)
+    assert (lab[2] == grid(g["labels_z2"], int)).all() and (lab[1] == R).all()
+    assert (bin_codes(a, buf)[2] == grid(g["bins_z2"], int)).all()
+    assert oracle.critical_points(d0)[p] == R
+    assert out[p] == np.float32(d1[p] - np.float32(np.float32(0.1) * hf))
+    assert [tuple(c) for c in np.argwhere(out != d1)] == [p]
+    assert (oracle.critical_points(out) == lab).all()
+    assert stats[2] == 1
+
+
+def test_saddle_refused_when_a_neighbour_would_change_type():
+    """End of Section IV-B: a correction that would create a critical point
+    absent from the original map is suppressed (fixture): moving p down
+    would make its x+ neighbour n a strict maximum."""
+    g, a, p, buf, w, hf, out, d0, d1, stats = _run_golden("rs_reject_new_type_3d.txt")
+    n = tuple(int(v) for v in g["n"].split())
+    lab = oracle.critical_points(a)
+    assert (lab[2] == grid(g["labels_z2"], int)).all() and lab[n] == R
+    # the candidate of the hand derivation, checked by plain comparisons:
+    v = np.float32(d1[p] - np.float32(np.float32(0.1) * hf))
+    F = d1.copy()
+    F[p] = v
+    z, y, x = p
+    assert F[z, y, x - 1] > v and F[z, y, x + 1] > v          # x pair higher
+    assert F[z, y - 1, x] > v and F[z, y + 1, x] > v          # y pair higher
+    assert F[z - 1, y, x] < v and F[z + 1, y, x] < v          # z pair lower: p a saddle
+    nz, ny, nx = n
+    nb = [F[nz, ny, nx - 1], F[nz, ny, nx + 1], F[nz, ny - 1, nx], F[nz, ny + 1, nx],
+          F[nz - 1, ny, nx], F[nz + 1, ny, nx]]
+    assert all(u < F[n] for u in nb)                          # n a new maximum
+    assert d1[p] == d1[n]                                     # before the move: a tie
+    # refused: p keeps its value and stays lost, nothing else moves
+    assert (out == d1).all()
+    assert stats[2] == 0
+    lo = oracle.critical_points(out)
+    assert lo[p] == R and lo[n] == R
+    e = oracle.topo_errors(lab, lo)
+    assert e[1].sum() == 0 and e[2].sum() == 0
+
+
 @pytest.mark.parametrize("ndim", [2, 3])
 def test_saddle_colouring_is_distance_two(ndim):
     """Within one colour round no two candidates may share a face neighbour, so
@@ -405,6 +486,28 @@ def test_rbf_weights_in_header():
     assert 0.5 <= s <= 1.0 and h["rbf_k"] in (3, 5, 7)
     want = np.array([math.exp(-d2 / (2 * s * s)) for d2 in range(1, 10)], np.float32)
     assert np.allclose(h["g"], want, rtol=1e-6, atol=0)
+
+
+def test_rbf_parameters_grow_with_smoothness():
+    """Section IV-B(3): sigma in [0.5, 1] is larger for smooth data and the
+    kernel size grows when the variation is low.  Along a family from smooth
+    to rough (Gaussian random fields with flatter and flatter spectra, then
+    white noise) neither may grow; a gentle ramp takes the largest kernel and
+    white noise the smallest kernel and sigma.  (The thresholds themselves
+    are this build's choice: the paper gives none.)"""
+    ramp = (np.arange(1024, dtype=np.float64)[None, :] / 1024 +
+            np.arange(64, dtype=np.float64)[:, None] / 640).astype(np.float32)
+    fields = [ramp] + [synth.grf((128, 128), s, 7).numpy() for s in (-8, -4, -3, -2, -1)]
+    fields.append(np.random.default_rng(5).random((128, 128)).astype(np.float32))
+    ks, sig = [], []
+    for a in fields:
+        h = oracle.header(oracle.compress(a, 1e-3, rel=True))
+        ks.append(h["rbf_k"])
+        sig.append(float(np.float32(h["rbf_sigma"])))
+    assert all(x >= y for x, y in zip(ks, ks[1:])), ks
+    assert all(x >= y for x, y in zip(sig, sig[1:])), sig
+    assert ks[0] == 7 and sig[0] > 0.95
+    assert ks[-1] == 3 and sig[-1] == 0.5
 
 
 def _fields_small():
