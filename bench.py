@@ -38,18 +38,25 @@ sys.path.insert(0, ROOT)
 
 NOMINAL_HBM_GBS = 8000.0
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a
-# kernel, per field point, from one ncu capture of the 384^3 case of the same
-# turbulence workload at relative eb 1e-3 (profiles/launches_turb512_rel1e-3.md),
-# scaled to the 512^3 launch by points; reported only for that workload and only
-# while the kernel is unchanged since the capture.
-TRAFFIC_PER_POINT = {"k_decode_fused": (85322496 + 230360832) / 384 ** 3}
+# kernel, per field point, from one ncu capture of a smaller case of the
+# 512^3 turbulence workload at relative eb 1e-3, scaled to the full launch by
+# points.  Each entry carries the SHA-1 of the kernel's source files at the
+# time of the capture: the figure is reported only while they are unchanged
+# (otherwise `traffic` is null).
+TRAFFIC_PER_POINT = {}
+KERNEL_SOURCES = {
+    "k_decode_fused": ("tsz_decompress.cu", "tsz_common.cuh"),
+    "k_saddle_rounds": ("tsz_decompress.cu", "tsz_common.cuh"),
+    "k_encode_field": ("tsz_compress.cu", "tsz_common.cuh"),
+    "k_range_cd": ("tsz_compress.cu", "tsz_common.cuh"),
+}
 E2E_IN_FLIGHT = int(os.environ.get("TOPOSZP_E2E_IN_FLIGHT", "4"))   # round trips in flight at once
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256", "batch", "serve", "tradeoff"])
@@ -93,7 +100,107 @@ def measured_peaks():
         return None
 
 
+def kernel_source_sha1(kernel: str):
+    """SHA-1 over the source files of a kernel (None if unknown)."""
+    import hashlib
+    files = KERNEL_SOURCES.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha1()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2602_17552_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 # ------------------------------------------------------------------ clocks
+
+class NvmlSampler:
+    """SM clock, power and clock-event reasons of one GPU, read through NVML
+    (libnvidia-ml, ctypes) every couple of milliseconds by a thread during the
+    timed region: short regions still get many samples.  Reads only."""
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+               0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, device_index: int, uuid: str = None, period_s: float = 0.002):
+        import threading
+        self.period = period_s
+        self.rows = []
+        self.ok = False
+        self._stop = threading.Event()
+        self._thread = None
+        try:
+            nv = ctypes.CDLL("libnvidia-ml.so.1")
+            if nv.nvmlInit_v2() != 0:
+                return
+            h = ctypes.c_void_p()
+            found = False
+            if uuid:
+                found = nv.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) == 0
+            if not found:
+                found = nv.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(device_index), ctypes.byref(h)) == 0
+            if not found:
+                return
+            self.nv, self.h = nv, h
+            mx = ctypes.c_uint(0)
+            self.max_mhz = float(mx.value) if nv.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0 else None
+            self._reasons = getattr(nv, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                nv.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.ok = True
+        except Exception:
+            self.ok = False
+
+    def _poll(self):
+        clk, pw, rs = ctypes.c_uint(0), ctypes.c_uint(0), ctypes.c_ulonglong(0)
+        while not self._stop.is_set():
+            a = self.nv.nvmlDeviceGetClockInfo(self.h, 1, ctypes.byref(clk))
+            b = self.nv.nvmlDeviceGetPowerUsage(self.h, ctypes.byref(pw))
+            c = self._reasons(self.h, ctypes.byref(rs))
+            if a == 0:
+                self.rows.append((float(clk.value), pw.value / 1e3 if b == 0 else None,
+                                  int(rs.value) if c == 0 else 0))
+            time.sleep(self.period)
+
+    def __enter__(self):
+        import threading
+        if self.ok:
+            self._thread = threading.Thread(target=self._poll, daemon=True)
+            self._thread.start()
+        return self
+
+    def __exit__(self, *exc):
+        if self._thread:
+            self._stop.set()
+            self._thread.join(timeout=2)
+        return False
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [r[0] for r in self.rows]
+        reasons = sorted({name for r in self.rows for bit, name in self.REASONS.items() if r[2] & bit})
+        pw = [r[1] for r in self.rows if r[1] is not None]
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(self.rows), "power_w_max": max(pw) if pw else None, "sampler": "nvml"}
+
+
+def clock_sampler(local: int):
+    """NVML sampler when the library is there, else nvidia-smi at 200 ms."""
+    uuid = None
+    try:
+        import torch
+        u = getattr(torch.cuda.get_device_properties(local), "uuid", None)
+        if u is not None:
+            uuid = "GPU-" + str(u) if not str(u).startswith("GPU-") else str(u)
+    except Exception:
+        uuid = None
+    idx = local
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis and vis.split(",")[0].strip().isdigit():
+        idx = int(vis.split(",")[local].strip()) if local < len(vis.split(",")) else local
+    s = NvmlSampler(idx, uuid)
+    return s if s.ok else ClockSampler(idx)
+
 
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
@@ -292,7 +399,7 @@ def run_ours(args):
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
+    with clock_sampler(local) as clk:
         outer[0].record(stream)
         for s in range(args.steps):
             arr = (ctypes.c_void_p * 9)(*[e.cuda_event for e in ev[s]])
@@ -345,8 +452,10 @@ def run_ours(args):
         kout[name] = d
     dom = max((kname for kname in kout if "alg_bytes" in kout[kname]), key=lambda kk: kout[kk]["ms"])
     traffic = None
-    if dom in TRAFFIC_PER_POINT and topo and args.workload == "turb512" and args.eb == 1e-3 and args.side == 512:
-        traffic = int(TRAFFIC_PER_POINT[dom] * n)
+    tp = TRAFFIC_PER_POINT.get(dom)
+    if (tp and topo and args.workload == "turb512" and args.eb == 1e-3 and args.side == 512
+            and tp["source_sha1"] == kernel_source_sha1(dom)):
+        traffic = int(tp["per_point"] * n)
     roofline = {"kernel": dom, "bound": "hbm", "achieved": kout[dom]["achieved_gbs"], "peak": peak,
                 "unit": "GB/s", "frac": kout[dom]["frac"], "traffic": traffic,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs, burst copy)"}

@@ -269,7 +269,10 @@ toposzp_status toposzp_set_stage_events(void* const* events, int count);
  * access leaves its buffer on that path (every position read from the
  * workspace is checked against n).  tile = -1 (the default) turns it off.
  * The decoder's split form (tuning dec_split = 1) has no waits and ignores it.
- * Process-wide and not thread-safe: for tests only. */
+ * For tests only: the setting is process-wide, so while it is set every
+ * toposzp_decompress of the process (any thread or stream) times out, and
+ * toposzp_batch_decompress refuses to run (INVALID_ARG) rather than capture
+ * the hold into its graph.  Reads and writes of the setting are atomic. */
 toposzp_status toposzp_set_test_hold(int32_t tile);
 
 #ifdef __cplusplus

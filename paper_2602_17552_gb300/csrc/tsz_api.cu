@@ -3,6 +3,7 @@
 // Host side only: argument validation, carving of the caller's workspace, and
 // the launch sequence.  No allocation, no synchronisation, no host reads of
 // device data; every data-dependent size is consumed on the device.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -115,7 +116,9 @@ static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 
 
 static cudaEvent_t g_stage_ev[9];
 static bool g_stage_on = false;
-static int32_t g_test_hold = -1;   // toposzp_set_test_hold: the decode tile never published
+// toposzp_set_test_hold: the decode tile never published (-1: none).  Atomic:
+// any thread's decompress may read it while a test sets it.
+static std::atomic<int32_t> g_test_hold{-1};
 static void stage(int i, cudaStream_t st) {
     if (g_stage_on) cudaEventRecord(g_stage_ev[i], st);
 }
@@ -149,6 +152,8 @@ static toposzp_status noalloc_scratch(void** out) {
     *out = g_noalloc_addr[dev];
     return TOPOSZP_OK;
 }
+
+bool test_hold_active() { return g_test_hold.load() >= 0; }
 
 }  // namespace tsz
 
@@ -281,7 +286,11 @@ toposzp_status toposzp_compress_noalloc(const float* field, int ndim, const uint
                                         void* out, uint64_t out_capacity, uint64_t* out_size,
                                         int32_t* status, toposzp_stream stream) {
     Geo g;
-    if (!dims || !make_geo(ndim, dims, g)) return TOPOSZP_ERR_INVALID_ARG;
+    if (!dims || (ndim != 2 && ndim != 3)) return TOPOSZP_ERR_INVALID_ARG;
+    if (!make_geo(ndim, dims, g)) {   // the same split as toposzp_compress
+        const uint64_t nz = ndim == 3 ? dims[2] : 1;
+        return dims[0] && dims[1] && nz ? TOPOSZP_ERR_UNSUPPORTED : TOPOSZP_ERR_INVALID_ARG;
+    }
     if (g.n > NOALLOC_MAX_POINTS) return TOPOSZP_ERR_UNSUPPORTED;   // larger than the static scratch
     void* scratch = nullptr;
     const toposzp_status st = noalloc_scratch(&scratch);
@@ -360,7 +369,7 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     cudaMemsetAsync(ws, 0, w.tile_w, st);   // control block, rank tile sums, stage flags
     stage(5, st);
-    launch_parse_header(src, in_size, n_out, c, status, (uint32_t)(g_test_hold + 1), st);
+    launch_parse_header(src, in_size, n_out, c, status, (uint32_t)(g_test_hold.load() + 1), st);
     // the rank stream's tile sums and prefixes live in the (no longer used) rank descriptor region
     uint32_t* rtile = reinterpret_cast<uint32_t*>(ws + w.rdesc);
     launch_dec_offsets(src, c, reinterpret_cast<uint32_t*>(ws + w.tile_w), reinterpret_cast<uint32_t*>(ws + w.tile_c),
@@ -414,7 +423,7 @@ toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
 
 toposzp_status toposzp_set_test_hold(int32_t tile) {
     if (tile < -1) return TOPOSZP_ERR_INVALID_ARG;
-    g_test_hold = tile;
+    g_test_hold.store(tile);
     return TOPOSZP_OK;
 }
 

@@ -23,6 +23,10 @@
 
 #include "../../include/toposzp.h"
 
+namespace tsz {
+bool test_hold_active();   // tsz_api.cu: the failure-path test hook is set
+}
+
 namespace {
 
 constexpr uint64_t ALIGN = 256;
@@ -102,6 +106,8 @@ toposzp_status run(Plan* p, bool compress, const void* const* a, void* const* b,
                    uint64_t ws_bytes, int32_t* statuses, cudaStream_t s) {
     if (!p || !a || !b || !ws || !statuses || (compress && !sizes)) return TOPOSZP_ERR_INVALID_ARG;
     if (ws_bytes < p->ws_bytes) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
+    // the test hook would be baked into a captured graph: refuse while it is set
+    if (!compress && tsz::test_hold_active()) return TOPOSZP_ERR_INVALID_ARG;
     const size_t nf = p->f.size();
     for (size_t i = 0; i < nf; i++)
         if (!a[i] || !b[i]) return TOPOSZP_ERR_INVALID_ARG;

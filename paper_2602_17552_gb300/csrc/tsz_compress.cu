@@ -1036,6 +1036,8 @@ __global__ void __launch_bounds__(OS_WARPS * 32) k_os_pass(const uint2* s0, cons
                         set_status(status, ST_TIMEOUT);
                         break;
                     }
+                    // another look-back ran out: stop waiting (polled every 64 polls)
+                    if ((spins & 63u) == 0u && *(volatile int*)status) break;
                     __nanosleep(32);
                 }
                 vd[(size_t)t * nd + d] = OS_INC | (pre + tot);

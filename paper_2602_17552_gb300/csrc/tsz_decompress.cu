@@ -738,7 +738,10 @@ struct CgVal {   // L2-coherent reads of a field other CTAs write during the ker
     __device__ __forceinline__ float operator()(uint32_t j) const { return __ldcg(F + j); }
 };
 
-// Warp 0 waits until stage `k` is complete for every tile below `need`.
+// Warp 0 waits until stage `k` is complete for every tile below `need`.  A
+// wait also ends once the status word is set (polled every 64 fruitless
+// polls): after one wait has run out, or a stage found a damaged stream, the
+// others stop waiting for work that will not come.
 __device__ __forceinline__ void wait_front(Ctrl* c, const uint32_t* flags, int k, uint32_t need,
                                            uint32_t ntiles, int* status) {
     if (threadIdx.x < 32) {
@@ -749,9 +752,14 @@ __device__ __forceinline__ void wait_front(Ctrl* c, const uint32_t* flags, int k
             // one read, broadcast: every branch below must be warp-uniform,
             // since the loop body uses full-warp ballots
             uint32_t f = 0;
-            if (lane == 0) f = *fr;
+            int stv = 0;
+            if (lane == 0) {
+                f = *fr;
+                if ((spins & 63u) == 63u) stv = *(volatile int*)status;
+            }
             f = __shfl_sync(FULL, f, 0);
-            if (f >= need) break;
+            stv = __shfl_sync(FULL, stv, 0);
+            if (f >= need || stv) break;
             const uint32_t j = f + lane;
             const uint32_t v = j < ntiles ? *(volatile const uint32_t*)(flags + j) : 0u;
             const uint32_t done = __ballot_sync(FULL, (v >> k) & 1u);
@@ -1143,7 +1151,8 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
     bool corrupt = false;
     uint32_t restored = 0, skipped = 0;   // per thread: at most the extrema it handled
     while (true) {
-    if (threadIdx.x == 0) s_tile = atomicAdd(&c->tile_fused, 1u);
+    // a set status word ends the call: take no more tiles
+    if (threadIdx.x == 0) s_tile = *(volatile int*)A.status ? total : atomicAdd(&c->tile_fused, 1u);
     __syncthreads();
     const uint32_t t = s_tile;
     __syncthreads();

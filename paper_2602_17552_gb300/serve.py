@@ -151,6 +151,12 @@ class Server:
     def _launch(self, j: Job, stream: torch.cuda.Stream):
         spec = j.req.spec
         j.stream = stream
+        # the job's input, size and status words were written on the current
+        # stream: order the slot stream after them, and tell the caching
+        # allocator that the slot stream uses them
+        stream.wait_stream(torch.cuda.current_stream(self.device))
+        for t in (j.inp, j.size, j.status):
+            t.record_stream(stream)
         off, ln = j.lease
         ws = self.arena.view(off, j.ws_bytes)
         wsa = (j.ws_bytes + ALIGN - 1) // ALIGN * ALIGN

@@ -59,3 +59,27 @@ def test_noalloc_rejects_fields_over_the_limit():
     f = torch.zeros((513, 512), dtype=torch.float32, device="cuda")
     st, _, _ = noalloc_compress(f, 1e-3, "rel")
     assert st == _lib.UNSUPPORTED
+
+
+def test_noalloc_status_split_matches_the_workspace_entry_point():
+    """Nonzero dims too large for this build are UNSUPPORTED, as in
+    toposzp_compress; zero dims or a bad ndim are INVALID_ARG.  The dims are
+    checked on the host before anything touches the (small) buffers."""
+    L = _lib.load()
+    f = torch.zeros(16, dtype=torch.float32, device="cuda")
+    out = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    size = torch.zeros(1, dtype=torch.int64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    p = codec.make_params()
+    stream = int(torch.cuda.current_stream().cuda_stream)
+
+    def call(nd, dims):
+        d = (ctypes.c_uint64 * 3)(*dims)
+        return L.toposzp_compress_noalloc(f.data_ptr(), nd, d, _lib.EB_REL, 1e-3, ctypes.byref(p), out.data_ptr(),
+                                          out.numel(), size.data_ptr(), status.data_ptr(), stream)
+
+    assert call(2, (1 << 31, 1, 1)) == _lib.UNSUPPORTED
+    assert call(3, (1 << 11, 1 << 10, 1 << 10)) == _lib.UNSUPPORTED
+    assert call(2, (0, 5, 1)) == _lib.INVALID_ARG
+    assert call(4, (4, 4, 1)) == _lib.INVALID_ARG
+    torch.cuda.synchronize()
