@@ -291,6 +291,123 @@ __device__ void slice_scan_pairs(uint32_t cnt, const unsigned long long (*sl)[2]
     __syncthreads();   // s_off and s_w are free again
 }
 
+// ---------------------------------------------------- bit-plane transposes
+//
+// A block's fixed-length code (Section II-C, BE) stores w bit planes: plane r
+// holds bit r of value e at bit e.  Values and planes are the rows and
+// columns of a bit matrix, so one turns into the other by a transpose done in
+// registers with the recursive block swap (H. S. Warren, "Hacker's Delight",
+// section 7-3): log2(k) rounds of masked shift-and-xor exchanges, instead of
+// one instruction per bit.  Narrow blocks use four 8x8 (or two 16x16)
+// matrices side by side in the byte (half-word) lanes of the same words: the
+// masks keep the lanes apart.  W, the width that picks the variant, is the
+// same for the whole warp (the branch is uniform); it bounds every block's
+// own width w.
+
+template <int S>
+__device__ __forceinline__ void bt_swap(uint32_t& a, uint32_t& b, uint32_t m) {
+    const uint32_t t = ((a >> S) ^ b) & m;
+    b ^= t;
+    a ^= t << S;
+}
+
+// four independent 8x8 transposes, one per byte lane of x[0..7]
+__device__ __forceinline__ void bt8x4(uint32_t (&x)[8]) {
+#pragma unroll
+    for (int i = 0; i < 4; i++) bt_swap<4>(x[i], x[i + 4], 0x0F0F0F0Fu);
+#pragma unroll
+    for (int i = 0; i < 8; i++)
+        if ((i & 2) == 0) bt_swap<2>(x[i], x[i + 2], 0x33333333u);
+#pragma unroll
+    for (int i = 0; i < 8; i += 2) bt_swap<1>(x[i], x[i + 1], 0x55555555u);
+}
+
+// two independent 16x16 transposes, one per half-word lane of x[0..15]
+__device__ __forceinline__ void bt16x2(uint32_t (&x)[16]) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) bt_swap<8>(x[i], x[i + 8], 0x00FF00FFu);
+#pragma unroll
+    for (int i = 0; i < 16; i++)
+        if ((i & 4) == 0) bt_swap<4>(x[i], x[i + 4], 0x0F0F0F0Fu);
+#pragma unroll
+    for (int i = 0; i < 16; i++)
+        if ((i & 2) == 0) bt_swap<2>(x[i], x[i + 2], 0x33333333u);
+#pragma unroll
+    for (int i = 0; i < 16; i += 2) bt_swap<1>(x[i], x[i + 1], 0x55555555u);
+}
+
+// one 32x32 transpose of x[0..31]
+__device__ __forceinline__ void bt32(uint32_t (&x)[32]) {
+#pragma unroll
+    for (int i = 0; i < 16; i++) bt_swap<16>(x[i], x[i + 16], 0x0000FFFFu);
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        if ((i & 8) == 0) bt_swap<8>(x[i], x[i + 8], 0x00FF00FFu);
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        if ((i & 4) == 0) bt_swap<4>(x[i], x[i + 4], 0x0F0F0F0Fu);
+#pragma unroll
+    for (int i = 0; i < 32; i++)
+        if ((i & 2) == 0) bt_swap<2>(x[i], x[i + 2], 0x33333333u);
+#pragma unroll
+    for (int i = 0; i < 32; i += 2) bt_swap<1>(x[i], x[i + 1], 0x55555555u);
+}
+
+// The 32 magnitudes of a block from its w planes (plane(r), r < w); W >= w.
+template <class Plane>
+__device__ __forceinline__ void planes_to_values(uint32_t W, uint32_t w, const Plane& plane, uint32_t (&v)[32]) {
+    if (W <= 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int r = 0; r < 8; r++) x[r] = (uint32_t)r < w ? plane(r) : 0u;
+        bt8x4(x);
+#pragma unroll
+        for (int e = 0; e < 32; e++) v[e] = (x[e & 7] >> (8 * (e >> 3))) & 0xFFu;
+    } else if (W <= 16) {
+        uint32_t x[16];
+#pragma unroll
+        for (int r = 0; r < 16; r++) x[r] = (uint32_t)r < w ? plane(r) : 0u;
+        bt16x2(x);
+#pragma unroll
+        for (int e = 0; e < 32; e++) v[e] = (x[e & 15] >> (16 * (e >> 4))) & 0xFFFFu;
+    } else {
+#pragma unroll
+        for (int r = 0; r < 32; r++) v[r] = (uint32_t)r < w ? plane(r) : 0u;
+        bt32(v);
+    }
+}
+
+// The w planes of a block from its 32 magnitudes (each below 2^W), handed to
+// put(r, plane) for r < w.
+template <class Put>
+__device__ __forceinline__ void values_to_planes(uint32_t W, uint32_t w, const uint32_t (&m)[32], const Put& put) {
+    if (W <= 8) {
+        uint32_t x[8];
+#pragma unroll
+        for (int i = 0; i < 8; i++) x[i] = m[i] | m[8 + i] << 8 | m[16 + i] << 16 | m[24 + i] << 24;
+        bt8x4(x);
+#pragma unroll
+        for (int r = 0; r < 8; r++)
+            if ((uint32_t)r < w) put(r, x[r]);
+    } else if (W <= 16) {
+        uint32_t x[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) x[i] = m[i] | m[16 + i] << 16;
+        bt16x2(x);
+#pragma unroll
+        for (int r = 0; r < 16; r++)
+            if ((uint32_t)r < w) put(r, x[r]);
+    } else {
+        uint32_t x[32];
+#pragma unroll
+        for (int i = 0; i < 32; i++) x[i] = m[i];
+        bt32(x);
+#pragma unroll
+        for (int r = 0; r < 32; r++)
+            if ((uint32_t)r < w) put(r, x[r]);
+    }
+}
+
 // spread the low 16 bits of x to the even bit positions
 __device__ __forceinline__ uint32_t spread16(uint32_t x) {
     x &= 0xFFFFu;

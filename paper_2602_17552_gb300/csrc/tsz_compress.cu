@@ -536,6 +536,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
         }
     }
     const uint32_t w = 32u - __clz(orr);   // bit length of max |d|
+    const uint32_t W = __reduce_max_sync(FULL, w);   // the warp's widest block: picks the transpose
     const uint32_t words = (b < nb && w) ? 1u + w : 0u;
     uint32_t xmM = 0, xmm = 0;   // extremum masks (bit e: element e), maxima / minima
     if (TOPO) {
@@ -623,12 +624,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
     if (words) {
         uint32_t* dst = s_buf + ow;
         dst[0] = sgn;
-        for (uint32_t p = 0; p < w; p++) {
-            uint32_t wd = 0;
-#pragma unroll
-            for (int e = 0; e < 32; e++) wd |= ((m[e] >> p) & 1u) << e;
-            dst[1 + p] = wd;
-        }
+        values_to_planes(W, w, m, [&](int r, uint32_t pl) { dst[1 + r] = pl; });
     }
     if (b < nb) {
         o.width[b] = (uint8_t)w;
@@ -751,6 +747,7 @@ __global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restri
             }
         }
         const uint32_t w = 32u - __clz(orr);
+        const uint32_t W = __reduce_max_sync(FULL, w);   // the warp's widest block: picks the transpose
         const uint32_t words = (b < nbd && w) ? 1u + w : 0u;
         uint32_t iw = words;
 #pragma unroll
@@ -774,12 +771,7 @@ __global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restri
         if (words) {
             uint32_t* dst = s_buf + ow;
             dst[0] = sgn;
-            for (uint32_t p = 0; p < w; p++) {
-                uint32_t wd = 0;
-#pragma unroll
-                for (int e = 0; e < 32; e++) wd |= ((m[e] >> p) & 1u) << e;
-                dst[1 + p] = wd;
-            }
+            values_to_planes(W, w, m, [&](int r, uint32_t pl) { dst[1 + r] = pl; });
         }
         if (b < nbd) {
             width[b] = (uint8_t)w;

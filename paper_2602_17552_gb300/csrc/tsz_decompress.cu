@@ -185,21 +185,14 @@ __global__ void __launch_bounds__(256, 3) k_decode_ranks(const uint8_t* __restri
         uint32_t woff = iw - words;
         for (uint32_t q = 0; q < warp; q++) woff += s_w[q];
         uint32_t v[32];
-#pragma unroll
-        for (int e = 0; e < 32; e++) v[e] = 0u;
         uint32_t sgn = 0;
-        if (w) {
-            if (woff + 1 + w <= len) {
-                sgn = s_buf[woff];
-                for (uint32_t p = w; p-- > 0;) {
-                    const uint32_t wd = s_buf[woff + 1 + p];
-#pragma unroll
-                    for (int e = 0; e < 32; e++) v[e] = (v[e] << 1) | ((wd >> e) & 1u);
-                }
-            } else {
-                corrupt = true;
-            }
+        uint32_t wv = w;   // planes present (0: constant block or a damaged stream)
+        if (w && woff + 1 + w > len) {
+            corrupt = true;
+            wv = 0;
         }
+        if (wv) sgn = s_buf[woff];
+        planes_to_values(__reduce_max_sync(FULL, wv), wv, [&](int r) { return s_buf[woff + 1 + r]; }, v);
         {
             int32_t q = f;
 #pragma unroll
@@ -886,23 +879,17 @@ __device__ void stage_decode(const FusedArgs& A, const Geo& g, const Layout& lo,
         woff += s_w[k];
         cpl += s_cp[k];
     }
-    // magnitudes from the planes, then signs and the Lorenzo prefix
+    // magnitudes from the planes (a transpose, see planes_to_values), then
+    // signs and the Lorenzo prefix
     uint32_t v[32];
-#pragma unroll
-    for (int e = 0; e < 32; e++) v[e] = 0u;
     uint32_t sgn = 0;
-    if (w) {
-        if (woff + 1 + w <= len) {
-            sgn = s_pay[woff];
-            for (uint32_t p = w; p-- > 0;) {
-                const uint32_t wd = s_pay[woff + 1 + p];
-#pragma unroll
-                for (int e = 0; e < 32; e++) v[e] = (v[e] << 1) | ((wd >> e) & 1u);
-            }
-        } else {
-            corrupt = true;
-        }
+    uint32_t wv = w;   // planes present (0: constant block or a damaged stream)
+    if (w && woff + 1 + w > len) {
+        corrupt = true;
+        wv = 0;
     }
+    if (wv) sgn = s_pay[woff];
+    planes_to_values(__reduce_max_sync(FULL, wv), wv, [&](int r) { return s_pay[woff + 1 + r]; }, v);
     {
         int32_t q = first;
 #pragma unroll
