@@ -170,10 +170,11 @@ class Server:
                                               status=j.status, stream=stream)
         j.done_ev.record(stream)
 
-    def run(self, requests, serial: bool = False, produced: list = None) -> tuple:
+    def run(self, requests, serial: bool = False, produced: list = None, keep=None) -> tuple:
         """Serve `requests` (synth.Request list sorted by arrival).  Returns
         (ServeStats, outputs); outputs[rid] is the compressed stream or decoded
-        field (CPU copy) when keep_outputs is set."""
+        field (CPU copy) when keep_outputs is set, or for the request ids in
+        `keep` when given."""
         jobs = produced if produced is not None else [Job(r, r.spec.shape()) for r in requests]
         for j in jobs:
             j.ws_bytes, j.out_bytes = _sizes(j.shape, j.req.op)
@@ -217,7 +218,7 @@ class Server:
                         raise RuntimeError(f"request {j.req.rid} failed with status {st}")
                     stats.latencies_ms.append(1e3 * (j.t_done - j.req.t_arrive))
                     stats.bytes_total += 4 * int(np.prod(j.shape))
-                    if self.keep_outputs:
+                    if (keep is None and self.keep_outputs) or (keep is not None and j.req.rid in keep):
                         if j.req.op == "compress":
                             outputs[j.req.rid] = j.out[:int(j.size.item())].cpu()
                         else:
@@ -237,6 +238,17 @@ class Server:
         torch.cuda.synchronize(self.device)
         stats.wall_s = clock() - first_arrival
         return stats, outputs
+
+
+def retimed(jobs, rate_hz: float, gaps):
+    """The same requests (and resident inputs) with arrival times from the
+    unit-rate inter-arrival gaps scaled to `rate_hz` (inf: all at once)."""
+    out, t = [], 0.0
+    for j, g in zip(jobs, gaps):
+        t = 0.0 if rate_hz == float("inf") else t + g / rate_hz
+        r = synth.Request(j.req.rid, t, j.req.op, j.req.spec)
+        out.append(Job(r, j.shape, inp=j.inp))
+    return out
 
 
 def plain_result(req: synth.Request, device="cuda"):
