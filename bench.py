@@ -475,7 +475,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": describe(spec), "n": n, "field_bytes": 4 * n, "eb_mode": mode, "eb": args.eb,
                    "topology": topo, "l2": f"inputs larger than L2 (field {4 * n / 1e6:.0f} MB > 129 MB)" if n * 4 > 129e6
-                   else "field fits in L2: no flush between steps", "parallelism": f"replicas x{ws_n}"},
+                   else "field fits in L2: no flush between steps", "parallelism": f"replicas x{ws_n}",
+                   "tuning": _lib.tuning_source},
         "compress_gbs": round(4 * n / (comp_ms * 1e-3) / 1e9, 2),
         "decompress_gbs": round(4 * n / (dec_ms * 1e-3) / 1e9, 2),
         "compress_ms": round(comp_ms, 4), "decompress_ms": round(dec_ms, 4),

@@ -215,6 +215,22 @@ typedef struct {
 } toposzp_tuning;
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
 
+/* Host.  Launch geometry for one size class of fields (no counterpart in the
+ * paper; no effect on any output bit).  Size classes by the number of points
+ * n: 0 for n < 2^16, 1 below 2^20, 2 below 2^24, 3 from 2^24.  Every call
+ * picks the setting of its (ndim, class) when one was given, else the one
+ * of toposzp_set_tuning; a decompression takes the 3D row of its class (the
+ * stream's dimension is read on the device only).  t = NULL clears the
+ * class.  Same value rules as toposzp_set_tuning; process-wide, not
+ * thread-safe. */
+toposzp_status toposzp_set_tuning_class(int ndim, int size_class, const toposzp_tuning* t);
+
+/* Host.  The size class of a field of these dims (-1 if the dims are invalid). */
+int toposzp_tuning_class(int ndim, const uint64_t dims[3]);
+
+/* Host.  The launch geometry a compression of these dims would use. */
+toposzp_status toposzp_get_tuning(int ndim, const uint64_t dims[3], toposzp_tuning* t);
+
 /* ---- Batched form (no counterpart in the paper).  Many uneven fields in one
  * CUDA-graph replay: a plan fixes the fields' shapes, bounds and parameters and
  * spreads them over parallel branch streams (longest first onto the

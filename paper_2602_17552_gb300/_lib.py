@@ -51,6 +51,7 @@ EXPORTS = ("toposzp_default_params", "toposzp_status_string", "toposzp_compress_
            "toposzp_compress",
            "toposzp_inspect", "toposzp_decompress", "toposzp_critical_points", "toposzp_topo_errors",
            "toposzp_set_stage_events", "toposzp_set_test_hold", "toposzp_compress_noalloc", "toposzp_noalloc_max_points", "toposzp_set_tuning",
+           "toposzp_set_tuning_class", "toposzp_tuning_class", "toposzp_get_tuning",
            "toposzp_batch_plan_create", "toposzp_batch_workspace_size", "toposzp_batch_branches",
            "toposzp_batch_compress", "toposzp_batch_decompress", "toposzp_batch_plan_destroy")
 
@@ -96,6 +97,12 @@ def load() -> ctypes.CDLL:
     L.toposzp_compress_noalloc.restype = c_int
     L.toposzp_set_tuning.argtypes = [ctypes.POINTER(Tuning)]
     L.toposzp_set_tuning.restype = c_int
+    L.toposzp_set_tuning_class.argtypes = [c_int, c_int, ctypes.POINTER(Tuning)]
+    L.toposzp_set_tuning_class.restype = c_int
+    L.toposzp_tuning_class.argtypes = [c_int, dims_t]
+    L.toposzp_tuning_class.restype = c_int
+    L.toposzp_get_tuning.argtypes = [c_int, dims_t, ctypes.POINTER(Tuning)]
+    L.toposzp_get_tuning.restype = c_int
     L.toposzp_noalloc_max_points.argtypes = []
     L.toposzp_noalloc_max_points.restype = u64
     L.toposzp_batch_plan_create.argtypes = [c_int, ctypes.POINTER(c_int), ctypes.POINTER(ctypes.c_uint64),
@@ -113,7 +120,40 @@ def load() -> ctypes.CDLL:
     L.toposzp_batch_plan_destroy.argtypes = [vp]
     L.toposzp_batch_plan_destroy.restype = None
     _lib = L
+    apply_tuning_file(L)
     return L
+
+
+# Launch geometry measured by the autotuner on a GB300 (per dimension and size
+# class), committed beside the library and applied when it is loaded.
+# TOPOSZP_TUNING names another file; an empty value keeps the defaults.
+TUNING_FILE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuning_gb300.json")
+tuning_source = "defaults"
+
+
+def tuning_struct(cfg: dict) -> Tuning:
+    keys = ("cd_threads", "cd_blocks_per_sm", "rounds_blocks_per_sm", "dec_slack_tiles", "saddle_records",
+            "dec_split", "rank_bitmap", "cd_columns")
+    return Tuning(*[int(cfg.get(k, 0)) for k in keys])
+
+
+def apply_tuning_file(L, path: str = None) -> str:
+    """Apply the per-class launch geometry of a tuning file (JSON with a
+    "classes" object keyed "2d_0" .. "3d_3"); returns what was applied."""
+    global tuning_source
+    import json
+    path = os.environ.get("TOPOSZP_TUNING", TUNING_FILE) if path is None else path
+    if not path or not os.path.exists(path):
+        return tuning_source
+    with open(path) as f:
+        cfg = json.load(f)
+    for key, c in cfg.get("classes", {}).items():
+        nd, k = int(key[0]), int(key.split("_")[1])
+        st = L.toposzp_set_tuning_class(nd, k, ctypes.byref(tuning_struct(c)))
+        if st:
+            raise TopoSZpError(st, f"toposzp_set_tuning_class {key}")
+    tuning_source = os.path.basename(path)
+    return tuning_source
 
 
 def dims3(ndim: int, dims) -> "ctypes.Array":

@@ -123,6 +123,57 @@ static void stage(int i, cudaStream_t st) {
     if (g_stage_on) cudaEventRecord(g_stage_ev[i], st);
 }
 
+
+// Launch geometry per (ndim, size class), picked at the start of every call:
+// the class's setting when one was given, else the process-wide default.  A
+// decompression takes the 3D row of its class (the field's dimension is
+// known on the device only).
+static Tuning g_default;
+static Tuning g_class[2][4];
+static bool g_class_set[2][4];
+
+static int size_class(uint64_t n) { return n < (1ull << 16) ? 0 : n < (1ull << 20) ? 1 : n < (1ull << 24) ? 2 : 3; }
+
+static void select_tuning(int ndim, uint64_t n) {
+    const int d = ndim == 3 ? 1 : 0, k = size_class(n);
+    g_tuning = g_class_set[d][k] ? g_class[d][k] : g_default;
+}
+
+static bool make_tuning(const toposzp_tuning* t, Tuning& u) {
+    if (t->cd_threads && t->cd_threads != 128 && t->cd_threads != 256 && t->cd_threads != 512) return false;
+    if (t->cd_blocks_per_sm < 0 || t->cd_blocks_per_sm > 32) return false;
+    if (t->rounds_blocks_per_sm != 0 && t->rounds_blocks_per_sm != 1 && t->rounds_blocks_per_sm != 2 &&
+        t->rounds_blocks_per_sm != 4)
+        return false;
+    if (t->dec_slack_tiles < 0 || t->dec_slack_tiles > 65536) return false;
+    if (t->saddle_records < -1 || t->saddle_records > 1) return false;
+    if (t->dec_split < 0 || t->dec_split > 1) return false;
+    if (t->rank_bitmap < -1 || t->rank_bitmap > 1) return false;
+    if (t->cd_columns < -1 || t->cd_columns > 0) return false;
+    u = Tuning();
+    if (t->cd_threads) u.cd_threads = t->cd_threads;
+    if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
+    u.rounds_blocks_per_sm = t->rounds_blocks_per_sm;
+    u.dec_slack_tiles = t->dec_slack_tiles;
+    u.saddle_records = t->saddle_records;
+    u.dec_split = t->dec_split;
+    u.rank_bitmap = t->rank_bitmap;
+    u.cd_columns = t->cd_columns;
+    return true;
+}
+
+static void export_tuning(const Tuning& u, toposzp_tuning* t) {
+    t->cd_threads = u.cd_threads;
+    t->cd_blocks_per_sm = u.cd_blocks_per_sm;
+    t->rounds_blocks_per_sm = u.rounds_blocks_per_sm;
+    t->dec_slack_tiles = u.dec_slack_tiles;
+    t->saddle_records = u.saddle_records;
+    t->dec_split = u.dec_split;
+    t->rank_bitmap = u.rank_bitmap;
+    t->cd_columns = u.cd_columns;
+}
+
+
 // ------------------------------------------------ allocation-free compress
 //
 // Scratch for toposzp_compress_noalloc: a file-scope device array sized for
@@ -235,6 +286,7 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     if (out_capacity < toposzp_compress_bound(ndim, dims)) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
     const CompressWs w = compress_ws(g.n);
     if (ws_bytes < w.end) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
+    select_tuning(ndim, g.n);
 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = reinterpret_cast<uint8_t*>(workspace);
@@ -361,6 +413,7 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
     if (!aligned16(in) || !aligned16(out) || !aligned16(workspace)) return TOPOSZP_ERR_INVALID_ARG;
     const DecompressWs w = decompress_ws(n_out);
     if (ws_bytes < w.end) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
+    select_tuning(3, n_out);   // the 3D row: the dimension is known on the device only
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = reinterpret_cast<uint8_t*>(workspace);
     const uint8_t* src = reinterpret_cast<const uint8_t*>(in);
@@ -395,28 +448,40 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
     return cudaGetLastError() == cudaSuccess ? TOPOSZP_OK : TOPOSZP_ERR_CUDA;
 }
 
+
+toposzp_status toposzp_set_tuning_class(int ndim, int size_class_index, const toposzp_tuning* t) {
+    if ((ndim != 2 && ndim != 3) || size_class_index < 0 || size_class_index > 3) return TOPOSZP_ERR_INVALID_ARG;
+    const int d = ndim == 3 ? 1 : 0;
+    if (!t) {
+        g_class_set[d][size_class_index] = false;
+        return TOPOSZP_OK;
+    }
+    Tuning u;
+    if (!make_tuning(t, u)) return TOPOSZP_ERR_INVALID_ARG;
+    g_class[d][size_class_index] = u;
+    g_class_set[d][size_class_index] = true;
+    return TOPOSZP_OK;
+}
+
+int toposzp_tuning_class(int ndim, const uint64_t dims[3]) {
+    Geo g;
+    if (!make_geo(ndim, dims, g)) return -1;
+    return size_class(g.n);
+}
+
+toposzp_status toposzp_get_tuning(int ndim, const uint64_t dims[3], toposzp_tuning* t) {
+    Geo g;
+    if (!t || !make_geo(ndim, dims, g)) return TOPOSZP_ERR_INVALID_ARG;
+    const int d = ndim == 3 ? 1 : 0, k = size_class(g.n);
+    export_tuning(g_class_set[d][k] ? g_class[d][k] : g_default, t);
+    return TOPOSZP_OK;
+}
+
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t) {
     if (!t) return TOPOSZP_ERR_INVALID_ARG;
-    if (t->cd_threads && t->cd_threads != 128 && t->cd_threads != 256 && t->cd_threads != 512)
-        return TOPOSZP_ERR_INVALID_ARG;
-    if (t->cd_blocks_per_sm < 0 || t->cd_blocks_per_sm > 32) return TOPOSZP_ERR_INVALID_ARG;
-    if (t->rounds_blocks_per_sm != 0 && t->rounds_blocks_per_sm != 1 && t->rounds_blocks_per_sm != 2 &&
-        t->rounds_blocks_per_sm != 4)
-        return TOPOSZP_ERR_INVALID_ARG;
-    if (t->dec_slack_tiles < 0 || t->dec_slack_tiles > 65536) return TOPOSZP_ERR_INVALID_ARG;
-    if (t->saddle_records < -1 || t->saddle_records > 1) return TOPOSZP_ERR_INVALID_ARG;
-    if (t->dec_split < 0 || t->dec_split > 1) return TOPOSZP_ERR_INVALID_ARG;
-    if (t->rank_bitmap < -1 || t->rank_bitmap > 1) return TOPOSZP_ERR_INVALID_ARG;
-    if (t->cd_columns < -1 || t->cd_columns > 0) return TOPOSZP_ERR_INVALID_ARG;
     Tuning u;
-    if (t->cd_threads) u.cd_threads = t->cd_threads;
-    if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
-    u.rounds_blocks_per_sm = t->rounds_blocks_per_sm;
-    u.dec_slack_tiles = t->dec_slack_tiles;
-    u.saddle_records = t->saddle_records;
-    u.dec_split = t->dec_split;
-    u.rank_bitmap = t->rank_bitmap;
-    u.cd_columns = t->cd_columns;
+    if (!make_tuning(t, u)) return TOPOSZP_ERR_INVALID_ARG;
+    g_default = u;
     g_tuning = u;
     return TOPOSZP_OK;
 }

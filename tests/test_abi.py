@@ -160,3 +160,33 @@ def test_inspect_accepts_every_oracle_header(lib, shape, opts):
     cbuf = ctypes.create_string_buffer(buf[:256], 256)
     assert lib.toposzp_inspect(cbuf, 256, ctypes.byref(info)) == _lib.OK
     assert info.total_size == len(buf)
+
+
+def test_tuning_classes_on_host(lib):
+    """Launch geometry per (ndim, size class): the class of a shape, a class
+    setting taking over from the default, clearing it, and refused values."""
+    import ctypes
+    from paper_2602_17552_gb300 import _lib
+    d = lambda *x: (ctypes.c_uint64 * 3)(*(list(x) + [1] * (3 - len(x))))
+    assert [lib.toposzp_tuning_class(2, d(a, b)) for a, b in ((255, 256), (256, 256), (1024, 1024), (4096, 4096))] \
+        == [0, 1, 2, 3]
+    assert lib.toposzp_tuning_class(3, d(0, 4, 4)) == -1
+    t = _lib.Tuning()
+    base = _lib.Tuning()
+    assert lib.toposzp_get_tuning(3, d(128, 128, 128), ctypes.byref(base)) == _lib.OK
+    try:
+        t.cd_threads, t.cd_blocks_per_sm, t.dec_split = 512, 4, 1
+        assert lib.toposzp_set_tuning_class(3, 2, ctypes.byref(t)) == _lib.OK
+        got = _lib.Tuning()
+        assert lib.toposzp_get_tuning(3, d(128, 128, 128), ctypes.byref(got)) == _lib.OK
+        assert (got.cd_threads, got.cd_blocks_per_sm, got.dec_split) == (512, 4, 1)
+        assert lib.toposzp_get_tuning(2, d(2000, 2000), ctypes.byref(got)) == _lib.OK   # the 2D row is untouched
+        assert lib.toposzp_set_tuning_class(3, 2, None) == _lib.OK
+        assert lib.toposzp_get_tuning(3, d(128, 128, 128), ctypes.byref(got)) == _lib.OK
+        assert got.cd_threads != 512 or base.cd_threads == 512
+        t.cd_threads = 100
+        assert lib.toposzp_set_tuning_class(3, 1, ctypes.byref(t)) == _lib.INVALID_ARG
+        assert lib.toposzp_set_tuning_class(4, 1, None) == _lib.INVALID_ARG
+        assert lib.toposzp_set_tuning_class(2, 4, None) == _lib.INVALID_ARG
+    finally:
+        _lib.apply_tuning_file(lib)

@@ -67,7 +67,7 @@ def test_launch_tuning_never_changes_bits():
                 assert torch.equal(got, w)
                 assert torch.equal(codec.decompress(got, tuple(f.shape)), codec.decompress(w, tuple(f.shape)))
     finally:
-        autotune.apply(autotune.DEFAULT)
+        autotune.restore()
 
 
 def test_batch_inside_a_callers_capture():

@@ -217,7 +217,7 @@ def test_parity_rank_paths_narrow_key_span():
             seen[mode] = (int(ctrl[4]), int(ctrl[7]))
             assert got == obuf, f"rank_bitmap={mode}: " + section_report(got, obuf)
     finally:
-        autotune.apply(autotune.DEFAULT)
+        autotune.restore()
     assert seen[0][0] == 1 and seen[0][1] > 0, seen     # bitmaps + bin table
     assert seen[1][0] == 1 and seen[1][1] == 0, seen    # bitmaps, no table
     assert seen[-1][0] == 0, seen                      # radix sort
@@ -245,7 +245,7 @@ def test_parity_saddle_rounds_many_tiles(shape):
             assert np.array_equal(out.view(np.uint32), oout.view(np.uint32)), \
                 (cfg, int(np.count_nonzero(out.view(np.uint32) != oout.view(np.uint32))))
     finally:
-        autotune.apply(autotune.DEFAULT)
+        autotune.restore()
 
 
 @pytest.mark.parametrize("shape", [(33, 65), (9, 10, 11), (100, 300), (20, 30, 40)])
