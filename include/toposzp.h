@@ -56,9 +56,20 @@ typedef enum {
 
 /* flags */
 #define TOPOSZP_NO_TOPO 1u   /* SZp only: no labels, ranks or fix-ups (Fig. 9 baseline) */
+/* RS^ by the literal RBF interpolation of Section IV-B(3), Eqs.
+ * RBF-interp-final and RBF-eval: the refined value at a lost saddle p whose
+ * whole ball N_r(p) lies in the grid is sum_i alpha_i D^(q_i) over
+ * q_i in N_r(p) \ {p}, alpha the weights at p of the Gaussian interpolant with
+ * a constant term (they sum to one), solved in binary64 when the stream is
+ * decoded; the step is not clamped (the acceptance checks alone bound it).
+ * Points whose ball leaves the grid keep the normalised kernel, unclamped.
+ * Without the flag: the normalised kernel with the step clamped to
+ * min(0.1 h, half the smallest nonzero face gap).  Stored in the header; the
+ * decoder follows the stream. */
+#define TOPOSZP_RBF_SOLVE 2u
 
 typedef struct {
-    uint32_t flags;       /* TOPOSZP_NO_TOPO or 0 */
+    uint32_t flags;       /* an OR of TOPOSZP_NO_TOPO and TOPOSZP_RBF_SOLVE; 0: neither */
     uint32_t rs_sweeps;   /* passes over the saddle colour rounds; 0 means 1 */
     int32_t rbf_k;        /* RBF kernel size 3, 5 or 7; 0 = adaptive (Section IV-B(3)) */
     float rbf_sigma;      /* Gaussian width; 0 = adaptive in [0.5, 1] */

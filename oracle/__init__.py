@@ -23,6 +23,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 OK, INVALID_ARG, NONFINITE, EB_TOO_SMALL, BUFFER_TOO_SMALL, CORRUPT = range(6)
 R, MIN, SAD, MAX = 0, 1, 2, 3
 NO_TOPO = 1
+RBF_SOLVE = 2
 
 
 def build(force: bool = False) -> str:
@@ -71,6 +72,9 @@ def lib():
                                 ctypes.c_void_p]
         L.orc_exp_neg.restype = ctypes.c_double
         L.orc_exp_neg.argtypes = [ctypes.c_double]
+        L.orc_rbf_solve.restype = ctypes.c_int
+        L.orc_rbf_solve.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_void_p]
         L.orc_colour.restype = ctypes.c_int
         L.orc_colour.argtypes = [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
                                  ctypes.POINTER(ctypes.c_int)]
@@ -153,6 +157,15 @@ def exp_neg(t: float) -> float:
     return lib().orc_exp_neg(float(t))
 
 
+def rbf_solve(ndim: int, r: int, sigma: float, at=(0, 0, 0)) -> np.ndarray:
+    """Weights of the RBF interpolant with a constant term over N_r(p) minus
+    p, evaluated at offset `at` (x, y, z) from p, in the offset table order
+    ((z, y, x) ascending; binary64)."""
+    out = np.zeros(343, np.float64)
+    m = lib().orc_rbf_solve(ndim, r, float(sigma), int(at[0]), int(at[1]), int(at[2]), out.ctypes.data)
+    return out[:m].copy()
+
+
 def colour(ndim: int, x: int, y: int, z: int = 0):
     nc = ctypes.c_int(0)
     c = lib().orc_colour(ndim, x, y, z, ctypes.byref(nc))
@@ -166,13 +179,14 @@ def compress_bound(shape) -> int:
 
 
 def compress(a, eb: float, rel: bool = True, no_topo: bool = False, rs_sweeps: int = 1,
-             rbf_k: int = 0, rbf_sigma: float = 0.0) -> bytes:
+             rbf_k: int = 0, rbf_sigma: float = 0.0, rbf_solve: bool = False) -> bytes:
     a = _f32(a)
     nd, d3 = _dims3(a)
     cap = int(lib().orc_compress_bound(nd, d3))
     out = np.empty(cap, np.uint8)
     size = ctypes.c_uint64(0)
-    st = lib().orc_compress(a.ctypes.data, nd, d3, int(rel), float(eb), NO_TOPO if no_topo else 0,
+    flags = (NO_TOPO if no_topo else 0) | (RBF_SOLVE if rbf_solve else 0)
+    st = lib().orc_compress(a.ctypes.data, nd, d3, int(rel), float(eb), flags,
                             int(rs_sweeps), int(rbf_k), float(rbf_sigma), out.ctypes.data, cap,
                             ctypes.byref(size))
     if st:

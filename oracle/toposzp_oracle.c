@@ -17,6 +17,7 @@
 #define MAGIC 0x505A5354u          /* "TSZP" little-endian */
 #define VERSION 1u
 #define FLAG_NO_TOPO 1u
+#define FLAG_RBF_SOLVE 2u
 
 /* ------------------------------------------------------------------ helpers */
 
@@ -314,6 +315,77 @@ static void rbf_params(uint64_t sum_abs, uint64_t n, uint64_t nblk, int32_t qmin
     *s_out = sigma;
 }
 
+/* Literal RBF interpolation (Section IV-B(3), Eqs. RBF-interp-final and
+ * RBF-eval): an interpolant through the values at the nodes q_i of
+ * N_r(p) \ {p} (p itself excluded: with p a node, the interpolant would
+ * return p's own value), phi(d) = exp(-d^2 / (2 sigma^2)).  Eq. RBF-eval
+ * states weights that sum to one; the bare Gaussian interpolant's do not
+ * (0.41 - 1.45 over the radii and widths used), so the interpolant carries a
+ * constant term, the polynomial-augmented form of RBF interpolation that
+ * reproduces constants: s(x) = sum_i w_i phi(|x - q_i|) + c with sum_i w_i = 0.
+ * Its value at a point e is alpha^T f with fixed weights alpha for fixed
+ * offsets and sigma.  Phi is symmetric positive definite: a Cholesky
+ * factorisation L L^T (the textbook order: each entry minus the products of
+ * earlier columns, k ascending), forward and back substitution for
+ * a = Phi^-1 phi_e and b = Phi^-1 1, and by elimination of c
+ *     alpha = a + b (1 - sum a) / sum b        (sums i ascending).
+ * Binary64 throughout; exp by orc_exp_neg. */
+int orc_rbf_solve(int ndim, int r, float sigma, int ex, int ey, int ez, double* alpha) {
+    int ox[343], oy[343], oz[343], m = 0;
+    const int rz = ndim == 3 ? r : 0;
+    for (int dz = -rz; dz <= rz; dz++)
+        for (int dy = -r; dy <= r; dy++)
+            for (int dx = -r; dx <= r; dx++) {
+                const int d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 == 0 || d2 > r * r) continue;
+                ox[m] = dx, oy[m] = dy, oz[m] = dz;
+                m++;
+            }
+    const double s = (double)sigma;
+    double* Lm = (double*)malloc((size_t)m * m * sizeof(double));
+    double* y = (double*)malloc((size_t)m * sizeof(double));
+    for (int i = 0; i < m; i++)
+        for (int j = 0; j <= i; j++) {
+            const int a = ox[i] - ox[j], b = oy[i] - oy[j], c = oz[i] - oz[j];
+            Lm[(size_t)i * m + j] = orc_exp_neg((double)(a * a + b * b + c * c) / (2.0 * s * s));
+        }
+    for (int j = 0; j < m; j++) {
+        double d = Lm[(size_t)j * m + j];
+        for (int k = 0; k < j; k++) d = d - Lm[(size_t)j * m + k] * Lm[(size_t)j * m + k];
+        const double ljj = sqrt(d);
+        Lm[(size_t)j * m + j] = ljj;
+        for (int i = j + 1; i < m; i++) {
+            double t = Lm[(size_t)i * m + j];
+            for (int k = 0; k < j; k++) t = t - Lm[(size_t)i * m + k] * Lm[(size_t)j * m + k];
+            Lm[(size_t)i * m + j] = t / ljj;
+        }
+    }
+    double* sol[2] = {alpha, (double*)malloc((size_t)m * sizeof(double))};
+    for (int rhs = 0; rhs < 2; rhs++) {
+        for (int i = 0; i < m; i++) {   /* L y = phi_e, then L y = 1 */
+            const int a = ox[i] - ex, b = oy[i] - ey, c = oz[i] - ez;
+            double t = rhs == 0 ? orc_exp_neg((double)(a * a + b * b + c * c) / (2.0 * s * s)) : 1.0;
+            for (int k = 0; k < i; k++) t = t - Lm[(size_t)i * m + k] * y[k];
+            y[i] = t / Lm[(size_t)i * m + i];
+        }
+        double* x = sol[rhs];
+        for (int i = m - 1; i >= 0; i--) {   /* L^T x = y */
+            double t = y[i];
+            for (int k = m - 1; k > i; k--) t = t - Lm[(size_t)k * m + i] * x[k];
+            x[i] = t / Lm[(size_t)i * m + i];
+        }
+    }
+    double sa = 0.0, sb = 0.0;
+    for (int i = 0; i < m; i++) sa = sa + alpha[i];
+    for (int i = 0; i < m; i++) sb = sb + sol[1][i];
+    const double cf = (1.0 - sa) / sb;
+    for (int i = 0; i < m; i++) alpha[i] = alpha[i] + sol[1][i] * cf;
+    free(sol[1]);
+    free(Lm);
+    free(y);
+    return m;
+}
+
 /* ------------------------------------------------------------ stream layout */
 
 typedef struct {
@@ -416,7 +488,7 @@ int orc_compress(const float* a, int ndim, const uint64_t dims[3], int rel, doub
     put64(h + 16, dims[0]);
     put64(h + 24, dims[1]);
     put64(h + 32, nz);
-    put32(h + 40, flags & FLAG_NO_TOPO);
+    put32(h + 40, flags & (FLAG_NO_TOPO | FLAG_RBF_SOLVE));
     put32(h + 44, (uint32_t)rel);
     putf64(h + 48, eb);
     putf64(h + 56, qp.eps);
@@ -512,6 +584,8 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
     qp.r_f = u2f(get32(in + 68));
     qp.h_f = u2f(get32(in + 72));
     int32_t kk = (int32_t)get32(in + 88);
+    const float sigma = u2f(get32(in + 92));
+    const int solve = (flags & FLAG_RBF_SOLVE) != 0;
     uint32_t sweeps = get32(in + 96);
     uint64_t n = get64(in + 104), nblk = get64(in + 112);
     uint64_t kmin = get64(in + 120), kmax = get64(in + 128);
@@ -525,7 +599,8 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
     /* a header this writer cannot produce marks a damaged stream (R7): every
      * field within the range compression gives it, every section offset equal
      * to the layout recomputed from the counts */
-    if (flags > 1u || sweeps < 1u || sweeps > 16u) return ORC_CORRUPT;
+    if (flags > 3u || sweeps < 1u || sweeps > 16u) return ORC_CORRUPT;
+    if (solve && !(isfinite(sigma) && sigma > 0.0f)) return ORC_CORRUPT;
     if (!(isfinite(qp.w_f) && qp.w_f > 0.0f) || !(isfinite(qp.h_f) && qp.h_f >= 0.0f)) return ORC_CORRUPT;
     if (dims[0] > n_out || dims[1] > n_out || dims[2] > n_out) return ORC_CORRUPT;
     if (kmin > cdiv(n, 2) || kmax > cdiv(n, 2) || (!topo && (kmin || kmax))) return ORC_CORRUPT;
@@ -622,6 +697,13 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
     orc_colour(ndim, 0, 0, 0, &ncol);
     int rz = ndim == 3 ? r : 0;
     upd_t* upd = (upd_t*)malloc((n + 1) * sizeof(upd_t));
+    /* with the literal interpolation: its weights at p, rounded to binary32 */
+    float af[343];
+    if (solve) {
+        double ad[343];
+        const int m = orc_rbf_solve(ndim, r, sigma, 0, 0, 0, ad);
+        for (int e = 0; e < m; e++) af[e] = (float)ad[e];
+    }
     for (uint32_t sw = 0; sw < sweeps; sw++) {
         for (int col = 0; col < ncol; col++) {
             uint64_t nupd = 0;
@@ -647,28 +729,40 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
                     if (g2 > 0.0f && g2 < gmin) gmin = g2;
                 }
                 if (gmin == INFINITY) continue;
-                /* normalised Gaussian kernel over N_r(p) \ {p}, fixed offset order (R14) */
+                /* normalised Gaussian kernel over N_r(p) \ {p}, fixed offset order (R14);
+                 * with the literal interpolation and the ball inside the grid,
+                 * the interpolant's value at p instead: sum alpha_e F(p + o_e) */
+                int ball_in = 1;
+                for (int ax = 0; ax < ndim; ax++)
+                    if (c[ax] < (uint64_t)r || c[ax] + (uint64_t)r >= d3[ax]) ball_in = 0;
                 float num = 0.0f, den = 0.0f;
+                int e = 0;
                 for (int dz = -rz; dz <= rz; dz++)
                     for (int dy = -r; dy <= r; dy++)
                         for (int dx = -r; dx <= r; dx++) {
                             int d2 = dx * dx + dy * dy + dz * dz;
                             if (d2 == 0 || d2 > r * r) continue;
                             int64_t x = (int64_t)c[0] + dx, y = (int64_t)c[1] + dy, z = (int64_t)c[2] + dz;
+                            const int slot = e++;
                             if (x < 0 || y < 0 || z < 0 || x >= (int64_t)dims[0] ||
                                 y >= (int64_t)dims[1] || z >= (int64_t)dims[2]) continue;
-                            float gw = g[d2 - 1];
+                            float gw = (solve && ball_in) ? af[slot] : g[d2 - 1];
                             float fv = F[(uint64_t)x + dims[0] * ((uint64_t)y + dims[1] * (uint64_t)z)];
                             float prod = gw * fv;
                             num = num + prod;
                             den = den + gw;
                         }
-                float u = num / den;
-                float capv = fminf(0.1f * qp.h_f, 0.5f * gmin);
-                float stp = u - Fp;
-                if (stp > capv) stp = capv;
-                if (stp < -capv) stp = -capv;
-                float v = Fp + stp;
+                float u = (solve && ball_in) ? num : num / den;
+                float v;
+                if (solve) {
+                    v = u;   /* the unclamped variant: acceptance alone bounds the step */
+                } else {
+                    float capv = fminf(0.1f * qp.h_f, 0.5f * gmin);
+                    float stp = u - Fp;
+                    if (stp > capv) stp = capv;
+                    if (stp < -capv) stp = -capv;
+                    v = Fp + stp;
+                }
                 if (v == Fp) continue;
                 /* acceptance: p becomes a saddle; no neighbour changes type except to
                  * its own original label (no new FP/FT, Section IV-B end); bound kept */

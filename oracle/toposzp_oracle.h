@@ -51,11 +51,16 @@ void orc_critical_points(const float* a, int ndim, const uint64_t dims[3], uint8
 uint64_t orc_ranks(const float* a, const uint8_t* labels, uint64_t n, const orc_qparams* p,
                    int32_t* delta_seq);
 double orc_exp_neg(double t);                                    /* exp(-t), t >= 0 */
+/* Weights of the Gaussian RBF interpolant over the offsets of N_r(p) \ {p}
+ * (table order: z, then y, then x ascending), evaluated at offset (ex, ey, ez)
+ * from p: alpha = Phi^-1 phi, in binary64.  Returns the number of offsets. */
+int orc_rbf_solve(int ndim, int r, float sigma, int ex, int ey, int ez, double* alpha);
 int orc_colour(int ndim, uint64_t x, uint64_t y, uint64_t z, int* ncol);   /* RS^ rounds */
 
 /* --- whole pipeline --- */
 uint64_t orc_compress_bound(int ndim, const uint64_t dims[3]);
-/* rel: 0 absolute eb, 1 eb * (max - min).  flags bit0: no topology (SZp only).
+/* rel: 0 absolute eb, 1 eb * (max - min).  flags bit0: no topology (SZp only);
+ * bit1: RS^ by the literal RBF interpolation, unclamped (see orc_decompress).
  * rbf_k / rbf_sigma: 0 = adaptive.  Returns a status; *out_size on success. */
 int orc_compress(const float* a, int ndim, const uint64_t dims[3], int rel, double eb,
                  uint32_t flags, uint32_t rs_sweeps, int32_t rbf_k, float rbf_sigma,

@@ -19,6 +19,7 @@ STATUS = {
 OK, INVALID_ARG, NONFINITE, EB_TOO_SMALL, BUFFER_TOO_SMALL, CORRUPT_STREAM, TIMEOUT, CUDA, UNSUPPORTED = range(9)
 EB_ABS, EB_REL = 0, 1
 NO_TOPO = 1
+RBF_SOLVE = 2
 
 
 class TopoSZpError(RuntimeError):

@@ -16,7 +16,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import EB_ABS, EB_REL, NO_TOPO, TopoSZpError
+from ._lib import EB_ABS, EB_REL, NO_TOPO, RBF_SOLVE, TopoSZpError
 
 _WS = {}   # (device, kind) -> cached workspace tensor (grown on demand)
 
@@ -61,10 +61,10 @@ def workspace(kind: str, nbytes: int, device) -> torch.Tensor:
     return buf
 
 
-def make_params(no_topo=False, rs_sweeps=1, rbf_k=0, rbf_sigma=0.0) -> _lib.Params:
+def make_params(no_topo=False, rs_sweeps=1, rbf_k=0, rbf_sigma=0.0, rbf_solve=False) -> _lib.Params:
     p = _lib.Params()
     _lib.load().toposzp_default_params(ctypes.byref(p))
-    p.flags = NO_TOPO if no_topo else 0
+    p.flags = (NO_TOPO if no_topo else 0) | (RBF_SOLVE if rbf_solve else 0)
     p.rs_sweeps = int(rs_sweeps)
     p.rbf_k = int(rbf_k)
     p.rbf_sigma = float(rbf_sigma)
@@ -116,10 +116,12 @@ def compress_async(field: torch.Tensor, eb: float, mode: str = "rel", *, params=
 
 
 def compress(field: torch.Tensor, eb: float, mode: str = "rel", *, no_topo=False, rs_sweeps=1, rbf_k=0,
-             rbf_sigma=0.0, stream=None) -> torch.Tensor:
+             rbf_sigma=0.0, rbf_solve=False, stream=None) -> torch.Tensor:
     """Compress and return the stream as a uint8 CUDA tensor of its exact length
-    (synchronises ``stream`` to read the length and the device status)."""
-    call = compress_async(field, eb, mode, params=make_params(no_topo, rs_sweeps, rbf_k, rbf_sigma),
+    (synchronises ``stream`` to read the length and the device status).
+    ``rbf_solve`` selects the literal RBF interpolation for the decoder's
+    saddle refinement (stored in the stream's header)."""
+    call = compress_async(field, eb, mode, params=make_params(no_topo, rs_sweeps, rbf_k, rbf_sigma, rbf_solve),
                           stream=stream)
     (torch.cuda.current_stream() if stream is None else stream).synchronize()
     _check(int(call.status.item()), "toposzp_compress (device)")
@@ -202,8 +204,8 @@ def topo_errors(labels_a: torch.Tensor, labels_b: torch.Tensor, n: int, *, strea
     return out.view(3, 4)
 
 
-def tradeoff(field: torch.Tensor, eb: float, mode: str = "rel", *, no_topo=False, labels=None,
-             stream=None) -> dict:
+def tradeoff(field: torch.Tensor, eb: float, mode: str = "rel", *, no_topo=False, rbf_solve=False,
+             labels=None, stream=None) -> dict:
     """One point of the bit-rate / topology-error trade-off (Section III-B,
     Table II): compress and decompress ``field`` and count the false
     negatives, false positives and false types of the decompressed field's
@@ -215,7 +217,7 @@ def tradeoff(field: torch.Tensor, eb: float, mode: str = "rel", *, no_topo=False
     n = field.numel()
     if labels is None:
         labels, _ = critical_points(field, counts=False, stream=stream)
-    buf = compress(field, eb, mode, no_topo=no_topo, stream=stream)
+    buf = compress(field, eb, mode, no_topo=no_topo, rbf_solve=rbf_solve, stream=stream)
     info = inspect(buf)
     dec = decompress(buf, tuple(field.shape), stream=stream)
     lab_d, _ = critical_points(dec, counts=False, stream=stream)

@@ -279,7 +279,7 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     if (!aligned16(field) || !aligned16(out) || !aligned16(workspace)) return TOPOSZP_ERR_INVALID_ARG;
     if (mode != TOPOSZP_EB_ABS && mode != TOPOSZP_EB_REL) return TOPOSZP_ERR_INVALID_ARG;
     if (!(eb > 0.0) || !std::isfinite(eb)) return TOPOSZP_ERR_INVALID_ARG;
-    if (p.flags & ~TOPOSZP_NO_TOPO) return TOPOSZP_ERR_INVALID_ARG;
+    if (p.flags & ~(TOPOSZP_NO_TOPO | TOPOSZP_RBF_SOLVE)) return TOPOSZP_ERR_INVALID_ARG;
     if (p.rs_sweeps > 16) return TOPOSZP_ERR_INVALID_ARG;
     if (p.rbf_k != 0 && p.rbf_k != 3 && p.rbf_k != 5 && p.rbf_k != 7) return TOPOSZP_ERR_INVALID_ARG;
     if (!(p.rbf_sigma >= 0.0f) || !std::isfinite(p.rbf_sigma)) return TOPOSZP_ERR_INVALID_ARG;
@@ -383,7 +383,10 @@ toposzp_status toposzp_inspect(const void* header_host, uint64_t header_bytes, t
     std::memcpy(&w_f, h + 64, 4);
     std::memcpy(&h_f, h + 72, 4);
     const bool topo = !(flags & TOPOSZP_NO_TOPO);
-    bool ok = nb == cdiv(n, L) && flags <= 1u && sweeps >= 1u && sweeps <= 16u;
+    float sigma;
+    std::memcpy(&sigma, h + 92, 4);
+    bool ok = nb == cdiv(n, L) && flags <= (TOPOSZP_NO_TOPO | TOPOSZP_RBF_SOLVE) && sweeps >= 1u && sweeps <= 16u;
+    ok = ok && (!(flags & TOPOSZP_RBF_SOLVE) || (std::isfinite(sigma) && sigma > 0.0f));
     ok = ok && (rk == 3 || rk == 5 || rk == 7) && std::isfinite(w_f) && w_f > 0.0f && std::isfinite(h_f) &&
          h_f >= 0.0f;
     ok = ok && kmin <= cdiv(n, 2) && kmax <= cdiv(n, 2) && (topo || (kmin == 0 && kmax == 0));

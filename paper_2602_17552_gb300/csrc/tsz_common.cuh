@@ -15,6 +15,8 @@ constexpr uint32_t HDR = 256;            // stream header bytes
 constexpr uint32_t MAGIC = 0x505A5354u;  // "TSZP"
 constexpr uint32_t VERSION = 1;
 constexpr uint32_t FLAG_NO_TOPO = 1;
+constexpr uint32_t FLAG_RBF_SOLVE = 2;   // RS^ by the literal interpolant's weights, unclamped
+constexpr int RBF_MAX_NODES = 122;       // |N_r(p) \ {p}| for r = 3 in 3D
 
 // labels of Section IV-A(1): r = 00, m = 01, s = 10, M = 11
 constexpr int LAB_R = 0, LAB_MIN = 1, LAB_SAD = 2, LAB_MAX = 3;
@@ -141,6 +143,7 @@ struct Ctrl {
     unsigned int sad_next[8];               // work counters of the rounds' evaluation
     Layout lo;
     float g_rbf[9];
+    float rbf_alpha[RBF_MAX_NODES];   // FLAG_RBF_SOLVE: the interpolant's weights at p, table order
 };
 
 // ------------------------------------------------------------------ helpers

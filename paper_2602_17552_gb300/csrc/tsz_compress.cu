@@ -1286,7 +1286,7 @@ __global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rb
     put<uint64_t>(h, 16, g.nx);
     put<uint64_t>(h, 24, g.ny);
     put<uint64_t>(h, 32, g.nz);
-    put<uint32_t>(h, 40, c->flags & FLAG_NO_TOPO);
+    put<uint32_t>(h, 40, c->flags & (FLAG_NO_TOPO | FLAG_RBF_SOLVE));
     put<uint32_t>(h, 44, (uint32_t)c->rel);
     put<double>(h, 48, c->eb);
     put<double>(h, 56, c->eps);

@@ -1,7 +1,9 @@
 // tsz_decompress.cu -- decompression kernels (Section IV-B of arXiv 2602.17552).
 //
 //   k_parse_header   one thread: validate the stream header against the call
-//                    and the buffer size, fill the control block
+//                    and the buffer size, fill the control block; with the
+//                    literal-interpolation flag the CTA then solves for the
+//                    RBF weights
 //   k_dec_tile_*     offset pre-pass: per 8192-point tile, payload words and
 //                    extremum counts -> exclusive prefixes (MD^ bookkeeping)
 //   k_decode_ranks   the inverse codec on the rank stream (delta sequence)
@@ -43,9 +45,8 @@ __device__ __forceinline__ T get(const uint8_t* h, int off) {
     return *reinterpret_cast<const T*>(h + off);
 }
 
-__global__ void k_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c,
-                               int* status, uint32_t test_hold) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+__device__ void parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c, int* status,
+                             uint32_t test_hold) {
     if (in_size < HDR || get<uint32_t>(in, 0) != MAGIC || get<uint32_t>(in, 4) != VERSION ||
         get<uint32_t>(in, 12) != L) {
         set_status(status, ST_CORRUPT);
@@ -55,7 +56,8 @@ __global__ void k_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_o
     const uint64_t nx = get<uint64_t>(in, 16), ny = get<uint64_t>(in, 24), nz = get<uint64_t>(in, 32);
     const uint32_t flags = get<uint32_t>(in, 40);
     bool ok = (ndim == 2 || ndim == 3) && nx >= 1 && ny >= 1 && nz >= 1 && nx < (1ull << 31) &&
-              ny < (1ull << 31) && nz < (1ull << 31) && (ndim == 3 || nz == 1) && flags <= 1;
+              ny < (1ull << 31) && nz < (1ull << 31) && (ndim == 3 || nz == 1) &&
+              flags <= (FLAG_NO_TOPO | FLAG_RBF_SOLVE);
     const uint64_t n = ok ? nx * ny : 0;
     ok = ok && n < (1ull << 31) && n * nz < (1ull << 31) && n * nz == n_out &&
          get<uint64_t>(in, 104) == n_out && get<uint64_t>(in, 112) == cdiv(n_out, L);
@@ -64,8 +66,10 @@ __global__ void k_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_o
     const uint32_t sweeps = get<uint32_t>(in, 96);
     const uint64_t kmin = get<uint64_t>(in, 120), kmax = get<uint64_t>(in, 128);
     const uint64_t pay = get<uint64_t>(in, 208), rpay = get<uint32_t>(in, 216);
+    const float sigma = get<float>(in, 92);
     const bool topo = !(flags & FLAG_NO_TOPO);
     ok = ok && isfinite(w_f) && w_f > 0.0f && isfinite(h_f) && h_f >= 0.0f;
+    ok = ok && (!(flags & FLAG_RBF_SOLVE) || (isfinite(sigma) && sigma > 0.0f));
     ok = ok && (rk == 3 || rk == 5 || rk == 7) && sweeps >= 1 && sweeps <= 16;
     ok = ok && kmin <= cdiv(n_out, 2) && kmax <= cdiv(n_out, 2) && (topo || (kmin == 0 && kmax == 0));
     const uint64_t nb = cdiv(n_out, L);
@@ -97,6 +101,7 @@ __global__ void k_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_o
     c->w_f = w_f;
     c->h_f = h_f;
     c->rbf_k = rk;
+    c->rbf_sigma = sigma;
     c->rs_sweeps = (int)sweeps;
     c->pay_words = pay;
     c->rank_words = rpay;
@@ -104,6 +109,111 @@ __global__ void k_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_o
     c->lo = lo;
     c->test_hold = test_hold;
     for (int i = 0; i < 9; i++) c->g_rbf[i] = get<float>(in, 220 + 4 * i);
+}
+
+// Weights of the literal RBF interpolation (Section IV-B(3), Eqs.
+// RBF-interp-final and RBF-eval) at p for the nodes q_i of N_r(p) \ {p} in
+// (z, y, x) table order: the Gaussian interpolant with a constant term,
+// s(x) = sum_i w_i phi(|x - q_i|) + c with sum_i w_i = 0, which reproduces
+// constants, so the weights sum to one as Eq. RBF-eval states.  With
+// a = Phi^-1 phi_p and b = Phi^-1 1 the weights are a + b (1 - sum a) / sum b.
+// One CTA, binary64 without contraction.  Phi = L L^T by right-looking
+// Cholesky: column j is finished (square root, division), then the trailing
+// triangle loses column j's products, so every entry sees its subtractions
+// in ascending column order -- the operations and their order of the
+// textbook column-by-column factorisation.  Substitutions the same way
+// (forward: ascending, back: descending).  Phi's entries depend on the
+// squared node distance only (0 .. 4 r^2): one exp per distinct distance.
+__device__ void rbf_solve_block(int ndim, int r, float sigma, float* alpha, double* sm) {
+    __shared__ int s_d2[RBF_MAX_NODES], s_x[RBF_MAX_NODES], s_y[RBF_MAX_NODES], s_z[RBF_MAX_NODES];
+    __shared__ double s_phi[37];
+    __shared__ int s_m;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        const int rz = ndim == 3 ? r : 0;
+        int m = 0;
+        for (int dz = -rz; dz <= rz; dz++)
+            for (int dy = -r; dy <= r; dy++)
+                for (int dx = -r; dx <= r; dx++) {
+                    const int d2 = dx * dx + dy * dy + dz * dz;
+                    if (d2 == 0 || d2 > r * r) continue;
+                    s_x[m] = dx, s_y[m] = dy, s_z[m] = dz, s_d2[m] = d2;
+                    m++;
+                }
+        s_m = m;
+    }
+    const double s = (double)sigma;
+    const double s2 = __dmul_rn(__dmul_rn(2.0, s), s);
+    for (int d = tid; d <= 4 * r * r; d += nt) s_phi[d] = exp_neg(__ddiv_rn((double)d, s2));
+    __syncthreads();
+    const int m = s_m;
+    double* A = sm;            // m x m row-major; the lower triangle holds Phi, then L
+    double* X = sm + m * m;    // two right-hand sides (phi_p, ones), then the solutions
+    for (int idx = tid; idx < m * m; idx += nt) {
+        const int i = idx / m, j = idx - i * m;
+        if (j > i) continue;
+        const int a = s_x[i] - s_x[j], b = s_y[i] - s_y[j], cz = s_z[i] - s_z[j];
+        A[idx] = s_phi[a * a + b * b + cz * cz];
+    }
+    for (int i = tid; i < m; i += nt) {
+        X[i] = s_phi[s_d2[i]];
+        X[m + i] = 1.0;
+    }
+    __syncthreads();
+    for (int j = 0; j < m; j++) {
+        if (tid == 0) A[j * m + j] = __dsqrt_rn(A[j * m + j]);
+        __syncthreads();
+        for (int i = j + 1 + tid; i < m; i += nt) A[i * m + j] = __ddiv_rn(A[i * m + j], A[j * m + j]);
+        __syncthreads();
+        const int t = m - 1 - j;
+        for (int idx = tid; idx < t * t; idx += nt) {
+            const int i = j + 1 + idx / t, k = j + 1 + idx % t;
+            if (k > i) continue;
+            A[i * m + k] = __dsub_rn(A[i * m + k], __dmul_rn(A[i * m + j], A[k * m + j]));
+        }
+        __syncthreads();
+    }
+    for (int i = 0; i < m; i++) {   // L y = rhs
+        if (tid < 2) X[tid * m + i] = __ddiv_rn(X[tid * m + i], A[i * m + i]);
+        __syncthreads();
+        const int t = m - 1 - i;
+        for (int idx = tid; idx < 2 * t; idx += nt) {
+            const int h = idx / t, i2 = i + 1 + idx % t;
+            X[h * m + i2] = __dsub_rn(X[h * m + i2], __dmul_rn(A[i2 * m + i], X[h * m + i]));
+        }
+        __syncthreads();
+    }
+    for (int i = m - 1; i >= 0; i--) {   // L^T x = y
+        if (tid < 2) X[tid * m + i] = __ddiv_rn(X[tid * m + i], A[i * m + i]);
+        __syncthreads();
+        for (int idx = tid; idx < 2 * i; idx += nt) {
+            const int h = idx / i, i2 = idx % i;
+            X[h * m + i2] = __dsub_rn(X[h * m + i2], __dmul_rn(A[i * m + i2], X[h * m + i]));
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double sa = 0.0, sb = 0.0;
+        for (int i = 0; i < m; i++) sa = __dadd_rn(sa, X[i]);
+        for (int i = 0; i < m; i++) sb = __dadd_rn(sb, X[m + i]);
+        const double cf = __ddiv_rn(__dsub_rn(1.0, sa), sb);
+        for (int i = 0; i < m; i++) alpha[i] = __double2float_rn(__dadd_rn(X[i], __dmul_rn(X[m + i], cf)));
+    }
+}
+
+// bytes of dynamic shared memory rbf_solve_block() takes at most
+constexpr int RBF_SOLVE_SMEM = (RBF_MAX_NODES * RBF_MAX_NODES + 2 * RBF_MAX_NODES) * 8;
+
+__global__ void __launch_bounds__(256) k_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out,
+                                                      Ctrl* c, int* status, uint32_t test_hold) {
+    extern __shared__ double sm_solve[];
+    __shared__ int s_solve;
+    if (threadIdx.x == 0) {
+        parse_header(in, in_size, n_out, c, status, test_hold);
+        s_solve = *status == 0 && (c->flags & (FLAG_NO_TOPO | FLAG_RBF_SOLVE)) == FLAG_RBF_SOLVE;
+    }
+    __syncthreads();
+    if (s_solve) rbf_solve_block(c->g.ndim, c->rbf_k / 2, c->rbf_sigma, c->rbf_alpha, sm_solve);
 }
 
 // --------------------------------------------------------------- inverse codec
@@ -336,16 +446,24 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
         if (gi > 0.0f && gi < gmin) gmin = gi;
     }
     if (isinf(gmin)) return false;
+    const bool solve = c->flags & FLAG_RBF_SOLVE;
     // Exact shortcut: |v - Fp| <= gmin / 2 keeps every distinct neighbour on its
     // side, so p's type with v depends only on the direction of the move; if
-    // neither direction gives a saddle, check (a) below rejects every v.
-    if (!saddle_feasible(nb, g.ndim, Fp)) return false;
-    // normalised Gaussian kernel over N_r(p) \ {p}, fixed (z, y, x) order
+    // neither direction gives a saddle, check (a) below rejects every v.  (The
+    // unclamped literal interpolation can step further: no shortcut there.)
+    if (!solve && !saddle_feasible(nb, g.ndim, Fp)) return false;
+    // normalised Gaussian kernel over N_r(p) \ {p}, fixed (z, y, x) order; with
+    // the literal interpolation and the ball inside the grid, the
+    // interpolant's value at p instead: sum alpha_e F(p + o_e)
     const int r = c->rbf_k / 2;
     const bool inside = x >= (uint32_t)r && x + r < g.nx && y >= (uint32_t)r && y + r < g.ny &&
                         (g.ndim == 2 || (z >= (uint32_t)r && z + r < g.nz));
     float num = 0.0f, den;
-    if (inside) {
+    if (inside && solve) {
+#pragma unroll 8
+        for (int e = 0; e < T.n; e++) num = __fadd_rn(num, __fmul_rn(c->rbf_alpha[e], F[(int)p + T.lin[e]]));
+        den = 1.0f;
+    } else if (inside) {
 #pragma unroll 8
         for (int e = 0; e < T.n; e++) num = __fadd_rn(num, __fmul_rn(c->g_rbf[T.d2[e] - 1], F[(int)p + T.lin[e]]));
         den = T.den_full;
@@ -359,12 +477,15 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
             den = __fadd_rn(den, gw);
         }
     }
-    const float u = __fdiv_rn(num, den);
-    const float capv = fminf(__fmul_rn(0.1f, c->h_f), __fmul_rn(0.5f, gmin));
-    float stp = __fsub_rn(u, Fp);
-    if (stp > capv) stp = capv;
-    if (stp < -capv) stp = -capv;
-    const float v = __fadd_rn(Fp, stp);
+    const float u = inside && solve ? num : __fdiv_rn(num, den);
+    float v = u;   // the literal interpolation: unclamped, acceptance alone bounds the step
+    if (!solve) {
+        const float capv = fminf(__fmul_rn(0.1f, c->h_f), __fmul_rn(0.5f, gmin));
+        float stp = __fsub_rn(u, Fp);
+        if (stp > capv) stp = capv;
+        if (stp < -capv) stp = -capv;
+        v = __fadd_rn(Fp, stp);
+    }
     if (v == Fp) return false;
     GlobalVal val{F};
     OverrideVal nv{F, p, v};
@@ -535,16 +656,23 @@ __device__ bool saddle_candidate_rec(const float* F, const uint32_t* labels, con
         if (gi > 0.0f && gi < gmin) gmin = gi;
     }
     if (isinf(gmin)) return false;
-    if (!saddle_feasible(nb, ND, Fp)) return false;
-    float num = 0.0f;
+    const bool solve = c->flags & FLAG_RBF_SOLVE;
+    if (!solve && !saddle_feasible(nb, ND, Fp)) return false;
+    float num = 0.0f, vn;
+    if (solve) {
 #pragma unroll
-    for (int e = 0; e < S.ns; e++) num = __fadd_rn(num, __fmul_rn(c->g_rbf[S.d2[e] - 1], v[e]));
-    const float u = __fdiv_rn(num, den_full);
-    const float capv = fminf(__fmul_rn(0.1f, c->h_f), __fmul_rn(0.5f, gmin));
-    float stp = __fsub_rn(u, Fp);
-    if (stp > capv) stp = capv;
-    if (stp < -capv) stp = -capv;
-    const float vn = __fadd_rn(Fp, stp);
+        for (int e = 0; e < S.ns; e++) num = __fadd_rn(num, __fmul_rn(c->rbf_alpha[e], v[e]));
+        vn = num;
+    } else {
+#pragma unroll
+        for (int e = 0; e < S.ns; e++) num = __fadd_rn(num, __fmul_rn(c->g_rbf[S.d2[e] - 1], v[e]));
+        const float u = __fdiv_rn(num, den_full);
+        const float capv = fminf(__fmul_rn(0.1f, c->h_f), __fmul_rn(0.5f, gmin));
+        float stp = __fsub_rn(u, Fp);
+        if (stp > capv) stp = capv;
+        if (stp < -capv) stp = -capv;
+        vn = __fadd_rn(Fp, stp);
+    }
     if (vn == Fp) return false;
     if (cls_vals<ND>(vn, nb) != LAB_SAD) return false;   // (a)
     const uint32_t st[3] = {1u, g.nx, g.nxy};
@@ -1054,6 +1182,7 @@ __device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* 
     const uint32_t ns = s_cnt;
     CgVal val{A.out};
     const uint32_t st[3] = {1u, g.nx, g.nxy};
+    const bool solve = A.c->flags & FLAG_RBF_SOLVE;   // no small-move filter: the step is unclamped
     for (uint32_t k0 = 0; k0 < ns; k0 += blockDim.x) {
         const uint32_t k = k0 + threadIdx.x;
         bool keep = false;
@@ -1089,7 +1218,7 @@ __device__ void stage_saddles(const FusedArgs& A, const Geo& g, const uint32_t* 
                 // rounds (none of them is saddle-labelled) keeps its status for
                 // good: if no small move of p can make it a saddle now, every
                 // colour round would reject it, so it is not listed.
-                keep = lost && (nbsad || saddle_feasible(nb, nd, fp));
+                keep = lost && (nbsad || solve || saddle_feasible(nb, nd, fp));
             }
         }
         const uint32_t bal = __ballot_sync(FULL, keep);
@@ -1335,7 +1464,14 @@ __global__ void __launch_bounds__(1024, 1) k_saddle_rounds(const uint8_t* __rest
 
 void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c, int* status,
                          uint32_t test_hold, cudaStream_t st) {
-    k_parse_header<<<1, 32, 0, st>>>(in, in_size, n_out, c, status, test_hold);
+    static bool attr_set[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !attr_set[dev]) {
+        cudaFuncSetAttribute(k_parse_header, cudaFuncAttributeMaxDynamicSharedMemorySize, RBF_SOLVE_SMEM);
+        if (dev >= 0 && dev < 64) attr_set[dev] = true;
+    }
+    k_parse_header<<<1, 256, RBF_SOLVE_SMEM, st>>>(in, in_size, n_out, c, status, test_hold);
 }
 
 void launch_decode_ranks(const uint8_t* in, Ctrl* c, const uint32_t* rpre, int32_t* delta, uint64_t max_k,

@@ -133,7 +133,7 @@ def test_test_hold_arguments(lib):
 
 
 @pytest.mark.parametrize("offset,value", [
-    (40, 2), (96, 0), (96, 17), (64, 0x7F800000), (72, 0xBF800000), (88, 4), (112, 1),
+    (40, 4), (96, 0), (96, 17), (64, 0x7F800000), (72, 0xBF800000), (88, 4), (112, 1),
     (120, 10 ** 6), (160, 0), (192, 7), (200, 1 << 40),
 ])
 def test_inspect_refuses_what_the_oracle_refuses(lib, offset, value):

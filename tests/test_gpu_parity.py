@@ -38,7 +38,7 @@ def gpu_roundtrip(a: np.ndarray, eb: float, rel: bool, **kw):
 
 def assert_parity(a, eb, rel=True, **kw):
     okw = dict(no_topo=kw.get("no_topo", False), rs_sweeps=kw.get("rs_sweeps", 1),
-               rbf_k=kw.get("rbf_k", 0), rbf_sigma=kw.get("rbf_sigma", 0.0))
+               rbf_k=kw.get("rbf_k", 0), rbf_sigma=kw.get("rbf_sigma", 0.0), rbf_solve=kw.get("rbf_solve", False))
     gbuf, gout = gpu_roundtrip(a, eb, rel, **okw)
     obuf = oracle.compress(a, eb, rel=rel, **okw)
     assert gbuf == obuf, section_report(gbuf, obuf)
@@ -269,3 +269,52 @@ def test_parity_rs_hand_cases(name):
     k = int(g.get("rbf_k", 3))
     s = float(g.get("rbf_sigma", 1.0))
     assert_parity(field(g), float(g["eps"]), rel=False, rbf_k=k, rbf_sigma=s)
+
+
+@pytest.mark.parametrize("k", [3, 5, 7])
+@pytest.mark.parametrize("name,make", [
+    ("climate_120x250", lambda: synth.climate_2d(120, 250, seed=9).numpy()),
+    ("turb_20", lambda: synth.turbulence_3d(20, seed=5).numpy()),
+    ("adv3d_17x9x13", lambda: synth.adversarial_small(2, (17, 9, 13)).numpy()),
+    ("mixed3d_45x37x29", lambda: synth.grf((29, 37, 45), -11 / 3, 4).numpy()),
+], ids=["climate_120x250", "turb_20", "adv3d_17x9x13", "mixed3d_45x37x29"])
+def test_parity_rbf_solve(name, make, k):
+    """The literal RBF interpolation (Section IV-B(3), Eqs. RBF-interp-final
+    and RBF-eval; header flag RBF_SOLVE): the weights solved on the device in
+    binary64 (up to 122 nodes at r = 3 in 3D) and the unclamped refinement
+    give the oracle's stream and field bit for bit."""
+    a = make()
+    for eb in (1e-2, 1e-3):
+        assert_parity(a, eb, rel=True, rbf_solve=True, rbf_k=k, rbf_sigma=0.5 + 0.1 * k / 2)
+
+
+@pytest.mark.parametrize("shape", [(96, 96, 96), (600, 700)])
+def test_parity_rbf_solve_many_tiles(shape):
+    """Literal interpolation on fields of many decode tiles, adaptive kernel,
+    two sweeps: with neighbourhood records and with direct field reads."""
+    from paper_2602_17552_gb300 import autotune
+    a = synth.turbulence_3d(shape[0], seed=11).numpy() if len(shape) == 3 else \
+        synth.climate_2d(*shape, seed=11).numpy()
+    opts = dict(rbf_solve=True, rs_sweeps=2)
+    obuf = oracle.compress(a, 1e-3, rel=True, **opts)
+    oout = oracle.decompress(obuf, a.shape)
+    f = torch.from_numpy(a).cuda()
+    try:
+        for cfg in ({}, {"saddle_records": -1}, {"dec_split": 1}):
+            autotune.apply({**autotune.DEFAULT, **cfg})
+            buf = codec.compress(f, 1e-3, "rel", **opts)
+            assert buf.cpu().numpy().tobytes() == obuf, cfg
+            out = codec.decompress(buf, a.shape).cpu().numpy()
+            assert np.array_equal(out.view(np.uint32), oout.view(np.uint32)), \
+                (cfg, int(np.count_nonzero(out.view(np.uint32) != oout.view(np.uint32))))
+    finally:
+        autotune.restore()
+
+
+def test_parity_rbf_solve_hand_cases():
+    """The hand-worked RS^ fixtures decoded with the literal interpolation."""
+    for name in ("h4_saddle.txt", "rs_shepard_2d_k5.txt", "rs_shepard_2d_k5_edge.txt", "rs_clamp_3d_k3.txt",
+                 "rs_reject_new_type_3d.txt"):
+        g = load(name)
+        assert_parity(field(g), float(g["eps"]), rel=False, rbf_k=int(g.get("rbf_k", 3)),
+                      rbf_sigma=float(g.get("rbf_sigma", 1.0)), rbf_solve=True)

@@ -510,6 +510,99 @@ def test_rbf_parameters_grow_with_smoothness():
     assert ks[-1] == 3 and sig[-1] == 0.5
 
 
+def _ball_offsets(ndim, r):
+    """N_r(p) minus p as (x, y, z) offsets, (z, y, x) ascending."""
+    rz = r if ndim == 3 else 0
+    return [(dx, dy, dz) for dz in range(-rz, rz + 1) for dy in range(-r, r + 1) for dx in range(-r, r + 1)
+            if 0 < dx * dx + dy * dy + dz * dz <= r * r]
+
+
+RBF_CASES = [(nd, r, s) for nd in (2, 3) for r in (1, 2, 3) for s in (0.5, 0.75, 1.0)]
+
+
+@pytest.mark.parametrize("ndim,r,sigma", RBF_CASES)
+def test_rbf_solve_equals_bordered_system(ndim, r, sigma):
+    """Eqs. RBF-interp-final / RBF-eval with a constant term: the evaluation
+    weights at p are the first m entries of M^-1 [phi_p; 1], M the bordered
+    matrix [[Phi, 1], [1^T, 0]] -- solved here by LU on the whole bordered
+    system, which the oracle never forms (it eliminates the constant by two
+    Cholesky solves).  The condition number of Phi stays below 1e4 for every
+    radius and width the compressor chooses, so 1e-10 relative is loose."""
+    P = np.array(_ball_offsets(ndim, r), np.float64)
+    m = len(P)
+    D2 = ((P[:, None, :] - P[None, :, :]) ** 2).sum(-1)
+    Phi = np.exp(-D2 / (2 * sigma * sigma))
+    M = np.ones((m + 1, m + 1))
+    M[:m, :m] = Phi
+    M[m, m] = 0.0
+    rhs = np.append(np.exp(-(P ** 2).sum(-1) / (2 * sigma * sigma)), 1.0)
+    want = np.linalg.solve(M, rhs)[:m]
+    got = oracle.rbf_solve(ndim, r, sigma)
+    assert got.shape == (m,) and m == {(2, 1): 4, (2, 2): 12, (2, 3): 28, (3, 1): 6, (3, 2): 32, (3, 3): 122}[(ndim, r)]
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max(), np.abs(got - want).max()
+    assert abs(got.sum() - 1.0) <= 1e-13
+
+
+@pytest.mark.parametrize("ndim,r,sigma", RBF_CASES)
+def test_rbf_solve_interpolates_and_is_symmetric(ndim, r, sigma):
+    """The interpolant passes through the data: evaluated at node j its
+    weights are the unit vector e_j.  At p, the ball's symmetries (axis flips
+    and, in the plane or cube, axis swaps) map nodes onto nodes, so nodes at
+    the same distance from p get the same weight; hence linear functions are
+    reproduced at p as well (sum alpha_i q_i = 0).  (Equal distance alone is
+    not enough: (3, 0, 0) and (2, 2, 1) are not images of one another.)"""
+    offs = _ball_offsets(ndim, r)
+    for j in range(0, len(offs), max(1, len(offs) // 7)):
+        w = oracle.rbf_solve(ndim, r, sigma, at=offs[j])
+        e = np.zeros(len(offs))
+        e[j] = 1.0
+        assert np.abs(w - e).max() <= 1e-11, (j, np.abs(w - e).max())
+    a = oracle.rbf_solve(ndim, r, sigma)
+    orbit = [tuple(sorted(abs(c) for c in o)) for o in offs]
+    for key in set(orbit):
+        grp = a[[k == key for k in orbit]]
+        assert np.ptp(grp) <= 1e-12, (key, grp)
+    assert len(set(orbit)) < len(offs)
+    assert np.abs((a[:, None] * np.array(offs, np.float64)).sum(0)).max() <= 1e-12
+
+
+def test_rbf_solve_mode_only_moves_saddle_candidates():
+    """The literal interpolation (header flag RBF_SOLVE) changes RS^ alone:
+    against the default reading the decoded fields differ only at
+    saddle-labelled points; FP = FT = 0 and the relaxed bound eps + h still
+    hold, and the streams differ in the flag word alone."""
+    for name, a in _fields_small():
+        for eb in (1e-2, 1e-3):
+            b0 = oracle.compress(a, eb, rel=True)
+            b1 = oracle.compress(a, eb, rel=True, rbf_solve=True)
+            assert oracle.header(b1)["flags"] == oracle.RBF_SOLVE
+            diff = [i for i in range(len(b0)) if b0[i] != b1[i]]
+            assert len(b0) == len(b1) and diff in ([], [40]), (name, diff)
+            o0, o1 = oracle.decompress(b0, a.shape), oracle.decompress(b1, a.shape)
+            la, l1 = oracle.critical_points(a), oracle.critical_points(o1)
+            moved = o0.view(np.uint32) != o1.view(np.uint32)
+            assert np.all(la[moved] == SAD), name
+            err = oracle.topo_errors(la, l1)
+            assert err[1].sum() == 0 and err[2].sum() == 0, (name, err)
+            h = oracle.header(b1)
+            dev = np.abs(a.astype(np.float64) - o1.astype(np.float64)).max()
+            assert dev <= h["eps"] + float(np.float32(h["h_f"])) * (1 + 2 ** -20), name
+
+
+def test_rbf_solve_needs_a_positive_width():
+    """With the literal interpolation the decoder solves with the header's
+    sigma: a width that is not a positive finite number marks the stream
+    damaged."""
+    import struct
+    a = synth.gaussian_bumps_2d(20, 24, count=4, seed=1).numpy()
+    buf = bytearray(oracle.compress(a, 1e-3, rel=True, rbf_solve=True))
+    for bad in (0.0, -1.0, float("nan"), float("inf")):
+        buf[92:96] = struct.pack("<f", bad)
+        with pytest.raises(oracle.OracleError) as ei:
+            oracle.decompress(bytes(buf), a.shape)
+        assert ei.value.status == oracle.CORRUPT
+
+
 def _fields_small():
     yield "bumps", synth.gaussian_bumps_2d(64, 80, count=20, seed=5).numpy()
     yield "climate", synth.climate_2d(60, 96, seed=2).numpy()
@@ -585,7 +678,7 @@ def test_corrupt_stream_rejected():
 
 
 @pytest.mark.parametrize("offset,value", [
-    (40, 2),                  # flags: only NO_TOPO is defined
+    (40, 4),                  # flags: only NO_TOPO and RBF_SOLVE are defined
     (96, 0), (96, 17),        # RS^ sweeps outside 1..16
     (64, 0x7F800000),         # bin width w = +inf
     (72, 0xBF800000),         # half-width h < 0
