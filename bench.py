@@ -720,24 +720,41 @@ def run_serve(args):
 
 
 def run_tradeoff(args):
-    """Bit rate against FN / FP / FT (Section III-B), TopoSZp and its SZp-only
-    mode (no topology sections), relative bounds 1e-3, 1e-4, 1e-5, on the
-    1800x3600 and 512^3 fields: the synthetic analogue of Table II / Fig. 8.
-    One JSON line; not a throughput measurement."""
+    """Bit rate against FN / FP / FT (Section III-B), TopoSZp (saddle
+    refinement by the clamped normalised kernel, and by the literal RBF
+    interpolation) and its SZp-only mode (no topology sections), relative
+    bounds 1e-3, 1e-4, 1e-5, on the 1800x3600 and 512^3 fields: the synthetic
+    analogue of Table II / Fig. 8.  decompress_ms: the median of three
+    CUDA-event timed decompress calls of the row's stream.  One JSON line."""
     import torch
     from paper_2602_17552_gb300 import codec
     torch.cuda.set_device(0)
     rows = []
+    modes = (("TopoSZp", {}), ("TopoSZp, literal RBF", {"rbf_solve": True}), ("SZp only", {"no_topo": True}))
+
+    def dec_ms(f, eb, kw):
+        buf = codec.compress(f, eb, "rel", **kw)
+        out = torch.empty_like(f)
+        ts = []
+        for _ in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            codec.decompress_async(buf, tuple(f.shape), out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(statistics.median(ts[1:]))
+
     for wl in ("climate", "turb512"):
         spec = workload_spec(wl, 1e-3, args.side)
         f = spec.make("cuda")
         labels, cnt = codec.critical_points(f)
         counts = cnt.cpu().tolist()
         for eb in (1e-3, 1e-4, 1e-5):
-            for no_topo in (False, True):
-                r = codec.tradeoff(f, eb, "rel", no_topo=no_topo, labels=labels)
+            for mode, kw in modes:
+                r = codec.tradeoff(f, eb, "rel", labels=labels, **kw)
                 rows.append({"field": describe(spec).split(", relative")[0], "eb_rel": eb,
-                             "mode": "SZp only" if no_topo else "TopoSZp", "counts_rmsM": counts,
+                             "mode": mode, "counts_rmsM": counts, "decompress_ms": round(dec_ms(f, eb, kw), 4),
                              **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}})
         del f, labels
         torch.cuda.empty_cache()
