@@ -43,7 +43,10 @@ NOMINAL_HBM_GBS = 8000.0
 # points.  Each entry carries the SHA-1 of the kernel's source files at the
 # time of the capture: the figure is reported only while they are unchanged
 # (otherwise `traffic` is null).
-TRAFFIC_PER_POINT = {}
+TRAFFIC_PER_POINT = {
+    # 301.25 MB per 384^3 launch (profiles/launches_turb512_rel1e-3.md)
+    "k_decode_fused": {"per_point": 5.3203, "source_sha1": "176ec3fd2da8611a5404c0bb502fb800051b66b3"},
+}
 KERNEL_SOURCES = {
     "k_decode_fused": ("tsz_decompress.cu", "tsz_common.cuh"),
     "k_saddle_rounds": ("tsz_decompress.cu", "tsz_common.cuh"),
@@ -59,7 +62,8 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256", "batch", "serve", "tradeoff"])
+    ap.add_argument("--workload", default="turb512", choices=["turb512", "climate", "bumps256", "batch", "serve", "tradeoff",
+                                                           "configs"])
     ap.add_argument("--fields", type=int, default=96, help="batch workload: number of fields")
     ap.add_argument("--branches", type=int, default=0, help="batch workload: graph branches (0 = tuned)")
     ap.add_argument("--requests", type=int, default=2000, help="serve workload: number of requests")
@@ -761,6 +765,81 @@ def run_tradeoff(args):
     print(json.dumps({"workload": "tradeoff", "data": "synthetic", "rows": rows}), flush=True)
 
 
+def run_configs(args):
+    """The per-configuration results table: configs 1-3 at each of their
+    bounds, plain compress and decompress calls timed alone (CUDA events,
+    median of 20 after 3 warm-ups, inputs resident in HBM), with the HBM
+    fraction of the algorithmic bytes -- compress: 8n (REL: range pass plus
+    main read) or 4n (ABS), plus C, plus 32 bytes per extremum (the key list
+    written and read by the rank stage); decompress: C + 4n -- over the
+    measured copy bandwidth, and the topology errors of the decoded field.
+    One JSON line; the oracle comparison of the same configurations is in
+    the parity tests."""
+    import torch
+    from paper_2602_17552_gb300 import codec
+    torch.cuda.set_device(0)
+    peaks = measured_peaks()
+    peak = float(peaks["hbm_gbs"]) if peaks else 6800.0
+    rows = []
+    cases = [("bumps256", None), ("climate", 1e-2), ("climate", 1e-3), ("climate", 1e-4),
+             ("turb512", 1e-3), ("turb512", 1e-5)]
+
+    def timed(fn, reps=20):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    for wl, eb in cases:
+        spec = workload_spec(wl, eb if eb is not None else 1e-3, args.side)
+        f = spec.make("cuda")
+        n = f.numel()
+        rel = spec.eb_mode == "rel"
+        eb_call = eb if rel else 1e-3 * float(f.max() - f.min())
+        mode = "rel" if rel else "abs"
+        out = torch.empty(codec.compress_bound(f.shape), dtype=torch.uint8, device="cuda")
+        cws = torch.empty(codec.compress_workspace_size(f.shape), dtype=torch.uint8, device="cuda")
+        dws = torch.empty(codec.decompress_workspace_size(f.shape), dtype=torch.uint8, device="cuda")
+        size = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        rec = torch.empty_like(f)
+        c_ms = timed(lambda: codec.compress_async(f, eb_call, mode, out=out, ws=cws, size=size, status=st))
+        csize = int(size.item())
+        buf = out[:csize]
+        d_ms = timed(lambda: codec.decompress_async(buf, f.shape, out=rec, ws=dws, status=st))
+        if int(st.item()):
+            raise RuntimeError(f"device status {int(st.item())} on {wl} {eb}")
+        info = codec.inspect(buf)
+        k = int(info.k_min + info.k_max)
+        lab_a, _ = codec.critical_points(f, counts=False)
+        lab_d, _ = codec.critical_points(rec, counts=False)
+        e = codec.topo_errors(lab_a, lab_d, n).cpu().tolist()
+        c_alg = (8 if rel else 4) * n + csize + 32 * k
+        d_alg = csize + 4 * n
+        rows.append({"config": describe(spec), "eb_mode": mode, "eb": eb_call, "n": n,
+                     "compressed_bytes": csize, "ratio": round(4 * n / csize, 3), "k_extrema": k,
+                     "compress_ms": round(c_ms, 4), "decompress_ms": round(d_ms, 4),
+                     "compress_gbs": round(4 * n / (c_ms * 1e-3) / 1e9, 2),
+                     "decompress_gbs": round(4 * n / (d_ms * 1e-3) / 1e9, 2),
+                     "compress_alg_bytes": c_alg, "decompress_alg_bytes": d_alg,
+                     "compress_frac_measured": round(c_alg / (c_ms * 1e-3) / 1e9 / peak, 4),
+                     "decompress_frac_measured": round(d_alg / (d_ms * 1e-3) / 1e9 / peak, 4),
+                     "max_err_over_eps": round(float((rec.double() - f.double()).abs().max()) / info.eps, 4),
+                     "fn_rmsM": e[0], "fp_rmsM": e[1], "ft_rmsM": e[2]})
+        del f, out, cws, dws, rec, lab_a, lab_d
+        torch.cuda.empty_cache()
+    print(json.dumps({"workload": "configs", "data": "synthetic", "peak_gbs": peak,
+                      "peak_source": "measured" if peaks else "fallback", "rows": rows}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -771,6 +850,8 @@ def main():
         run_serve(args)
     elif args.workload == "tradeoff":
         run_tradeoff(args)
+    elif args.workload == "configs":
+        run_configs(args)
     else:
         run_ours(args)
 
