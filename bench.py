@@ -44,7 +44,7 @@ NOMINAL_HBM_GBS = 8000.0
 # time of the capture: the figure is reported only while they are unchanged
 # (otherwise `traffic` is null).
 TRAFFIC_PER_POINT = {
-    # 301.25 MB per 384^3 launch (profiles/launches_turb512_rel1e-3.md)
+    # 301.25 MB per launch at 384^3, relative eb 1e-3
     "k_decode_fused": {"per_point": 5.3203, "source_sha1": "176ec3fd2da8611a5404c0bb502fb800051b66b3"},
 }
 KERNEL_SOURCES = {
@@ -470,7 +470,7 @@ def run_ours(args):
     # kernels per call (tsz_api.cu launch sequences; on the key-bitmap path the
     # radix-sort kernels are launched and return at once)
     launches_c = 24 if topo else 7
-    launches_d = 6
+    launches_d = 7
     result = {
         "metric": "compress+decompress throughput (uncompressed bytes / round-trip time)",
         "value": round(value, 2), "unit": "GB/s", "n_gpus": ws_n, "steps": args.steps,

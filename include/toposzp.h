@@ -67,9 +67,20 @@ typedef enum {
  * min(0.1 h, half the smallest nonzero face gap).  Stored in the header; the
  * decoder follows the stream. */
 #define TOPOSZP_RBF_SOLVE 2u
+/* Format v2 (stream version 2): blocks are tiles of 32 points, 8 x 4 in 2D
+ * and 4 x 4 x 2 in 3D (x fastest), in raster order over the block grid, in
+ * place of 32 consecutive points (Section II-C's B + LZ, tile-shaped).  Per
+ * block, of the residuals of q - q_0 along the block's element order and its
+ * block-local 2D / 3D Lorenzo residuals, the set with the smaller widest
+ * residual is coded (bit 7 of the block's width byte: 1 = Lorenzo); positions
+ * outside the grid take the code of the nearest point inside.  Every other
+ * section and every decoded value are those of format v1: the flag changes
+ * only the coded size.  toposzp_inspect reports it in info->flags; the
+ * decoder reads the version from the stream. */
+#define TOPOSZP_TILE_BLOCKS 4u
 
 typedef struct {
-    uint32_t flags;       /* an OR of TOPOSZP_NO_TOPO and TOPOSZP_RBF_SOLVE; 0: neither */
+    uint32_t flags;       /* an OR of TOPOSZP_NO_TOPO, TOPOSZP_RBF_SOLVE, TOPOSZP_TILE_BLOCKS */
     uint32_t rs_sweeps;   /* passes over the saddle colour rounds; 0 means 1 */
     int32_t rbf_k;        /* RBF kernel size 3, 5 or 7; 0 = adaptive (Section IV-B(3)) */
     float rbf_sigma;      /* Gaussian width; 0 = adaptive in [0.5, 1] */

@@ -24,6 +24,7 @@ OK, INVALID_ARG, NONFINITE, EB_TOO_SMALL, BUFFER_TOO_SMALL, CORRUPT = range(6)
 R, MIN, SAD, MAX = 0, 1, 2, 3
 NO_TOPO = 1
 RBF_SOLVE = 2
+TILE_BLOCKS = 4
 
 
 def build(force: bool = False) -> str:
@@ -56,6 +57,8 @@ def lib():
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
         L.orc_compress_bound.restype = ctypes.c_uint64
         L.orc_compress_bound.argtypes = [ctypes.c_int, u64p]
+        L.orc_tile_blocks.restype = ctypes.c_uint64
+        L.orc_tile_blocks.argtypes = [ctypes.c_int, u64p]
         L.orc_critical_points.restype = None
         L.orc_critical_points.argtypes = [ctypes.c_void_p, ctypes.c_int, u64p, ctypes.c_void_p]
         L.orc_classify.restype = ctypes.c_int
@@ -178,14 +181,22 @@ def compress_bound(shape) -> int:
     return int(lib().orc_compress_bound(nd, d3))
 
 
+def tile_blocks(shape) -> int:
+    """Number of format-v2 (tile-shaped) blocks covering a grid of `shape`."""
+    a = np.empty(shape, np.uint8)
+    nd, d3 = _dims3(a)
+    return int(lib().orc_tile_blocks(nd, d3))
+
+
 def compress(a, eb: float, rel: bool = True, no_topo: bool = False, rs_sweeps: int = 1,
-             rbf_k: int = 0, rbf_sigma: float = 0.0, rbf_solve: bool = False) -> bytes:
+             rbf_k: int = 0, rbf_sigma: float = 0.0, rbf_solve: bool = False, tile_blocks: bool = False) -> bytes:
     a = _f32(a)
     nd, d3 = _dims3(a)
     cap = int(lib().orc_compress_bound(nd, d3))
     out = np.empty(cap, np.uint8)
     size = ctypes.c_uint64(0)
-    flags = (NO_TOPO if no_topo else 0) | (RBF_SOLVE if rbf_solve else 0)
+    flags = ((NO_TOPO if no_topo else 0) | (RBF_SOLVE if rbf_solve else 0) |
+             (TILE_BLOCKS if tile_blocks else 0))
     st = lib().orc_compress(a.ctypes.data, nd, d3, int(rel), float(eb), flags,
                             int(rs_sweeps), int(rbf_k), float(rbf_sigma), out.ctypes.data, cap,
                             ctypes.byref(size))

@@ -15,9 +15,11 @@
 #define L 32u                      /* block length (B stage), Section II-C / IV-A */
 #define HDR 256u                   /* stream header bytes */
 #define MAGIC 0x505A5354u          /* "TSZP" little-endian */
-#define VERSION 1u
+#define VERSION 1u                 /* blocks of L consecutive points (R6) */
+#define VERSION_TILES 2u           /* format v2: tile-shaped blocks (R19) */
 #define FLAG_NO_TOPO 1u
 #define FLAG_RBF_SOLVE 2u
+#define FLAG_TILE_BLOCKS 4u        /* compress only: write format v2 */
 
 /* ------------------------------------------------------------------ helpers */
 
@@ -284,6 +286,167 @@ static int codec_decode(const uint8_t* width, const int32_t* first, const uint32
     return off == pay_words ? 0 : -1;
 }
 
+/* Format v2 (R19): tile-shaped blocks of L = 32 points, 8 x 4 in 2D and
+ * 4 x 4 x 2 in 3D (x fastest), in raster order over the block grid.  Element
+ * e of a block sits at (e mod BX, (e / BX) mod BY, e / (BX BY)) inside it;
+ * a position outside the domain takes the code of the nearest point inside
+ * (each coordinate clamped).  The residuals are the Lorenzo differences of
+ * q' = q - q_0 inside the block, with q' = 0 outside it (the 2D predictor
+ * q'(x-1,y) + q'(x,y-1) - q'(x-1,y-1), its 3D analogue over the seven
+ * preceding corners), in 32-bit modular arithmetic; the decoder undoes them
+ * with prefix sums along x, y and z.  d_0 = 0, and the block's first value
+ * q_0, width, sign plane and magnitude planes are stored as in format v1. */
+static void tile_shape(int ndim, uint32_t* bx, uint32_t* by, uint32_t* bz) {
+    *bx = ndim == 3 ? 4u : 8u;
+    *by = 4u;
+    *bz = ndim == 3 ? 2u : 1u;
+}
+
+uint64_t orc_tile_blocks(int ndim, const uint64_t dims[3]) {
+    uint32_t bx, by, bz;
+    tile_shape(ndim, &bx, &by, &bz);
+    uint64_t nz = ndim == 3 ? dims[2] : 1;
+    return cdiv(dims[0], bx) * cdiv(dims[1], by) * cdiv(nz, bz);
+}
+
+/* the block's codes q'[e] = q[e] - q[0] of block (gx, gy, gz), e in element order */
+static void tile_gather(const int32_t* q, const uint64_t d3[3], uint32_t bx, uint32_t by, uint32_t bz,
+                        uint64_t gx, uint64_t gy, uint64_t gz, int32_t qq[L]) {
+    for (uint32_t e = 0; e < L; e++) {
+        uint64_t x = gx * bx + e % bx, y = gy * by + (e / bx) % by, z = gz * bz + e / (bx * by);
+        if (x >= d3[0]) x = d3[0] - 1;
+        if (y >= d3[1]) y = d3[1] - 1;
+        if (z >= d3[2]) z = d3[2] - 1;
+        qq[e] = q[x + d3[0] * (y + d3[1] * z)];
+    }
+}
+
+static void codec_encode_tiles(const int32_t* q, int ndim, const uint64_t d3[3], codec_t* cd) {
+    uint32_t bx, by, bz;
+    tile_shape(ndim, &bx, &by, &bz);
+    const uint64_t nbx = cdiv(d3[0], bx), nby = cdiv(d3[1], by), nbz = cdiv(d3[2], bz);
+    const uint64_t nblk = nbx * nby * nbz;
+    cd->nblk = nblk;
+    cd->cbits = (uint32_t*)calloc(cdiv(nblk, 32) + 1, 4);
+    cd->width = (uint8_t*)calloc(nblk + 1, 1);
+    cd->first = (int32_t*)calloc(nblk + 1, 4);
+    cd->pay = (uint32_t*)calloc(nblk * (L + 1) + 1, 4);
+    cd->pay_words = 0;
+    cd->sum_abs = 0;   /* not used by format v2: the linear-block sum is taken */
+    for (uint64_t b = 0; b < nblk; b++) {
+        int32_t qq[L];
+        tile_gather(q, d3, bx, by, bz, b % nbx, (b / nbx) % nby, b / (nbx * nby), qq);
+        uint32_t qp[L];   /* q' modulo 2^32 */
+        for (uint32_t e = 0; e < L; e++) qp[e] = (uint32_t)qq[e] - (uint32_t)qq[0];
+        /* both predictors: 0 = the chain in element order, 1 = Lorenzo */
+        uint32_t mag2[2][L], sgn2[2] = {0, 0}, mx2[2] = {0, 0};
+        for (uint32_t e = 0; e < L; e++) {
+            const uint32_t ex = e % bx, ey = (e / bx) % by, ez = e / (bx * by);
+            /* inclusion-exclusion over the corners (ex - sx, ey - sy, ez - sz), s in {0,1}^3 */
+            uint32_t du = 0;
+            for (uint32_t sm = 0; sm < 8; sm++) {
+                const uint32_t sx = sm & 1u, sy = (sm >> 1) & 1u, sz = (sm >> 2) & 1u;
+                if (sx > ex || sy > ey || sz > ez) continue;
+                const uint32_t v = qp[(ex - sx) + bx * ((ey - sy) + by * (ez - sz))];
+                if ((sx + sy + sz) & 1u) du -= v;
+                else du += v;
+            }
+            const uint32_t dc = e ? qp[e] - qp[e - 1] : 0u;
+            const uint32_t dd[2] = {dc, du};
+            for (int k = 0; k < 2; k++) {
+                int32_t d;
+                memcpy(&d, &dd[k], 4);
+                if (d < 0) sgn2[k] |= 1u << e;
+                mag2[k][e] = d < 0 ? (uint32_t)(-(int64_t)d) : (uint32_t)d;
+                if (mag2[k][e] > mx2[k]) mx2[k] = mag2[k][e];
+            }
+        }
+        const int sel = mx2[1] < mx2[0];
+        const uint32_t* mag = mag2[sel];
+        const uint32_t sgn = sgn2[sel], mx = mx2[sel];
+        uint32_t w = 0;
+        while (w < 32 && (mx >> w) != 0) w++;
+        cd->width[b] = (uint8_t)(w | (uint32_t)sel << 7);
+        cd->first[b] = qq[0];
+        if (w == 0) {
+            cd->cbits[b / 32] |= 1u << (b % 32);
+            continue;
+        }
+        cd->pay[cd->pay_words++] = sgn;
+        for (uint32_t pl = 0; pl < w; pl++) {
+            uint32_t word = 0;
+            for (uint32_t e = 0; e < L; e++) word |= ((mag[e] >> pl) & 1u) << e;
+            cd->pay[cd->pay_words++] = word;
+        }
+    }
+}
+
+/* Inverse of codec_encode_tiles: residuals, prefix sums along x, then y, then
+ * z (modulo 2^32), plus q_0; positions outside the domain are dropped. */
+static int codec_decode_tiles(const uint8_t* width, const int32_t* first, const uint32_t* pay, uint64_t pay_words,
+                              int ndim, const uint64_t d3[3], int32_t* q) {
+    uint32_t bx, by, bz;
+    tile_shape(ndim, &bx, &by, &bz);
+    const uint64_t nbx = cdiv(d3[0], bx), nby = cdiv(d3[1], by), nbz = cdiv(d3[2], bz);
+    const uint64_t nblk = nbx * nby * nbz;
+    uint64_t off = 0;
+    for (uint64_t b = 0; b < nblk; b++) {
+        const uint32_t w = width[b] & 0x7Fu, sel = width[b] >> 7;
+        uint32_t acc[L];
+        if (w > 32 || (sel && w == 0)) return -1;
+        if (w == 0) {
+            for (uint32_t e = 0; e < L; e++) acc[e] = 0;
+        } else if (!sel) {
+            if (off + 1 + w > pay_words) return -1;
+            const uint32_t sgn = pay[off];
+            for (uint32_t e = 0; e < L; e++) {
+                uint32_t m = 0;
+                for (uint32_t pl = 0; pl < w; pl++) m |= ((pay[off + 1 + pl] >> e) & 1u) << pl;
+                acc[e] = ((sgn >> e) & 1u) ? 0u - m : m;
+            }
+            off += 1 + w;
+            for (uint32_t e = 1; e < L; e++) acc[e] += acc[e - 1];   /* the element-order chain */
+        } else {
+            if (off + 1 + w > pay_words) return -1;
+            const uint32_t sgn = pay[off];
+            for (uint32_t e = 0; e < L; e++) {
+                uint32_t m = 0;
+                for (uint32_t pl = 0; pl < w; pl++) m |= ((pay[off + 1 + pl] >> e) & 1u) << pl;
+                acc[e] = ((sgn >> e) & 1u) ? 0u - m : m;
+            }
+            off += 1 + w;
+            for (uint32_t e = 0; e < L; e++)   /* along x */
+                if (e % bx) acc[e] += acc[e - 1];
+            for (uint32_t e = 0; e < L; e++)   /* along y */
+                if ((e / bx) % by) acc[e] += acc[e - bx];
+            for (uint32_t e = 0; e < L; e++)   /* along z */
+                if (e / (bx * by)) acc[e] += acc[e - bx * by];
+        }
+        const uint64_t gx = b % nbx, gy = (b / nbx) % nby, gz = b / (nbx * nby);
+        for (uint32_t e = 0; e < L; e++) {
+            const uint64_t x = gx * bx + e % bx, y = gy * by + (e / bx) % by, z = gz * bz + e / (bx * by);
+            if (x >= d3[0] || y >= d3[1] || z >= d3[2]) continue;
+            const uint32_t v = acc[e] + (uint32_t)first[b];
+            int32_t vi;
+            memcpy(&vi, &v, 4);
+            q[x + d3[0] * (y + d3[1] * z)] = vi;
+        }
+    }
+    return off == pay_words ? 0 : -1;
+}
+
+/* The neighbour variation of the RBF parameters, sum |q_j - q_{j-1}| within
+ * blocks of L consecutive points (format v1's residual sum), for either format. */
+static uint64_t linear_sum_abs(const int32_t* q, uint64_t n) {
+    uint64_t s = 0;
+    for (uint64_t i = 1; i < n; i++) {
+        if (i % L == 0) continue;
+        const int64_t d = (int64_t)q[i] - (int64_t)q[i - 1];
+        s += (uint64_t)(d < 0 ? -d : d);
+    }
+    return s;
+}
+
 /* ----------------------------------------------------- RBF parameters (IV-B) */
 
 /* exp(-t) for t >= 0 by scaling and squaring: exp(-t) = (exp(-t/1024))^1024 with
@@ -415,6 +578,8 @@ static void rank_layout(uint64_t s7, uint64_t k, uint64_t rpay, uint64_t sub[5])
 uint64_t orc_compress_bound(int ndim, const uint64_t dims[3]) {
     uint64_t n = dims[0] * dims[1] * (ndim == 3 ? dims[2] : 1);
     uint64_t nb = cdiv(n, L);
+    const uint64_t nbt = orc_tile_blocks(ndim, dims);   /* format v2's block count */
+    if (nbt > nb) nb = nbt;
     return HDR + 16 * 12 + 2 * (4 * cdiv(nb, 32) + nb + 4 * nb) + 4 * cdiv(n, 16) +
            4 * (L + 1) * nb + 4 * L * nb;
 }
@@ -459,12 +624,19 @@ int orc_compress(const float* a, int ndim, const uint64_t dims[3], int rel, doub
     /* QZ, then B + LZ + BE */
     int32_t* q = (int32_t*)malloc(n * sizeof(int32_t));
     for (uint64_t i = 0; i < n; i++) q[i] = orc_quantize(a[i], &qp);
+    const int tiles = (flags & FLAG_TILE_BLOCKS) != 0;
     codec_t cd;
-    codec_encode(q, n, &cd);
+    if (tiles) {
+        const uint64_t d3[3] = {dims[0], dims[1], nz};
+        codec_encode_tiles(q, ndim, d3, &cd);
+    } else {
+        codec_encode(q, n, &cd);
+    }
+    const uint64_t sum_abs = linear_sum_abs(q, n);
 
     int32_t kk;
     float sigma, g[9];
-    rbf_params(cd.sum_abs, n, cd.nblk, orc_quantize(qp.vmin, &qp), orc_quantize(qp.vmax, &qp),
+    rbf_params(sum_abs, n, cdiv(n, L), orc_quantize(qp.vmin, &qp), orc_quantize(qp.vmax, &qp),
                rbf_k, rbf_sigma, &kk, &sigma, g);
 
     layout_t lo;
@@ -482,7 +654,7 @@ int orc_compress(const float* a, int ndim, const uint64_t dims[3], int rel, doub
     memset(out, 0, end);
     uint8_t* h = out;
     put32(h + 0, MAGIC);
-    put32(h + 4, VERSION);
+    put32(h + 4, tiles ? VERSION_TILES : VERSION);
     put32(h + 8, (uint32_t)ndim);
     put32(h + 12, L);
     put64(h + 16, dims[0]);
@@ -506,7 +678,7 @@ int orc_compress(const float* a, int ndim, const uint64_t dims[3], int rel, doub
     put64(h + 120, kmin);
     put64(h + 128, kmax);
     put64(h + 136, ksad);
-    put64(h + 144, cd.sum_abs);
+    put64(h + 144, sum_abs);
     put64(h + 152, lo.s1);
     put64(h + 160, lo.s2);
     put64(h + 168, lo.s4);
@@ -572,7 +744,10 @@ int orc_colour(int ndim, uint64_t x, uint64_t y, uint64_t z, int* ncol) {
 int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
                    float* d0, float* d1, uint64_t stats[4]) {
     if (size < HDR) return ORC_CORRUPT;
-    if (get32(in) != MAGIC || get32(in + 4) != VERSION || get32(in + 12) != L) return ORC_CORRUPT;
+    const uint32_t version = get32(in + 4);
+    if (get32(in) != MAGIC || (version != VERSION && version != VERSION_TILES) || get32(in + 12) != L)
+        return ORC_CORRUPT;
+    const int tiles = version == VERSION_TILES;
     int ndim = (int)get32(in + 8);
     uint64_t dims[3] = {get64(in + 16), get64(in + 24), get64(in + 32)};
     uint32_t flags = get32(in + 40);
@@ -594,7 +769,8 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
     for (int i = 0; i < 9; i++) g[i] = u2f(get32(in + 220 + 4 * i));
     if ((ndim != 2 && ndim != 3) || dims[0] == 0 || dims[1] == 0 || dims[2] == 0) return ORC_CORRUPT;
     if (ndim == 2 && dims[2] != 1) return ORC_CORRUPT;
-    if (n != dims[0] * dims[1] * dims[2] || n != n_out || nblk != cdiv(n, L)) return ORC_CORRUPT;
+    if (n != dims[0] * dims[1] * dims[2] || n != n_out) return ORC_CORRUPT;
+    if (nblk != (tiles ? orc_tile_blocks(ndim, dims) : cdiv(n, L))) return ORC_CORRUPT;
     if (kk != 3 && kk != 5 && kk != 7) return ORC_CORRUPT;
     /* a header this writer cannot produce marks a damaged stream (R7): every
      * field within the range compression gives it, every section offset equal
@@ -621,8 +797,11 @@ int orc_decompress(const uint8_t* in, uint64_t size, float* out, uint64_t n_out,
 
     /* BE^, LZ^ + B^ */
     int32_t* q = (int32_t*)malloc(n * sizeof(int32_t));
-    if (codec_decode(in + lo.s2, (const int32_t*)(in + lo.s4), (const uint32_t*)(in + lo.s5),
-                     pay_words, n, q)) { free(q); return ORC_CORRUPT; }
+    const int bad = tiles ? codec_decode_tiles(in + lo.s2, (const int32_t*)(in + lo.s4),
+                                               (const uint32_t*)(in + lo.s5), pay_words, ndim, dims, q)
+                          : codec_decode(in + lo.s2, (const int32_t*)(in + lo.s4), (const uint32_t*)(in + lo.s5),
+                                         pay_words, n, q);
+    if (bad) { free(q); return ORC_CORRUPT; }
     /* QZ^ */
     float* F = out;
     for (uint64_t i = 0; i < n; i++) F[i] = orc_dequantize(q[i], &qp);

@@ -58,9 +58,13 @@ int orc_rbf_solve(int ndim, int r, float sigma, int ex, int ey, int ez, double* 
 int orc_colour(int ndim, uint64_t x, uint64_t y, uint64_t z, int* ncol);   /* RS^ rounds */
 
 /* --- whole pipeline --- */
-uint64_t orc_compress_bound(int ndim, const uint64_t dims[3]);
+uint64_t orc_compress_bound(int ndim, const uint64_t dims[3]);   /* either format */
+/* Blocks of format v2 (8 x 4 tiles in 2D, 4 x 4 x 2 in 3D) covering the grid. */
+uint64_t orc_tile_blocks(int ndim, const uint64_t dims[3]);
 /* rel: 0 absolute eb, 1 eb * (max - min).  flags bit0: no topology (SZp only);
- * bit1: RS^ by the literal RBF interpolation, unclamped (see orc_decompress).
+ * bit1: RS^ by the literal RBF interpolation, unclamped (see orc_decompress);
+ * bit2: format v2, tile-shaped blocks with block-local 2D / 3D Lorenzo
+ * residuals (header version 2; the decoded field equals format v1's).
  * rbf_k / rbf_sigma: 0 = adaptive.  Returns a status; *out_size on success. */
 int orc_compress(const float* a, int ndim, const uint64_t dims[3], int rel, double eb,
                  uint32_t flags, uint32_t rs_sweeps, int32_t rbf_k, float rbf_sigma,

@@ -20,6 +20,7 @@ OK, INVALID_ARG, NONFINITE, EB_TOO_SMALL, BUFFER_TOO_SMALL, CORRUPT_STREAM, TIME
 EB_ABS, EB_REL = 0, 1
 NO_TOPO = 1
 RBF_SOLVE = 2
+TILE_BLOCKS = 4
 
 
 class TopoSZpError(RuntimeError):

@@ -16,7 +16,7 @@ from dataclasses import dataclass
 import torch
 
 from . import _lib
-from ._lib import EB_ABS, EB_REL, NO_TOPO, RBF_SOLVE, TopoSZpError
+from ._lib import EB_ABS, EB_REL, NO_TOPO, RBF_SOLVE, TILE_BLOCKS, TopoSZpError
 
 _WS = {}   # (device, kind) -> cached workspace tensor (grown on demand)
 
@@ -61,10 +61,12 @@ def workspace(kind: str, nbytes: int, device) -> torch.Tensor:
     return buf
 
 
-def make_params(no_topo=False, rs_sweeps=1, rbf_k=0, rbf_sigma=0.0, rbf_solve=False) -> _lib.Params:
+def make_params(no_topo=False, rs_sweeps=1, rbf_k=0, rbf_sigma=0.0, rbf_solve=False,
+                tile_blocks=False) -> _lib.Params:
     p = _lib.Params()
     _lib.load().toposzp_default_params(ctypes.byref(p))
-    p.flags = (NO_TOPO if no_topo else 0) | (RBF_SOLVE if rbf_solve else 0)
+    p.flags = ((NO_TOPO if no_topo else 0) | (RBF_SOLVE if rbf_solve else 0) |
+               (TILE_BLOCKS if tile_blocks else 0))
     p.rs_sweeps = int(rs_sweeps)
     p.rbf_k = int(rbf_k)
     p.rbf_sigma = float(rbf_sigma)
@@ -116,12 +118,15 @@ def compress_async(field: torch.Tensor, eb: float, mode: str = "rel", *, params=
 
 
 def compress(field: torch.Tensor, eb: float, mode: str = "rel", *, no_topo=False, rs_sweeps=1, rbf_k=0,
-             rbf_sigma=0.0, rbf_solve=False, stream=None) -> torch.Tensor:
+             rbf_sigma=0.0, rbf_solve=False, tile_blocks=False, stream=None) -> torch.Tensor:
     """Compress and return the stream as a uint8 CUDA tensor of its exact length
     (synchronises ``stream`` to read the length and the device status).
     ``rbf_solve`` selects the literal RBF interpolation for the decoder's
-    saddle refinement (stored in the stream's header)."""
-    call = compress_async(field, eb, mode, params=make_params(no_topo, rs_sweeps, rbf_k, rbf_sigma, rbf_solve),
+    saddle refinement (stored in the stream's header); ``tile_blocks`` writes
+    format v2 (tile-shaped blocks; the same decoded field, a smaller stream
+    on most fields)."""
+    call = compress_async(field, eb, mode,
+                          params=make_params(no_topo, rs_sweeps, rbf_k, rbf_sigma, rbf_solve, tile_blocks),
                           stream=stream)
     (torch.cuda.current_stream() if stream is None else stream).synchronize()
     _check(int(call.status.item()), "toposzp_compress (device)")

@@ -48,9 +48,11 @@ static bool make_geo(int ndim, const uint64_t dims[3], Geo& g) {
     return true;
 }
 
-constexpr CompressWs compress_ws_c(uint64_t n) {
+// nb_fmt: the blocks of a format-v2 stream (0 for format v1): the encoder's
+// tiles then cover the larger of its payload tiles and the linear tiles
+constexpr CompressWs compress_ws_c(uint64_t n, uint64_t nb_fmt = 0) {
     CompressWs w{};
-    const uint64_t nb = cdiv(n, L);
+    const uint64_t nb = cdiv(n, L) > nb_fmt ? cdiv(n, L) : nb_fmt;
     w.G = SORT_G;
     w.list_cap = (uint32_t)(cdiv(n, 2) + 1);
     w.ntiles = (uint32_t)cdiv(nb, TILE_BLOCKS);
@@ -79,22 +81,26 @@ constexpr CompressWs compress_ws_c(uint64_t n) {
     return w;
 }
 
-CompressWs compress_ws(uint64_t n) { return compress_ws_c(n); }
+CompressWs compress_ws(uint64_t n, uint64_t nb_fmt) { return compress_ws_c(n, nb_fmt); }
 
 DecompressWs decompress_ws(uint64_t n) {
     DecompressWs w;
     const uint64_t nb = cdiv(n, L);
     w.ntiles = (uint32_t)cdiv(nb, 256);   // the fused decoder's 8192-point tiles
+    // Per-tile counts and prefixes cover the linear tiles and the payload
+    // tiles (256 blocks) of either format: a format-v2 stream has at most n
+    // blocks, whatever the grid's shape (the host does not know it here).
+    const uint64_t tcap = hmax<uint64_t>(w.ntiles, cdiv(n, 256));
     w.rank_tiles = (uint32_t)cdiv(cdiv(n + 2, L), TILE_BLOCKS) + 1;
     w.sad_cap = (uint32_t)n;
     uint64_t o = 0;
     w.ctrl = o; o = a256(o + CTRL_BYTES);
     w.rdesc = o; o = a256(o + 16ull * (w.rank_tiles + 1));
     w.flags = o; o = a256(o + 4ull * (w.ntiles + 1));
-    w.tile_w = o; o = a256(o + 4ull * (w.ntiles + 1));
-    w.tile_c = o; o = a256(o + 4ull * (w.ntiles + 1));
-    w.pay_pre = o; o = a256(o + 8ull * (w.ntiles + 1));
-    w.cp_pre = o; o = a256(o + 4ull * (w.ntiles + 1));
+    w.tile_w = o; o = a256(o + 4ull * (tcap + 1));
+    w.tile_c = o; o = a256(o + 4ull * (tcap + 1));
+    w.pay_pre = o; o = a256(o + 8ull * (tcap + 1));
+    w.cp_pre = o; o = a256(o + 4ull * (tcap + 1));
     w.cp_idx = o; o = a256(o + 4ull * (n + 2));
     w.delta = o; o = a256(o + 4ull * (n + 2));
     w.newv = o; o = a256(o + 4ull * (n + 2));
@@ -104,8 +110,9 @@ DecompressWs decompress_ws(uint64_t n) {
     return w;
 }
 
-__global__ void k_init_ctrl(Ctrl* c, Geo g, int rel, double eb, uint32_t flags, int sweeps) {
+__global__ void k_init_ctrl(Ctrl* c, Geo g, int rel, double eb, uint32_t flags, int sweeps, uint32_t nb_fmt) {
     c->g = g;
+    c->nb_fmt = nb_fmt;
     c->rel = rel;
     c->eb = eb;
     c->flags = flags;
@@ -238,7 +245,7 @@ const char* toposzp_status_string(toposzp_status s) {
 uint64_t toposzp_compress_bound(int ndim, const uint64_t dims[3]) {
     Geo g;
     if (!make_geo(ndim, dims, g)) return 0;
-    const uint64_t n = g.n, nb = g.nb, nbd = cdiv(n + 2, L);
+    const uint64_t n = g.n, nb = hmax<uint64_t>(g.nb, tile_blocks(ndim, g.nx, g.ny, g.nz)), nbd = cdiv(n + 2, L);
     return HDR + 16 * 10 + 4 * cdiv(nb, 32) + nb + 4 * nb + 4 * cdiv(n, 16) + 4 * (L + 1) * nb +
            4 * cdiv(nbd, 32) + nbd + 4 * nbd + 4 * (L + 1) * nbd;
 }
@@ -246,7 +253,7 @@ uint64_t toposzp_compress_bound(int ndim, const uint64_t dims[3]) {
 uint64_t toposzp_compress_workspace_size(int ndim, const uint64_t dims[3]) {
     Geo g;
     if (!make_geo(ndim, dims, g)) return 0;
-    return compress_ws(g.n).end;
+    return hmax<uint64_t>(compress_ws(g.n).end, compress_ws(g.n, tile_blocks(ndim, g.nx, g.ny, g.nz)).end);
 }
 
 uint64_t toposzp_decompress_workspace_size(int ndim, const uint64_t dims[3]) {
@@ -279,12 +286,14 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     if (!aligned16(field) || !aligned16(out) || !aligned16(workspace)) return TOPOSZP_ERR_INVALID_ARG;
     if (mode != TOPOSZP_EB_ABS && mode != TOPOSZP_EB_REL) return TOPOSZP_ERR_INVALID_ARG;
     if (!(eb > 0.0) || !std::isfinite(eb)) return TOPOSZP_ERR_INVALID_ARG;
-    if (p.flags & ~(TOPOSZP_NO_TOPO | TOPOSZP_RBF_SOLVE)) return TOPOSZP_ERR_INVALID_ARG;
+    if (p.flags & ~(TOPOSZP_NO_TOPO | TOPOSZP_RBF_SOLVE | TOPOSZP_TILE_BLOCKS)) return TOPOSZP_ERR_INVALID_ARG;
     if (p.rs_sweeps > 16) return TOPOSZP_ERR_INVALID_ARG;
     if (p.rbf_k != 0 && p.rbf_k != 3 && p.rbf_k != 5 && p.rbf_k != 7) return TOPOSZP_ERR_INVALID_ARG;
     if (!(p.rbf_sigma >= 0.0f) || !std::isfinite(p.rbf_sigma)) return TOPOSZP_ERR_INVALID_ARG;
     if (out_capacity < toposzp_compress_bound(ndim, dims)) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
-    const CompressWs w = compress_ws(g.n);
+    const bool tiles = (p.flags & TOPOSZP_TILE_BLOCKS) != 0;
+    const uint32_t nbf = tiles ? (uint32_t)tile_blocks(ndim, g.nx, g.ny, g.nz) : g.nb;
+    const CompressWs w = compress_ws(g.n, tiles ? nbf : 0);
     if (ws_bytes < w.end) return TOPOSZP_ERR_BUFFER_TOO_SMALL;
     select_tuning(ndim, g.n);
 
@@ -298,18 +307,18 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
     const bool topo = !(p.flags & TOPOSZP_NO_TOPO);
     const int sms = sm_count();
     Layout lo;
-    make_layout(g.n, g.nb, topo, 0, 0, 0, lo);
+    make_layout(g.n, nbf, topo, 0, 0, 0, lo);
     uint32_t* labels = reinterpret_cast<uint32_t*>(o + lo.s6);
 
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     cudaMemsetAsync(ws, 0, w.os_desc_a, st);   // control block, per-tile counts, sort histograms and counters
-    k_init_ctrl<<<1, 1, 0, st>>>(c, g, mode == TOPOSZP_EB_REL ? 1 : 0, eb, p.flags, (int)p.rs_sweeps);
+    k_init_ctrl<<<1, 1, 0, st>>>(c, g, mode == TOPOSZP_EB_REL ? 1 : 0, eb, p.flags, (int)p.rs_sweeps, nbf);
     stage(0, st);
     launch_range_cd(field, g, c, labels, topo, sms, st);
     stage(1, st);
     launch_qparams(c, status, st);
     launch_encode_field(field, labels, c, tcnt, reinterpret_cast<uint32_t*>(ws + w.tmpM), w.agg - w.tmpM, o, lo,
-                        listM, listm, topo, g.nb, sms, status, st);
+                        listM, listm, topo, g, nbf, tiles, sms, status, st);
     stage(2, st);
     if (topo) {
         SortWs sw;
@@ -358,7 +367,9 @@ toposzp_status toposzp_inspect(const void* header_host, uint64_t header_bytes, t
     const uint8_t* h = reinterpret_cast<const uint8_t*>(header_host);
     auto u32 = [&](int off) { uint32_t v; std::memcpy(&v, h + off, 4); return v; };
     auto u64 = [&](int off) { uint64_t v; std::memcpy(&v, h + off, 8); return v; };
-    if (u32(0) != MAGIC || u32(4) != VERSION || u32(12) != L) return TOPOSZP_ERR_CORRUPT_STREAM;
+    const uint32_t version = u32(4);
+    if (u32(0) != MAGIC || (version != VERSION && version != VERSION_TILES) || u32(12) != L)
+        return TOPOSZP_ERR_CORRUPT_STREAM;
     std::memset(info, 0, sizeof(*info));
     info->ndim = (int)u32(8);
     info->dims[0] = u64(16);
@@ -385,7 +396,10 @@ toposzp_status toposzp_inspect(const void* header_host, uint64_t header_bytes, t
     const bool topo = !(flags & TOPOSZP_NO_TOPO);
     float sigma;
     std::memcpy(&sigma, h + 92, 4);
-    bool ok = nb == cdiv(n, L) && flags <= (TOPOSZP_NO_TOPO | TOPOSZP_RBF_SOLVE) && sweeps >= 1u && sweeps <= 16u;
+    const uint64_t nb_want = version == VERSION_TILES
+                                 ? tile_blocks(info->ndim, info->dims[0], info->dims[1], info->dims[2])
+                                 : cdiv(n, L);
+    bool ok = nb == nb_want && flags <= (TOPOSZP_NO_TOPO | TOPOSZP_RBF_SOLVE) && sweeps >= 1u && sweeps <= 16u;
     ok = ok && (!(flags & TOPOSZP_RBF_SOLVE) || (std::isfinite(sigma) && sigma > 0.0f));
     ok = ok && (rk == 3 || rk == 5 || rk == 7) && std::isfinite(w_f) && w_f > 0.0f && std::isfinite(h_f) &&
          h_f >= 0.0f;
@@ -399,7 +413,7 @@ toposzp_status toposzp_inspect(const void* header_host, uint64_t header_bytes, t
         return TOPOSZP_ERR_CORRUPT_STREAM;
     info->total_size = u64(200);
     std::memcpy(&info->eps, h + 56, 8);
-    info->flags = u32(40);
+    info->flags = u32(40) | (version == VERSION_TILES ? TOPOSZP_TILE_BLOCKS : 0u);
     info->k_min = u64(120);
     info->k_max = u64(128);
     info->k_saddle = u64(136);
@@ -432,6 +446,10 @@ toposzp_status toposzp_decompress(const void* in, uint64_t in_size, float* out, 
                        reinterpret_cast<unsigned long long*>(ws + w.pay_pre), reinterpret_cast<uint32_t*>(ws + w.cp_pre),
                        rtile, w.ntiles, sms, status, st);
     launch_decode_ranks(src, c, rtile, reinterpret_cast<int32_t*>(ws + w.delta), n_out, sms, status, st);
+    // format v2's S1 (returns at once on a format-v1 stream, whose S1 is in the fused decoder)
+    launch_decode_tiles(src, c, out, reinterpret_cast<unsigned long long*>(ws + w.pay_pre),
+                        reinterpret_cast<uint32_t*>(ws + w.cp_pre), reinterpret_cast<uint32_t*>(ws + w.cp_idx), n_out,
+                        sms, status, st);
     stage(6, st);
     launch_decode_fused(src, c, out, reinterpret_cast<unsigned long long*>(ws + w.pay_pre),
                         reinterpret_cast<uint32_t*>(ws + w.cp_pre), reinterpret_cast<int32_t*>(ws + w.delta),

@@ -13,9 +13,13 @@ namespace tsz {
 constexpr uint32_t L = 32;               // block length of the B stage (Section II-C)
 constexpr uint32_t HDR = 256;            // stream header bytes
 constexpr uint32_t MAGIC = 0x505A5354u;  // "TSZP"
-constexpr uint32_t VERSION = 1;
+constexpr uint32_t VERSION = 1;         // blocks of L consecutive points
+constexpr uint32_t VERSION_TILES = 2;   // format v2: tile-shaped blocks (see tile_shape)
 constexpr uint32_t FLAG_NO_TOPO = 1;
 constexpr uint32_t FLAG_RBF_SOLVE = 2;   // RS^ by the literal interpolant's weights, unclamped
+// Format v2 in the control block's flags (the stream itself says version 2;
+// the header's flag word keeps only the two bits above).
+constexpr uint32_t FLAG_TILE_BLOCKS = 4;
 constexpr int RBF_MAX_NODES = 122;       // |N_r(p) \ {p}| for r = 3 in 3D
 
 // labels of Section IV-A(1): r = 00, m = 01, s = 10, M = 11
@@ -39,6 +43,8 @@ constexpr uint32_t SPIN_LIMIT = 1u << 22;
 __host__ __device__ constexpr inline uint64_t cdiv(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
 template <class T>
 __host__ __device__ inline T hmin(T a, T b) { return a < b ? a : b; }
+template <class T>
+__host__ __device__ inline T hmax(T a, T b) { return a < b ? b : a; }
 __host__ __device__ inline uint64_t align16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
 
 // Division by a run-time invariant d by multiply-high and shifts (the
@@ -76,6 +82,18 @@ struct Geo {
     uint32_t nb;           // blocks of L
     FastDiv fx, fy;        // division by nx and by ny
 };
+
+// Format v2 blocks: L = 32 points shaped 8 x 4 in 2D and 4 x 4 x 2 in 3D (x
+// fastest), in raster order over the block grid; element e of a block sits
+// at (e mod BX, (e / BX) mod BY, e / (BX BY)) inside it.
+template <int ND>
+struct TileShape {
+    static constexpr uint32_t BX = ND == 3 ? 4u : 8u, BY = 4u, BZ = ND == 3 ? 2u : 1u;
+};
+__host__ __device__ inline uint64_t tile_blocks(int ndim, uint64_t nx, uint64_t ny, uint64_t nz) {
+    const uint64_t bx = ndim == 3 ? 4 : 8, by = 4, bz = ndim == 3 ? 2 : 1;
+    return ((nx + bx - 1) / bx) * ((ny + by - 1) / by) * ((nz + bz - 1) / bz);
+}
 
 __host__ __device__ inline void geo_divs(Geo& g) {
     g.fx = make_fastdiv(g.nx);
@@ -144,6 +162,7 @@ struct Ctrl {
     Layout lo;
     float g_rbf[9];
     float rbf_alpha[RBF_MAX_NODES];   // FLAG_RBF_SOLVE: the interpolant's weights at p, table order
+    uint32_t nb_fmt;                  // blocks of the stream (g.nb in format v1, the tiles in v2)
 };
 
 // ------------------------------------------------------------------ helpers

@@ -474,7 +474,14 @@ constexpr int TILE_POS_BITS = 13;                    // 8192 points per tile
 static_assert(ENC_TILE_BLOCKS * 32 == (1 << TILE_POS_BITS), "tile size");
 static_assert(ENC_TILE_BLOCKS * ENC_ROW >= TILE_PAY, "payload staging");
 
-template <bool TOPO>
+//
+// CODEC = false (format v2, whose payload k_encode_tiles writes): the same
+// pass over the linear tiles without the payload -- the extremum lists, the
+// tile's extremum count, and the residual sum of the RBF parameters (always
+// that of blocks of 32 consecutive points).  The grid may then hold more
+// CTAs than linear tiles (as many as the format's payload tiles): those only
+// zero their count.
+template <bool TOPO, bool CODEC>
 __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict__ a,
                                                          const uint32_t* __restrict__ labels, Ctrl* c,
                                                          uint2* tcnt, EncOut o, uint2* listM, uint2* listm,
@@ -490,6 +497,10 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
     const uint32_t tile = blockIdx.x;
     const uint32_t b = tile * ENC_TILE_BLOCKS + t;   // this thread's block
     const uint64_t p0 = (uint64_t)tile * (ENC_TILE_BLOCKS * 32);
+    if (!CODEC && p0 >= n) {
+        if (t == 0) tcnt[tile] = make_uint2(0u, 0u);
+        return;
+    }
     const uint64_t left = (uint64_t)n - p0;
     const uint32_t npts = left < (uint64_t)(ENC_TILE_BLOCKS * 32) ? (uint32_t)left : (uint32_t)(ENC_TILE_BLOCKS * 32);
     if (t == 0) s_sum = 0;
@@ -537,7 +548,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
     }
     const uint32_t w = 32u - __clz(orr);   // bit length of max |d|
     const uint32_t W = __reduce_max_sync(FULL, w);   // the warp's widest block: picks the transpose
-    const uint32_t words = (b < nb && w) ? 1u + w : 0u;
+    const uint32_t words = (CODEC && b < nb && w) ? 1u + w : 0u;
     uint32_t xmM = 0, xmm = 0;   // extremum masks (bit e: element e), maxima / minima
     if (TOPO) {
         const uint32_t lo0 = lw.x & 0x55555555u, hi0 = (lw.x >> 1) & 0x55555555u;
@@ -620,6 +631,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
             }
         }
     }
+    if (!CODEC) return;
     __syncthreads();   // the staged values are no longer read: the buffer takes the payload
     if (words) {
         uint32_t* dst = s_buf + ow;
@@ -633,6 +645,120 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
     {   // constant-block bits: one word per warp of blocks
         const uint32_t cb = __ballot_sync(FULL, b < nb && w == 0);
         if (lane == 0 && (b >> 5) < (nb + 31) / 32) o.cbits[b >> 5] = cb;
+    }
+    __syncthreads();
+    uint32_t* slot = o.pay + (size_t)tile * TILE_PAY;
+    for (uint32_t k = t; k < tw; k += 256) slot[k] = s_buf[k];
+}
+
+// Format v2 field encoder (tile-shaped blocks, Section II-C's B + LZ + BE on
+// 8 x 4 / 4 x 4 x 2 tiles): one payload tile of 256 blocks per CTA, one block
+// per thread.  The block's 32 values are read from the field (positions
+// outside the domain take the nearest inside point, each coordinate
+// clamped) and quantised; q' = q - q_0.  Two residual sets, in 32-bit
+// modular arithmetic: the chain in element order, d_e = q'_e - q'_{e-1},
+// and the block-local Lorenzo differences (inclusion-exclusion over the
+// preceding corners, q' = 0 outside the block).  The one with the smaller
+// widest residual is coded (Lorenzo only when strictly smaller), its choice
+// in bit 7 of the width byte; sign and magnitude planes as in format v1.
+// The payload goes to the tile's scratch slot and the tile's word count to
+// tcnt[tile].x; the linear pass (CODEC = false) has written .y already.
+template <int ND>
+__global__ void __launch_bounds__(256, 4) k_encode_tiles(const float* __restrict__ a, Ctrl* c, uint2* tcnt,
+                                                         EncOut o, int* status) {
+    using TS = TileShape<ND>;
+    constexpr uint32_t BX = TS::BX, BY = TS::BY, BZ = TS::BZ;
+    __shared__ __align__(16) uint32_t s_buf[TILE_PAY];
+    __shared__ uint32_t s_wsum[8];
+    if (*status) return;
+    const Geo g = c->g;
+    const uint32_t nbf = c->nb_fmt;
+    const float r = c->r_f;
+    const uint32_t t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t tile = blockIdx.x;
+    const uint32_t b = tile * ENC_TILE_BLOCKS + t;
+    uint32_t mag[32];
+    uint32_t sgn = 0, w = 0, sel = 0;
+    int32_t first = 0;
+    if (b < nbf) {
+        const uint32_t nbx = (g.nx + BX - 1) / BX, nby = (g.ny + BY - 1) / BY;
+        const uint32_t gx = b % nbx, gy = (b / nbx) % nby, gz = b / (nbx * nby);
+        uint32_t qp[32];
+#pragma unroll
+        for (int e = 0; e < 32; e++) {
+            const uint32_t x = min(gx * BX + (uint32_t)e % BX, g.nx - 1);
+            const uint32_t y = min(gy * BY + ((uint32_t)e / BX) % BY, g.ny - 1);
+            const uint32_t z = min(gz * BZ + (uint32_t)e / (BX * BY), g.nz - 1);
+            qp[e] = (uint32_t)quantize(__ldg(a + (size_t)x + (size_t)g.nx * (y + (size_t)g.ny * z)), r);
+        }
+        first = (int32_t)qp[0];
+#pragma unroll
+        for (int e = 31; e >= 0; e--) qp[e] -= qp[0];
+        uint32_t mx0 = 0, mx1 = 0;
+#pragma unroll
+        for (int e = 0; e < 32; e++) {
+            const uint32_t dc = e ? qp[e] - qp[e - 1] : 0u;
+            const uint32_t ac = (int32_t)dc < 0 ? 0u - dc : dc;
+            mx0 = max(mx0, ac);
+        }
+#pragma unroll
+        for (int e = 0; e < 32; e++) {
+            const uint32_t ex = (uint32_t)e % BX, ey = ((uint32_t)e / BX) % BY, ez = (uint32_t)e / (BX * BY);
+            uint32_t du = 0;
+#pragma unroll
+            for (uint32_t sm = 0; sm < 8; sm++) {
+                const uint32_t sx = sm & 1u, sy = (sm >> 1) & 1u, sz = (sm >> 2) & 1u;
+                if (sx > ex || sy > ey || sz > ez) continue;
+                const uint32_t v = qp[(ex - sx) + BX * ((ey - sy) + BY * (ez - sz))];
+                du = (sx + sy + sz) & 1u ? du - v : du + v;
+            }
+            mag[e] = du;   // the Lorenzo residual, signed, for now
+            const uint32_t al = (int32_t)du < 0 ? 0u - du : du;
+            mx1 = max(mx1, al);
+        }
+        sel = mx1 < mx0 ? 1u : 0u;
+        const uint32_t mx = sel ? mx1 : mx0;
+        w = 32u - __clz(mx);
+#pragma unroll
+        for (int e = 0; e < 32; e++) {
+            const uint32_t d = sel ? mag[e] : (e ? qp[e] - qp[e - 1] : 0u);
+            const bool neg = (int32_t)d < 0;
+            if (neg) sgn |= 1u << e;
+            mag[e] = neg ? 0u - d : d;
+        }
+    }
+    const uint32_t W = __reduce_max_sync(FULL, w);
+    const uint32_t words = (b < nbf && w) ? 1u + w : 0u;
+    uint32_t iw = words;
+#pragma unroll
+    for (int of = 1; of < 32; of <<= 1) {
+        const uint32_t a0 = __shfl_up_sync(FULL, iw, of);
+        if (lane >= (uint32_t)of) iw += a0;
+    }
+    if (lane == 31) s_wsum[warp] = iw;
+    __syncthreads();
+    uint32_t ow = iw - words, tw = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        if (k < (int)warp) ow += s_wsum[k];
+        tw += s_wsum[k];
+    }
+    if (words) {
+        uint32_t* dst = s_buf + ow;
+        dst[0] = sgn;
+        values_to_planes(W, w, mag, [&](int q, uint32_t pl) { dst[1 + q] = pl; });
+    }
+    if (b < nbf) {
+        o.width[b] = (uint8_t)(w | sel << 7);
+        o.first[b] = first;
+    }
+    {
+        const uint32_t cb = __ballot_sync(FULL, b < nbf && w == 0);
+        if (lane == 0 && (b >> 5) < (nbf + 31) / 32) o.cbits[b >> 5] = cb;
+    }
+    if (t == 0) {
+        reinterpret_cast<uint32_t*>(tcnt + tile)[0] = tw;
+        if (tw) atomicAdd(&c->sl_tile[tile / slice_len(gridDim.x)][0], (unsigned long long)tw);
     }
     __syncthreads();
     uint32_t* slot = o.pay + (size_t)tile * TILE_PAY;
@@ -703,7 +829,7 @@ __global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restri
     const uint32_t nbd = (uint32_t)cdiv(k, L);
     const uint32_t ntiles = (nbd + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;
     Layout lo;
-    make_layout(c->g.n, c->g.nb, true, c->pay_words, k, 0, lo);
+    make_layout(c->g.n, c->nb_fmt, true, c->pay_words, k, 0, lo);
     uint32_t* cbits = reinterpret_cast<uint32_t*>(out + lo.r1);
     uint8_t* width = out + lo.r2;
     int32_t* first = reinterpret_cast<int32_t*>(out + lo.r4);
@@ -813,7 +939,7 @@ __global__ void __launch_bounds__(256) k_rank_copy(const uint32_t* __restrict__ 
     const uint32_t nbd = (uint32_t)cdiv(k, L);
     const uint32_t ntiles = (nbd + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;
     Layout lo;
-    make_layout(c->g.n, c->g.nb, true, c->pay_words, k, 0, lo);
+    make_layout(c->g.n, c->nb_fmt, true, c->pay_words, k, 0, lo);
     uint32_t* pay = reinterpret_cast<uint32_t*>(out + lo.r5);
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint32_t p0 = tpre[t].x, cnt = tpre[t + 1].x - p0;
@@ -1260,11 +1386,12 @@ __global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rb
     const bool topo = !(c->flags & FLAG_NO_TOPO);
     const uint64_t k = topo ? c->k_total : 0;
     Layout lo;
-    make_layout(g.n, g.nb, topo, c->pay_words, k, topo ? c->rank_words : 0, lo);
+    const uint32_t nbf = c->nb_fmt;   // blocks of the stream's format
+    make_layout(g.n, nbf, topo, c->pay_words, k, topo ? c->rank_words : 0, lo);
     // padding
-    zero_bytes(out, lo.s1 + 4 * cdiv(g.nb, 32), lo.s2);
-    zero_bytes(out, lo.s2 + g.nb, lo.s4);
-    zero_bytes(out, lo.s4 + 4ull * g.nb, lo.s6);
+    zero_bytes(out, lo.s1 + 4 * cdiv(nbf, 32), lo.s2);
+    zero_bytes(out, lo.s2 + nbf, lo.s4);
+    zero_bytes(out, lo.s4 + 4ull * nbf, lo.s6);
     zero_bytes(out, lo.s6 + (topo ? 4 * cdiv(g.n, 16) : 0), lo.s5);
     if (topo) {
         uint64_t nbd = cdiv(k, L);
@@ -1280,7 +1407,7 @@ __global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rb
     uint8_t* h = out;
     for (int i = 0; i < (int)HDR; i += 4) put<uint32_t>(h, i, 0u);
     put<uint32_t>(h, 0, MAGIC);
-    put<uint32_t>(h, 4, VERSION);
+    put<uint32_t>(h, 4, (c->flags & FLAG_TILE_BLOCKS) ? VERSION_TILES : VERSION);
     put<uint32_t>(h, 8, (uint32_t)g.ndim);
     put<uint32_t>(h, 12, L);
     put<uint64_t>(h, 16, g.nx);
@@ -1300,7 +1427,7 @@ __global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rb
     put<float>(h, 92, sigma);
     put<uint32_t>(h, 96, (uint32_t)c->rs_sweeps);
     put<uint64_t>(h, 104, g.n);
-    put<uint64_t>(h, 112, g.nb);
+    put<uint64_t>(h, 112, nbf);
     put<uint64_t>(h, 120, topo ? c->cnt_min : 0ull);
     put<uint64_t>(h, 128, topo ? c->cnt_max : 0ull);
     put<uint64_t>(h, 136, topo ? c->k_sad : 0ull);
@@ -1418,18 +1545,27 @@ __global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsi
 
 void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2* tcnt, uint32_t* scratch,
                          uint64_t region_bytes, uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo,
-                         uint32_t nb, int sms, int* status, cudaStream_t st) {
+                         const Geo& g, uint32_t nb_fmt, bool tiles, int sms, int* status, cudaStream_t st) {
     EncOut o{reinterpret_cast<uint32_t*>(out + lo.s1), out + lo.s2,
              reinterpret_cast<int32_t*>(out + lo.s4), scratch};
-    const uint32_t ntiles = (nb + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS;   // one tile per CTA
+    // one tile per CTA: the linear 8192-point tiles, or in format v2 as many
+    // as either the linear tiles or the payload tiles need
+    const uint32_t ntiles = hmax<uint32_t>((g.nb + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS,
+                                           (nb_fmt + ENC_TILE_BLOCKS - 1) / ENC_TILE_BLOCKS);
     if (topo) {
         // the rank mode (key bitmaps or sort) is decided here, so the encoder can set the bits
         const unsigned long long slot_bytes = 4ull * TILE_PAY * ntiles;
         k_bm_zero<<<(uint32_t)sms * 8, 256, 0, st>>>(c, scratch, region_bytes, slot_bytes, g_tuning.rank_bitmap,
                                                       status);
-        k_encode_field<true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+        if (tiles) k_encode_field<true, false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+        else k_encode_field<true, true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
     } else {
-        k_encode_field<false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+        if (tiles) k_encode_field<false, false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+        else k_encode_field<false, true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+    }
+    if (tiles) {
+        if (g.ndim == 3) k_encode_tiles<3><<<ntiles, 256, 0, st>>>(a, c, tcnt, o, status);
+        else k_encode_tiles<2><<<ntiles, 256, 0, st>>>(a, c, tcnt, o, status);
     }
     k_enc_tile_scan<<<SCAN_SLICES, 1024, 0, st>>>(tcnt, ntiles, c, status);
     uint32_t cg = hmin<uint32_t>(ntiles, (uint32_t)sms * 8);

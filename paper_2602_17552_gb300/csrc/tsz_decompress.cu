@@ -29,6 +29,17 @@ namespace tsz {
 constexpr int DT_WARPS = 8;
 constexpr int DT_BLOCKS = DT_WARPS * 32;
 
+// The decoder's tiles: linear tiles of 8192 points (labels, extremum lists,
+// the wavefront) and payload tiles of 256 blocks.  In format v1 they are the
+// same tiles; in format v2 the per-tile counts and prefixes cover the larger
+// number of the two.
+__host__ __device__ inline uint32_t lin_tiles(const Geo& g) {
+    return (uint32_t)((g.n + (uint64_t)DT_BLOCKS * 32 - 1) / ((uint64_t)DT_BLOCKS * 32));
+}
+__host__ __device__ inline uint32_t all_tiles(const Geo& g) {
+    return hmax<uint32_t>(lin_tiles(g), (g.nb + DT_BLOCKS - 1) / DT_BLOCKS);
+}
+
 // Label word wi with the codes of points >= n cleared (a valid stream has
 // them zero already; clearing keeps every count consistent on any stream).
 __device__ __forceinline__ uint32_t label_word(const uint32_t* labels, uint32_t wi, uint32_t n) {
@@ -47,11 +58,13 @@ __device__ __forceinline__ T get(const uint8_t* h, int off) {
 
 __device__ void parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ctrl* c, int* status,
                              uint32_t test_hold) {
-    if (in_size < HDR || get<uint32_t>(in, 0) != MAGIC || get<uint32_t>(in, 4) != VERSION ||
+    const uint32_t version = in_size >= HDR ? get<uint32_t>(in, 4) : 0u;
+    if (in_size < HDR || get<uint32_t>(in, 0) != MAGIC || (version != VERSION && version != VERSION_TILES) ||
         get<uint32_t>(in, 12) != L) {
         set_status(status, ST_CORRUPT);
         return;
     }
+    const bool tiles = version == VERSION_TILES;
     const int ndim = (int)get<uint32_t>(in, 8);
     const uint64_t nx = get<uint64_t>(in, 16), ny = get<uint64_t>(in, 24), nz = get<uint64_t>(in, 32);
     const uint32_t flags = get<uint32_t>(in, 40);
@@ -59,8 +72,9 @@ __device__ void parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out
               ny < (1ull << 31) && nz < (1ull << 31) && (ndim == 3 || nz == 1) &&
               flags <= (FLAG_NO_TOPO | FLAG_RBF_SOLVE);
     const uint64_t n = ok ? nx * ny : 0;
-    ok = ok && n < (1ull << 31) && n * nz < (1ull << 31) && n * nz == n_out &&
-         get<uint64_t>(in, 104) == n_out && get<uint64_t>(in, 112) == cdiv(n_out, L);
+    ok = ok && n < (1ull << 31) && n * nz < (1ull << 31) && n * nz == n_out && get<uint64_t>(in, 104) == n_out;
+    const uint64_t nb = get<uint64_t>(in, 112);
+    ok = ok && nb == (tiles ? tile_blocks(ndim, nx, ny, nz) : cdiv(n_out, L));
     const float w_f = get<float>(in, 64), h_f = get<float>(in, 72);
     const int32_t rk = (int32_t)get<uint32_t>(in, 88);
     const uint32_t sweeps = get<uint32_t>(in, 96);
@@ -72,7 +86,6 @@ __device__ void parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out
     ok = ok && (!(flags & FLAG_RBF_SOLVE) || (isfinite(sigma) && sigma > 0.0f));
     ok = ok && (rk == 3 || rk == 5 || rk == 7) && sweeps >= 1 && sweeps <= 16;
     ok = ok && kmin <= cdiv(n_out, 2) && kmax <= cdiv(n_out, 2) && (topo || (kmin == 0 && kmax == 0));
-    const uint64_t nb = cdiv(n_out, L);
     ok = ok && pay <= nb * (L + 1) && rpay <= cdiv(kmin + kmax, L) * (L + 1);
     if (!ok) {
         set_status(status, ST_CORRUPT);
@@ -97,7 +110,8 @@ __device__ void parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out
     g.nb = (uint32_t)nb;
     geo_divs(g);
     c->g = g;
-    c->flags = flags;
+    c->flags = flags | (tiles ? FLAG_TILE_BLOCKS : 0u);
+    c->nb_fmt = (uint32_t)nb;
     c->w_f = w_f;
     c->h_f = h_f;
     c->rbf_k = rk;
@@ -742,7 +756,8 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
     const bool topo = !(c->flags & FLAG_NO_TOPO);
     const uint8_t* widths = in + lo.s2;
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(in + lo.s6);
-    const uint32_t ntiles = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
+    const uint32_t ntiles = all_tiles(g);
+    const bool tiles = c->flags & FLAG_TILE_BLOCKS;
     const int lane = threadIdx.x & 31;
     bool corrupt = false;
     for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < ntiles; t += (gridDim.x * blockDim.x) >> 5) {
@@ -751,8 +766,10 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
         for (int j = 0; j < DT_BLOCKS / 32; j++) {
             const uint32_t b = t * DT_BLOCKS + j * 32 + lane;
             if (b < g.nb) {
-                uint32_t w = __ldg(widths + b);
-                if (w > 32) { corrupt = true; w = 0; }
+                // format v2: bit 7 picks the block's predictor (never with w = 0)
+                const uint32_t wb = __ldg(widths + b);
+                uint32_t w = tiles ? (wb & 0x7Fu) : wb;
+                if (w > 32 || (tiles && (wb >> 7) && w == 0)) { corrupt = true; w = 0; }
                 words += w ? 1u + w : 0u;
             }
         }
@@ -821,7 +838,7 @@ __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t*
             if (rw != c->rank_words) set_status(status, ST_CORRUPT);
         }
     }
-    const uint32_t ntiles = (c->g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
+    const uint32_t ntiles = all_tiles(c->g);
     unsigned long long tw, tc;
     slice_scan_pairs(
         ntiles, c->sl_tile, [&](uint32_t i) { return make_uint2(tile_w[i], tile_c[i]); },
@@ -1258,7 +1275,9 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
     const Geo& g = S.g;
     const Layout& lo = S.lo;
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
-    const uint32_t ntiles = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
+    const uint32_t ntiles = lin_tiles(g);
+    // format v2: S1 ran before (k_decode_tiles); S2 starts on a finished field
+    const bool s1 = !(c->flags & FLAG_TILE_BLOCKS);
     const uint32_t H = TOPO ? fused_reach(g, ntiles) : 0u;
     // stage lag: the reach H plus some slack, so that a stage rarely waits for
     // tiles that CTAs took just before this one
@@ -1273,7 +1292,7 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
     const uint32_t t = s_tile;
     __syncthreads();
     if (t >= total) break;
-    if (t < ntiles) {
+    if (s1 && t < ntiles) {
         stage_decode<TOPO>(A, g, lo, t, s_pay, s_w, s_cp, corrupt);
         if (t + 1 != S.hold) mark_done(c, A.flags, 1, t, ntiles);
         else __syncthreads();   // the test hook: this tile is never published
@@ -1281,7 +1300,7 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
     if (TOPO) {
         const long long s2 = (long long)t - Lg, s3 = (long long)t - 2 * Lg, s4 = (long long)t - 3 * Lg;
         if (s2 >= 0 && s2 < ntiles) {
-            wait_front(c, A.flags, 1, (uint32_t)hmin<long long>(s2 + H, ntiles - 1) + 1, ntiles, A.status);
+            if (s1) wait_front(c, A.flags, 1, (uint32_t)hmin<long long>(s2 + H, ntiles - 1) + 1, ntiles, A.status);
             stage_extrema(A, g, labels, (uint32_t)s2, restored, skipped);
             mark_done(c, A.flags, 2, (uint32_t)s2, ntiles);
         }
@@ -1325,6 +1344,7 @@ __global__ void __launch_bounds__(256, 4) k_decode_stage(FusedArgs A) {
     Ctrl* c = A.c;
     const bool topo = !(c->flags & FLAG_NO_TOPO);
     if (K > 1 && !topo) return;
+    if (K == 1 && (c->flags & FLAG_TILE_BLOCKS)) return;   // format v2: k_decode_tiles is S1
     if (threadIdx.x == 0) {
         S.g = c->g;
         S.lo = c->lo;
@@ -1333,7 +1353,7 @@ __global__ void __launch_bounds__(256, 4) k_decode_stage(FusedArgs A) {
     const Geo& g = S.g;
     const Layout& lo = S.lo;
     const uint32_t* labels = reinterpret_cast<const uint32_t*>(A.in + lo.s6);
-    const uint32_t ntiles = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS;
+    const uint32_t ntiles = lin_tiles(g);
     bool corrupt = false;
     uint32_t restored = 0, skipped = 0;   // per thread: at most the extrema it handled
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -1361,6 +1381,145 @@ __global__ void __launch_bounds__(256, 4) k_decode_stage(FusedArgs A) {
             if (skipped) atomicAdd(&c->stat_skipped, (unsigned long long)skipped);
         }
     }
+}
+
+// ------------------------------------------------------- format v2: S1
+//
+// S1 for tile-shaped blocks (the inverse of k_encode_tiles): one payload tile
+// of 256 blocks per CTA and step, one block per thread.  The tile's payload
+// is staged in shared memory as in stage_decode; a thread rebuilds its
+// block's residuals from the planes, undoes the coded predictor in 32-bit
+// modular arithmetic (the chain: a prefix sum in element order; Lorenzo:
+// prefix sums along x, then y, then z), adds q_0, dequantises and writes the
+// points of the block that lie inside the grid.  For each linear tile the
+// extremum positions go to cp_idx as S1 of format v1 writes them.  A
+// format-v1 stream returns at once (the fused decoder's S1 decodes it).
+template <int ND>
+__device__ void tiles_decode_one(const uint8_t* in, const Ctrl* c, const Geo& g, const Layout& lo, float* out,
+                                 const unsigned long long* pay_pre, uint32_t t, uint32_t* s_pay, uint32_t* s_w,
+                                 bool& corrupt) {
+    using TS = TileShape<ND>;
+    constexpr uint32_t BX = TS::BX, BY = TS::BY, BZ = TS::BZ;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint8_t* widths = in + lo.s2;
+    const int32_t* firsts = reinterpret_cast<const int32_t*>(in + lo.s4);
+    const uint32_t* pay = reinterpret_cast<const uint32_t*>(in + lo.s5);
+    const uint32_t b = t * DT_BLOCKS + threadIdx.x;
+    uint32_t wb = 0;
+    int32_t first = 0;
+    if (b < g.nb) {
+        wb = __ldg(widths + b);
+        first = __ldg(firsts + b);
+    }
+    const unsigned long long P0 = pay_pre[t], P1 = pay_pre[t + 1];
+    uint32_t len = 0;
+    if (P1 >= P0 && P1 - P0 <= (unsigned long long)DT_BLOCKS * 33 && P1 <= c->pay_words) len = (uint32_t)(P1 - P0);
+    else corrupt = true;
+    for (uint32_t i = threadIdx.x; i < len; i += blockDim.x) s_pay[i] = __ldg(pay + P0 + i);
+    uint32_t w = wb & 0x7Fu, sel = wb >> 7;
+    if (w > 32 || (sel && w == 0)) w = 0, sel = 0;   // a damaged stream (the tile sums flag it)
+    const uint32_t words = w ? 1u + w : 0u;
+    uint32_t iw = words;
+#pragma unroll
+    for (int of = 1; of < 32; of <<= 1) {
+        const uint32_t a0 = __shfl_up_sync(FULL, iw, of);
+        if (lane >= (uint32_t)of) iw += a0;
+    }
+    if (lane == 31) s_w[warp] = iw;
+    __syncthreads();
+    uint32_t woff = iw - words;
+    for (uint32_t k = 0; k < warp; k++) woff += s_w[k];
+    uint32_t wv = w;
+    if (w && woff + 1 + w > len) {
+        corrupt = true;
+        wv = 0;
+    }
+    uint32_t v[32];
+    const uint32_t sgn = wv ? s_pay[woff] : 0u;
+    planes_to_values(__reduce_max_sync(FULL, wv), wv, [&](int r) { return s_pay[woff + 1 + r]; }, v);
+#pragma unroll
+    for (int e = 0; e < 32; e++) v[e] = (sgn >> e) & 1u ? 0u - v[e] : v[e];
+    if (sel) {
+#pragma unroll
+        for (int e = 0; e < 32; e++)
+            if ((uint32_t)e % BX) v[e] += v[e - 1];
+#pragma unroll
+        for (int e = 0; e < 32; e++)
+            if (((uint32_t)e / BX) % BY) v[e] += v[e - BX];
+#pragma unroll
+        for (int e = 0; e < 32; e++)
+            if ((uint32_t)e / (BX * BY)) v[e] += v[e - BX * BY];
+    } else {
+#pragma unroll
+        for (int e = 1; e < 32; e++) v[e] += v[e - 1];
+    }
+    if (b < g.nb) {
+        const float w_f = c->w_f;
+        const uint32_t nbx = (g.nx + BX - 1) / BX, nby = (g.ny + BY - 1) / BY;
+        const uint32_t gx = b % nbx, gy = (b / nbx) % nby, gz = b / (nbx * nby);
+#pragma unroll
+        for (int e = 0; e < 32; e++) {
+            const uint32_t x = gx * BX + (uint32_t)e % BX, y = gy * BY + ((uint32_t)e / BX) % BY,
+                           z = gz * BZ + (uint32_t)e / (BX * BY);
+            if (x < g.nx && y < g.ny && z < g.nz)
+                out[(size_t)x + (size_t)g.nx * (y + (size_t)g.ny * z)] =
+                    dequantize((int32_t)(v[e] + (uint32_t)first), w_f);
+        }
+    }
+    __syncthreads();   // s_pay and s_w are reused by the next step
+}
+
+// the extremum positions of linear tile t, in index order (bit 31: a maximum)
+__device__ void tiles_cp_list(const uint8_t* in, const Ctrl* c, const Geo& g, const Layout& lo,
+                              const uint32_t* cp_pre, uint32_t* cp_idx, uint32_t t, uint32_t* s_cp, bool& corrupt) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t* labels = reinterpret_cast<const uint32_t*>(in + lo.s6);
+    const uint32_t bl = t * DT_BLOCKS + threadIdx.x;   // a linear block of 32 points: two label words
+    const uint32_t l0 = label_word(labels, 2 * bl, g.n), l1 = label_word(labels, 2 * bl + 1, g.n);
+    uint32_t xm = compact16(l0) | compact16(l1) << 16;
+    const uint32_t xM = compact16(l0 & (l0 >> 1)) | compact16(l1 & (l1 >> 1)) << 16;
+    const uint32_t ncp = __popc(xm);
+    uint32_t ic = ncp;
+#pragma unroll
+    for (int of = 1; of < 32; of <<= 1) {
+        const uint32_t a1 = __shfl_up_sync(FULL, ic, of);
+        if (lane >= (uint32_t)of) ic += a1;
+    }
+    if (lane == 31) s_cp[warp] = ic;
+    __syncthreads();
+    uint32_t cpl = ic - ncp;
+    for (uint32_t k = 0; k < warp; k++) cpl += s_cp[k];
+    const unsigned long long k = c->k_total;
+    unsigned long long pos = cp_pre[t] + cpl;
+    while (xm) {
+        const int e = __ffs(xm) - 1;
+        xm &= xm - 1;
+        if (pos < k) cp_idx[pos] = (bl * 32u + (uint32_t)e) | ((xM >> e) & 1u) << 31;
+        else corrupt = true;
+        pos++;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_decode_tiles(const uint8_t* __restrict__ in, Ctrl* c, float* out,
+                                                      const unsigned long long* pay_pre, const uint32_t* cp_pre,
+                                                      uint32_t* cp_idx, int* status) {
+    __shared__ __align__(16) uint32_t s_pay[DT_BLOCKS * 33];
+    __shared__ uint32_t s_w[DT_WARPS], s_cp[DT_WARPS];
+    if (*status || !(c->flags & FLAG_TILE_BLOCKS)) return;
+    const Geo g = c->g;
+    const Layout lo = c->lo;
+    const bool topo = !(c->flags & FLAG_NO_TOPO);
+    const uint32_t npt = (g.nb + DT_BLOCKS - 1) / DT_BLOCKS, nlt = lin_tiles(g), nt = hmax(npt, nlt);
+    bool corrupt = false;
+    for (uint32_t t = blockIdx.x; t < nt; t += gridDim.x) {   // uniform across the CTA
+        if (t < npt) {
+            if (g.ndim == 3) tiles_decode_one<3>(in, c, g, lo, out, pay_pre, t, s_pay, s_w, corrupt);
+            else tiles_decode_one<2>(in, c, g, lo, out, pay_pre, t, s_pay, s_w, corrupt);
+        }
+        if (topo && t < nlt) tiles_cp_list(in, c, g, lo, cp_pre, cp_idx, t, s_cp, corrupt);
+    }
+    if (corrupt) set_status(status, ST_CORRUPT);
 }
 
 // RS^ colour rounds over the lost-saddle list (cooperative: the grid syncs
@@ -1472,6 +1631,14 @@ void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ct
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
     k_parse_header<<<1, 256, RBF_SOLVE_SMEM, st>>>(in, in_size, n_out, c, status, test_hold);
+}
+
+void launch_decode_tiles(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
+                         const uint32_t* cp_pre, uint32_t* cp_idx, uint64_t n, int sms, int* status,
+                         cudaStream_t st) {
+    // a format-v2 stream has at most n blocks; the CTAs step over the tiles
+    const uint32_t grid = (uint32_t)hmax<uint64_t>(1, hmin<uint64_t>(cdiv(n, DT_BLOCKS), (uint64_t)sms * 8));
+    k_decode_tiles<<<grid, 256, 0, st>>>(in, c, out, pay_pre, cp_pre, cp_idx, status);
 }
 
 void launch_decode_ranks(const uint8_t* in, Ctrl* c, const uint32_t* rpre, int32_t* delta, uint64_t max_k,

@@ -36,7 +36,7 @@ struct DecompressWs {
     uint64_t ctrl, rdesc, flags, tile_w, tile_c, pay_pre, cp_pre, cp_idx, delta, newv, sad, sadv, end;
     uint32_t ntiles, rank_tiles, sad_cap;
 };
-CompressWs compress_ws(uint64_t n);
+CompressWs compress_ws(uint64_t n, uint64_t nb_fmt = 0);   // nb_fmt: blocks of format v2 (0: v1)
 DecompressWs decompress_ws(uint64_t n);
 
 // ---- compression launchers (tsz_compress.cu)
@@ -47,7 +47,7 @@ void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsi
 void launch_qparams(Ctrl* c, int* status, cudaStream_t st);
 void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2* tcnt, uint32_t* scratch,
                          uint64_t region_bytes, uint8_t* out, const Layout& lo, uint2* listM, uint2* listm, bool topo,
-                         uint32_t nb, int sms, int* status, cudaStream_t st);
+                         const Geo& g, uint32_t nb_fmt, bool tiles, int sms, int* status, cudaStream_t st);
 void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm, uint64_t tmp_bytes,
                   const SortWs& sw, uint2* agg, uint32_t agg_stride, const uint2* tpre, int32_t* delta, int G,
                   int sms, int* status, cudaStream_t st);
@@ -62,6 +62,9 @@ void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ct
 void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* tile_c,
                         unsigned long long* pay_pre, uint32_t* cp_pre, uint32_t* rtile_w, uint32_t ntiles, int sms,
                         int* status, cudaStream_t st);
+void launch_decode_tiles(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
+                         const uint32_t* cp_pre, uint32_t* cp_idx, uint64_t n, int sms, int* status,
+                         cudaStream_t st);
 void launch_decode_ranks(const uint8_t* in, Ctrl* c, const uint32_t* rpre, int32_t* delta, uint64_t max_k,
                          int sms, int* status, cudaStream_t st);
 void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,

@@ -39,6 +39,26 @@ def test_batch_equals_plain(branches, graph):
         assert torch.equal(it.dec.view(torch.int32), dec.view(torch.int32))
 
 
+@pytest.mark.slow
+def test_batch_config4_every_field_equals_plain():
+    """The 96-field mixed batch of the batched workload (48 2D fields of side
+    128-4096, 48 3D fields of side 64-384, relative bounds 1e-2 to 1e-4,
+    about 2.5 GB) through one graph replay: each field's stream bytes and
+    decoded values equal those of a plain per-field call."""
+    specs = synth.mixed_batch()
+    fs = [sp.make("cuda") for sp in specs]
+    ebs = [sp.eb for sp in specs]
+    plan = batch.BatchPlan.create(fs, ebs, "rel", branches=8).capture()
+    plan.compress()
+    plan.decompress()
+    plan.check()
+    for i, (f, eb, got, it) in enumerate(zip(fs, ebs, plan.streams_bytes(), plan.items)):
+        want = codec.compress(f, eb, "rel")
+        assert torch.equal(got, want), f"field {i} {tuple(f.shape)}: stream differs"
+        dec = codec.decompress(want, tuple(f.shape))
+        assert torch.equal(it.dec.view(torch.int32), dec.view(torch.int32)), f"field {i}: decoded values differ"
+
+
 def test_batch_no_topo_and_abs():
     fs, ebs = _fields()
     plan = batch.BatchPlan.create(fs, [1e-2] * len(fs), "abs", branches=4, no_topo=True).capture()

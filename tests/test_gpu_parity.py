@@ -38,7 +38,8 @@ def gpu_roundtrip(a: np.ndarray, eb: float, rel: bool, **kw):
 
 def assert_parity(a, eb, rel=True, **kw):
     okw = dict(no_topo=kw.get("no_topo", False), rs_sweeps=kw.get("rs_sweeps", 1),
-               rbf_k=kw.get("rbf_k", 0), rbf_sigma=kw.get("rbf_sigma", 0.0), rbf_solve=kw.get("rbf_solve", False))
+               rbf_k=kw.get("rbf_k", 0), rbf_sigma=kw.get("rbf_sigma", 0.0), rbf_solve=kw.get("rbf_solve", False),
+               tile_blocks=kw.get("tile_blocks", False))
     gbuf, gout = gpu_roundtrip(a, eb, rel, **okw)
     obuf = oracle.compress(a, eb, rel=rel, **okw)
     assert gbuf == obuf, section_report(gbuf, obuf)
@@ -318,3 +319,50 @@ def test_parity_rbf_solve_hand_cases():
         g = load(name)
         assert_parity(field(g), float(g["eps"]), rel=False, rbf_k=int(g.get("rbf_k", 3)),
                       rbf_sigma=float(g.get("rbf_sigma", 1.0)), rbf_solve=True)
+
+
+def _tile_field(shape, seed=4):
+    if len(shape) == 3 and min(shape) >= 8:
+        return synth.grf(shape, -11 / 3, seed).numpy()
+    if len(shape) == 2 and min(shape) >= 8:
+        return synth.climate_2d(*shape, seed=seed).numpy()
+    return np.random.default_rng(seed).standard_normal(shape).astype(np.float32)
+
+
+@pytest.mark.parametrize("shape", [(300, 517), (24, 24, 24), (29, 37, 45), (33, 65), (9, 10, 11), (1, 1), (1, 37),
+                                   (37, 1), (1, 1, 40), (5, 1, 7), (40, 1, 1), (2, 3, 5), (7, 9, 13)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_parity_tile_blocks(shape):
+    """Format v2, tile-shaped blocks (TOPOSZP_TILE_BLOCKS): the CUDA stream
+    equals the oracle's byte for byte (the per-block predictor choice and
+    the clamped codes of blocks that stick out of the grid included), and
+    the decoded field equals both the oracle's and the format-v1 field."""
+    a = _tile_field(shape)
+    for eb, nt in ((1e-2, False), (1e-4, False), (1e-3, True)):
+        _, oout = assert_parity(a, eb, rel=True, no_topo=nt, tile_blocks=True)
+        _, v1 = gpu_roundtrip(a, eb, True, no_topo=nt)
+        assert np.array_equal(oout.view(np.uint32), v1.view(np.uint32))
+
+
+@pytest.mark.parametrize("shape", [(96, 96, 96), (600, 700)])
+def test_parity_tile_blocks_many_tiles(shape):
+    """Format v2 on fields of many tiles, through the fused decoder (S1 done
+    by the tile kernel) with and without neighbourhood records, and through
+    the split stages."""
+    from paper_2602_17552_gb300 import autotune
+    a = synth.turbulence_3d(shape[0], seed=11).numpy() if len(shape) == 3 else \
+        synth.climate_2d(*shape, seed=11).numpy()
+    obuf = oracle.compress(a, 1e-3, rel=True, tile_blocks=True)
+    oout = oracle.decompress(obuf, a.shape)
+    f = torch.from_numpy(a).cuda()
+    try:
+        for cfg in ({}, {"saddle_records": -1}, {"dec_split": 1}):
+            autotune.apply({**autotune.DEFAULT, **cfg})
+            buf = codec.compress(f, 1e-3, "rel", tile_blocks=True)
+            assert buf.cpu().numpy().tobytes() == obuf, cfg
+            out = codec.decompress(buf, a.shape).cpu().numpy()
+            assert np.array_equal(out.view(np.uint32), oout.view(np.uint32)), cfg
+    finally:
+        autotune.restore()
+    info = codec.inspect(buf)
+    assert info.flags & _lib.TILE_BLOCKS

@@ -603,6 +603,135 @@ def test_rbf_solve_needs_a_positive_width():
         assert ei.value.status == oracle.CORRUPT
 
 
+# ------------------------------------------------ format v2: tile-shaped blocks
+
+def _sections(buf):
+    h = oracle.header(buf)
+    nb = h["nb"]
+    width = np.frombuffer(buf[h["off_s2"]:h["off_s2"] + nb], np.uint8)
+    first = np.frombuffer(buf[h["off_s4"]:h["off_s4"] + 4 * nb], "<i4")
+    pay = np.frombuffer(buf[h["off_s5"]:h["off_s5"] + 4 * h["pay_words"]], "<u4")
+    return h, width, first, pay
+
+
+def test_tile_block_lorenzo_hand_case():
+    """Format v2 (Section II-C's B + LZ on a tile-shaped block): one 8 x 4
+    block of integer values with |a| <= 85 and absolute eps 0.5, so the bin
+    width is just below 1 and every code equals its value.  The codes are
+    q = 7 + 3x + 5y + 2xy.  Worked by hand:
+    - Lorenzo residuals: 0 at the corner, 3 along row 0, 5 down column 0, and
+      the mixed term 2 inside.  The widest is 5, so w = 3.
+    - The element-order chain jumps by -16, -30 and -44 at the row starts, so
+      Lorenzo is coded: width byte 0x83, first value 7.
+    - Payload: the sign plane 0, then magnitude planes 0x010101FE (bit 0: the
+      3s and 5s), 0xFEFEFEFE (bit 1: the 3s and 2s), 0x01010100 (bit 2: the 5s)."""
+    y, x = np.mgrid[0:4, 0:8]
+    a = (7 + 3 * x + 5 * y + 2 * x * y).astype(np.float32)
+    buf = oracle.compress(a, 0.5, rel=False, no_topo=True, tile_blocks=True)
+    h, width, first, pay = _sections(buf)
+    assert h["version"] == 2 and h["nb"] == 1
+    assert width.tolist() == [0x83] and first.tolist() == [7]
+    assert pay.tolist() == [0, 0x010101FE, 0xFEFEFEFE, 0x01010100]
+    out = oracle.decompress(buf, a.shape)
+    assert np.abs(out.astype(np.float64) - a).max() <= 0.5
+
+
+def test_tile_block_chain_hand_case():
+    """Rows 0 1 0 1 ... repeated in every row: the chain's residuals are
+    +1 (odd e) and -1 (even e > 0), width 1; Lorenzo's are +-1 along row 0
+    and 0 elsewhere, also width 1.  On a tie the chain is coded: width byte
+    0x01, sign plane 0x55555554 (the even e > 0), magnitude plane 0xFFFFFFFE."""
+    a = np.tile(np.array([0, 1] * 4, np.float32), (4, 1))
+    buf = oracle.compress(a, 0.5, rel=False, no_topo=True, tile_blocks=True)
+    h, width, first, pay = _sections(buf)
+    assert width.tolist() == [0x01] and first.tolist() == [0]
+    assert pay.tolist() == [0x55555554, 0xFFFFFFFE]
+
+
+def _tile_cases():
+    rng = np.random.default_rng(11)
+    yield "bumps", synth.gaussian_bumps_2d(64, 80, count=20, seed=5).numpy()
+    yield "climate", synth.climate_2d(61, 97, seed=2).numpy()
+    yield "turb", synth.turbulence_3d(20, seed=3).numpy()
+    yield "ragged3", synth.grf((7, 9, 13), -11 / 3, 4).numpy()
+    yield "adv2", synth.adversarial_small(1, (33, 17)).numpy()
+    yield "adv3", synth.adversarial_small(2, (9, 8, 7)).numpy()
+    for shape in [(1, 1), (1, 37), (37, 1), (3, 3), (1, 1, 40), (5, 1, 7), (40, 1, 1), (2, 3, 5)]:
+        yield f"rand{shape}", rng.standard_normal(shape).astype(np.float32)
+    yield "checker", ((1.0 + rng.random((10, 12))) * np.where(np.indices((10, 12)).sum(0) % 2, 1.0, -1.0)).astype(np.float32)
+
+
+@pytest.mark.parametrize("opts", [dict(rel=True, eb=1e-2), dict(rel=True, eb=1e-4), dict(rel=False, eb=0.05),
+                                  dict(rel=True, eb=1e-3, no_topo=True)])
+def test_tile_format_decodes_to_the_format_v1_field(opts):
+    """Format v2 changes only how the codes are coded: the decoded field, the
+    labels and the rank stream equal format v1's bit for bit, on 2D and 3D
+    fields, ragged and one-point-thin grids (where most of a block lies
+    outside the grid and takes clamped codes), and for both bound modes."""
+    for name, a in _tile_cases():
+        b1 = oracle.compress(a, **opts)
+        b2 = oracle.compress(a, tile_blocks=True, **opts)
+        h1, h2 = oracle.header(b1), oracle.header(b2)
+        assert h1["version"] == 1 and h2["version"] == 2, name
+        assert h2["nb"] == oracle.tile_blocks(a.shape), name
+        assert h1["sum_abs"] == h2["sum_abs"] and h1["rbf_k"] == h2["rbf_k"], name
+        if not opts.get("no_topo"):
+            n = a.size
+            lab1 = b1[h1["off_s6"]:h1["off_s6"] + 4 * ((n + 15) // 16)]
+            lab2 = b2[h2["off_s6"]:h2["off_s6"] + 4 * ((n + 15) // 16)]
+            assert lab1 == lab2, name
+            assert b1[h1["off_s7"]:h1["total"]] == b2[h2["off_s7"]:h2["total"]], name
+        o1, o2 = oracle.decompress(b1, a.shape), oracle.decompress(b2, a.shape)
+        assert np.array_equal(o1.view(np.uint32), o2.view(np.uint32)), name
+
+
+def test_tile_blocks_count_and_bound():
+    """Blocks of format v2: ceil(nx/8) ceil(ny/4) in 2D, ceil(nx/4) ceil(ny/4)
+    ceil(nz/2) in 3D; the compression bound covers either format."""
+    assert oracle.tile_blocks((4, 8)) == 1 and oracle.tile_blocks((5, 9)) == 4
+    assert oracle.tile_blocks((37, 1)) == 10 and oracle.tile_blocks((1, 37)) == 5
+    assert oracle.tile_blocks((2, 4, 4)) == 1 and oracle.tile_blocks((3, 5, 5)) == 8
+    assert oracle.tile_blocks((40, 1, 1)) == 20
+    rng = np.random.default_rng(3)
+    for shape in [(1, 1000), (1000, 1), (1, 1, 300), (300, 1, 1), (17, 23, 5)]:
+        a = rng.standard_normal(shape).astype(np.float32)
+        assert len(oracle.compress(a, 1e-5, tile_blocks=True)) <= oracle.compress_bound(shape)
+
+
+def test_tile_blocks_code_smooth_fields_smaller():
+    """On the smooth synthetic fields the tile-shaped blocks code fewer
+    payload words than runs of 32 consecutive points (same decoded field)."""
+    for name, a in (("turb", synth.turbulence_3d(32, seed=3).numpy()),
+                    ("bumps", synth.gaussian_bumps_2d(96, 128, count=20, seed=5).numpy())):
+        for eb in (1e-3, 1e-4):
+            p1 = oracle.header(oracle.compress(a, eb, no_topo=True))["pay_words"]
+            p2 = oracle.header(oracle.compress(a, eb, no_topo=True, tile_blocks=True))["pay_words"]
+            assert p2 < p1, (name, eb, p1, p2)
+
+
+def test_tile_stream_damage_rejected():
+    """A format-v2 width byte with the predictor bit but no planes, and a
+    format-v1 stream relabelled as version 2 (its block count no longer
+    matches the grid's tiles), mark the stream damaged."""
+    import struct
+    a = synth.gaussian_bumps_2d(20, 24, count=4, seed=1).numpy()
+    buf = bytearray(oracle.compress(a, 1e-3, tile_blocks=True))
+    h = oracle.header(bytes(buf))
+    w = np.frombuffer(bytes(buf[h["off_s2"]:h["off_s2"] + h["nb"]]), np.uint8)
+    j = int(np.nonzero(w == 0)[0][0]) if (w == 0).any() else None
+    if j is not None:
+        bad = bytearray(buf)
+        bad[h["off_s2"] + j] = 0x80
+        with pytest.raises(oracle.OracleError):
+            oracle.decompress(bytes(bad), a.shape)
+    b = synth.gaussian_bumps_2d(21, 24, count=4, seed=1).numpy()   # 16 runs of 32, 18 tiles
+    v1 = bytearray(oracle.compress(b, 1e-3))
+    v1[4:8] = struct.pack("<I", 2)
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.decompress(bytes(v1), b.shape)
+    assert ei.value.status == oracle.CORRUPT
+
+
 def _fields_small():
     yield "bumps", synth.gaussian_bumps_2d(64, 80, count=20, seed=5).numpy()
     yield "climate", synth.climate_2d(60, 96, seed=2).numpy()
