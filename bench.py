@@ -728,26 +728,35 @@ def run_tradeoff(args):
     refinement by the clamped normalised kernel, and by the literal RBF
     interpolation) and its SZp-only mode (no topology sections), relative
     bounds 1e-3, 1e-4, 1e-5, on the 1800x3600 and 512^3 fields: the synthetic
-    analogue of Table II / Fig. 8.  decompress_ms: the median of three
-    CUDA-event timed decompress calls of the row's stream.  One JSON line."""
+    analogue of Table II / Fig. 8; with format v2 (tile-shaped blocks) beside
+    both codings.  compress_ms / decompress_ms: the median of three CUDA-event
+    timed calls of the row's mode.  One JSON line."""
     import torch
     from paper_2602_17552_gb300 import codec
     torch.cuda.set_device(0)
     rows = []
-    modes = (("TopoSZp", {}), ("TopoSZp, literal RBF", {"rbf_solve": True}), ("SZp only", {"no_topo": True}))
+    modes = (("TopoSZp", {}), ("TopoSZp, tile blocks (v2)", {"tile_blocks": True}),
+             ("TopoSZp, literal RBF", {"rbf_solve": True}), ("SZp only", {"no_topo": True}),
+             ("SZp only, tile blocks (v2)", {"no_topo": True, "tile_blocks": True}))
 
-    def dec_ms(f, eb, kw):
+    def times_ms(f, eb, kw):
+        """median of three CUDA-event timed compress calls and decompress calls"""
+        params = codec.make_params(**kw)
         buf = codec.compress(f, eb, "rel", **kw)
         out = torch.empty_like(f)
-        ts = []
-        for _ in range(4):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            codec.decompress_async(buf, tuple(f.shape), out=out)
-            e1.record()
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        return float(statistics.median(ts[1:]))
+        res = []
+        for fn in (lambda: codec.compress_async(f, eb, "rel", params=params),
+                   lambda: codec.decompress_async(buf, tuple(f.shape), out=out)):
+            ts = []
+            for _ in range(4):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            res.append(float(statistics.median(ts[1:])))
+        return res
 
     for wl in ("climate", "turb512"):
         spec = workload_spec(wl, 1e-3, args.side)
@@ -757,8 +766,10 @@ def run_tradeoff(args):
         for eb in (1e-3, 1e-4, 1e-5):
             for mode, kw in modes:
                 r = codec.tradeoff(f, eb, "rel", labels=labels, **kw)
+                c_ms, d_ms = times_ms(f, eb, kw)
                 rows.append({"field": describe(spec).split(", relative")[0], "eb_rel": eb,
-                             "mode": mode, "counts_rmsM": counts, "decompress_ms": round(dec_ms(f, eb, kw), 4),
+                             "mode": mode, "counts_rmsM": counts, "compress_ms": round(c_ms, 4),
+                             "decompress_ms": round(d_ms, 4),
                              **{k: (round(v, 4) if isinstance(v, float) else v) for k, v in r.items()}})
         del f, labels
         torch.cuda.empty_cache()

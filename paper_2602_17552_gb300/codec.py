@@ -210,7 +210,7 @@ def topo_errors(labels_a: torch.Tensor, labels_b: torch.Tensor, n: int, *, strea
 
 
 def tradeoff(field: torch.Tensor, eb: float, mode: str = "rel", *, no_topo=False, rbf_solve=False,
-             labels=None, stream=None) -> dict:
+             tile_blocks=False, labels=None, stream=None) -> dict:
     """One point of the bit-rate / topology-error trade-off (Section III-B,
     Table II): compress and decompress ``field`` and count the false
     negatives, false positives and false types of the decompressed field's
@@ -222,7 +222,7 @@ def tradeoff(field: torch.Tensor, eb: float, mode: str = "rel", *, no_topo=False
     n = field.numel()
     if labels is None:
         labels, _ = critical_points(field, counts=False, stream=stream)
-    buf = compress(field, eb, mode, no_topo=no_topo, rbf_solve=rbf_solve, stream=stream)
+    buf = compress(field, eb, mode, no_topo=no_topo, rbf_solve=rbf_solve, tile_blocks=tile_blocks, stream=stream)
     info = inspect(buf)
     dec = decompress(buf, tuple(field.shape), stream=stream)
     lab_d, _ = critical_points(dec, counts=False, stream=stream)
