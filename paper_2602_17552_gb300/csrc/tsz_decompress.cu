@@ -533,7 +533,10 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
 // change during the rounds are the listed candidates, all saddle-labelled; the
 // record marks the saddle-labelled slots and those are read from the field
 // when a round needs them, so a record always gives current values and the
-// arithmetic is exactly that of saddle_candidate().
+// arithmetic is exactly that of saddle_candidate().  Every candidate gets a
+// record, also near the grid's faces, where a mask marks the slots inside the
+// grid: field reads there would make the few warps holding such a candidate
+// two to three times slower, and those warps set the end of every round.
 //
 // Slots: the RBF neighbourhood N_r(p) \ {p} in the RBF table's (z, y, x)
 // order, then the remaining points at Manhattan distance 1..2 (the face
@@ -581,38 +584,64 @@ struct RecStencil {
             }
         }
     }
-    // record words: the slots and the saddle-slot mask, padded to 16 bytes
-    __host__ __device__ constexpr int words() const { return (n + 1 + 3) / 4 * 4; }
+    // the slots of the RBF neighbourhood, and face f's neighbours (p is always inside)
+    __host__ __device__ constexpr uint32_t ball_mask() const { return ns == 32 ? 0xFFFFFFFFu : (1u << ns) - 1u; }
+    __host__ __device__ constexpr uint32_t nbr_mask(int f) const {
+        uint32_t m = 0;
+        for (int k = 0; k < 2 * ND; k++)
+            if (nbr[f][k] >= 0) m |= 1u << nbr[f][k];
+        return m;
+    }
+    // record words: the slots, the saddle-slot mask and the in-grid mask, padded to 16 bytes
+    __host__ __device__ constexpr int words() const { return (n + 2 + 3) / 4 * 4; }
 };
 constexpr int REC_MAX_WORDS = 36;   // the largest record (3D, r = 2)
+static_assert(RecStencil<3, 1>{}.words() <= REC_MAX_WORDS && RecStencil<3, 2>{}.words() <= REC_MAX_WORDS &&
+                  RecStencil<2, 1>{}.words() <= REC_MAX_WORDS && RecStencil<2, 2>{}.words() <= REC_MAX_WORDS &&
+                  RecStencil<2, 3>{}.words() <= REC_MAX_WORDS,
+              "record size");
+static_assert(RecStencil<3, 2>{}.n <= 32 && RecStencil<2, 3>{}.n <= 32, "slot masks are 32 bits");
 
 // Record kinds: 3D r = 1, 2 and 2D r = 1, 2, 3 (3D r = 3 keeps the field reads).
 __host__ __device__ inline bool rec_supported(int ndim, int r) {
     return ndim == 3 ? (r == 1 || r == 2) : (r >= 1 && r <= 3);
 }
 
-// Candidates with records: the whole RBF neighbourhood and both face rings inside the grid.
+// Candidates whose whole RBF neighbourhood and both face rings lie inside the
+// grid: their record has every slot (no bounds checks when it is gathered).
 __device__ __forceinline__ bool rec_inside(const Geo& g, int r, uint32_t x, uint32_t y, uint32_t z) {
     const uint32_t m = r > 2 ? (uint32_t)r : 2u;
     return x >= m && x + m < g.nx && y >= m && y + m < g.ny && (g.ndim == 2 || (z >= m && z + m < g.nz));
 }
 
+// A candidate's record: its slot values, the saddle-labelled slots (read live
+// in the rounds) and the slots inside the grid.  Near the grid's faces some
+// slots lie outside: they are not read and their bit is clear.
 template <int ND, int R>
 __device__ __forceinline__ void rec_gather(const float* F, const uint32_t* labels, const Geo& g, uint32_t p,
-                                           uint32_t* rec) {
+                                           uint32_t x, uint32_t y, uint32_t z, bool inside, uint32_t* rec) {
     constexpr RecStencil<ND, R> S{};
     constexpr int W = S.words();
     uint32_t w[W];
-    uint32_t dyn = 0;
+    uint32_t dyn = 0, vm = 0;
 #pragma unroll
     for (int e = 0; e < S.n; e++) {
-        const uint32_t q = p + (uint32_t)(S.dx[e] + S.dy[e] * (int)g.nx + S.dz[e] * (int)g.nxy);
-        w[e] = __float_as_uint(F[q]);
-        dyn |= (label_at(labels, q) == LAB_SAD ? 1u : 0u) << e;
+        const bool in = inside || ((long long)x + S.dx[e] >= 0 && (long long)x + S.dx[e] < (long long)g.nx &&
+                                   (long long)y + S.dy[e] >= 0 && (long long)y + S.dy[e] < (long long)g.ny &&
+                                   (long long)z + S.dz[e] >= 0 && (long long)z + S.dz[e] < (long long)g.nz);
+        uint32_t wv = 0u;
+        if (in) {
+            const uint32_t q = p + (uint32_t)(S.dx[e] + S.dy[e] * (int)g.nx + S.dz[e] * (int)g.nxy);
+            wv = __float_as_uint(F[q]);
+            dyn |= (label_at(labels, q) == LAB_SAD ? 1u : 0u) << e;
+            vm |= 1u << e;
+        }
+        w[e] = wv;
     }
     w[S.n] = dyn;
+    w[S.n + 1] = vm;
 #pragma unroll
-    for (int e = S.n + 1; e < W; e++) w[e] = 0u;
+    for (int e = S.n + 2; e < W; e++) w[e] = 0u;
     uint4* d = reinterpret_cast<uint4*>(rec);
 #pragma unroll
     for (int k = 0; k < W / 4; k++) d[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
@@ -629,7 +658,28 @@ __device__ __forceinline__ int cls_vals(float v, const float* n) {
     return (int)((uint32_t)(m | M) | ((uint32_t)(s | M) << 1));
 }
 
-// saddle_candidate() for a candidate with a record (rec_inside holds).
+// classify()'s rule for a point with a face neighbour outside the grid
+// (present: bit k set for neighbour k): a minimum or maximum over the
+// neighbours present, never a saddle.
+template <int ND>
+__device__ __forceinline__ int cls_vals_cut(float v, const float* n, uint32_t present) {
+    int nn = 0, nhi = 0, nlo = 0;
+#pragma unroll
+    for (int k = 0; k < 2 * ND; k++) {
+        if (!((present >> k) & 1u)) continue;
+        nn++;
+        nhi += n[k] > v;
+        nlo += n[k] < v;
+    }
+    if (nn == 0) return LAB_R;
+    return nhi == nn ? LAB_MIN : (nlo == nn ? LAB_MAX : LAB_R);
+}
+
+// saddle_candidate() for a candidate with a record: the same arithmetic in the
+// same order.  Slots outside the grid (clear bits of the record's in-grid
+// mask) are never read: a cut RBF ball takes the normalised kernel over the
+// slots inside, a face neighbour on the grid's boundary is classified over
+// the neighbours it has.
 template <int ND, int R>
 __device__ bool saddle_candidate_rec(const float* F, const uint32_t* labels, const Geo& g, const Ctrl* c,
                                      float den_full, uint32_t p, const uint32_t* rec, float& vout) {
@@ -642,7 +692,11 @@ __device__ bool saddle_candidate_rec(const float* F, const uint32_t* labels, con
         const uint4 t = s4[k];
         w[4 * k] = t.x, w[4 * k + 1] = t.y, w[4 * k + 2] = t.z, w[4 * k + 3] = t.w;
     }
-    const uint32_t dyn = w[S.n];
+    const uint32_t dyn = w[S.n], vm = w[S.n + 1];
+    // a saddle label is only valid at interior points; anything else is a bad stream
+#pragma unroll
+    for (int f = 0; f < 2 * ND; f++)
+        if (!((vm >> S.face[f]) & 1u)) return false;
     float v[S.n];
 #pragma unroll
     for (int e = 0; e < S.n; e++)
@@ -672,20 +726,37 @@ __device__ bool saddle_candidate_rec(const float* F, const uint32_t* labels, con
     if (isinf(gmin)) return false;
     const bool solve = c->flags & FLAG_RBF_SOLVE;
     if (!solve && !saddle_feasible(nb, ND, Fp)) return false;
+    const bool ball_in = (vm & S.ball_mask()) == S.ball_mask();
     float num = 0.0f, vn;
-    if (solve) {
+    if (solve && ball_in) {
 #pragma unroll
         for (int e = 0; e < S.ns; e++) num = __fadd_rn(num, __fmul_rn(c->rbf_alpha[e], v[e]));
         vn = num;
     } else {
+        float den = den_full;
+        if (ball_in) {
 #pragma unroll
-        for (int e = 0; e < S.ns; e++) num = __fadd_rn(num, __fmul_rn(c->g_rbf[S.d2[e] - 1], v[e]));
-        const float u = __fdiv_rn(num, den_full);
-        const float capv = fminf(__fmul_rn(0.1f, c->h_f), __fmul_rn(0.5f, gmin));
-        float stp = __fsub_rn(u, Fp);
-        if (stp > capv) stp = capv;
-        if (stp < -capv) stp = -capv;
-        vn = __fadd_rn(Fp, stp);
+            for (int e = 0; e < S.ns; e++) num = __fadd_rn(num, __fmul_rn(c->g_rbf[S.d2[e] - 1], v[e]));
+        } else {   // the ball cut by the grid: its slots inside, in table order
+            den = 0.0f;
+#pragma unroll
+            for (int e = 0; e < S.ns; e++) {
+                if (!((vm >> e) & 1u)) continue;
+                const float gw = c->g_rbf[S.d2[e] - 1];
+                num = __fadd_rn(num, __fmul_rn(gw, v[e]));
+                den = __fadd_rn(den, gw);
+            }
+        }
+        const float u = __fdiv_rn(num, den);
+        if (solve) {
+            vn = u;   // the literal interpolation: unclamped
+        } else {
+            const float capv = fminf(__fmul_rn(0.1f, c->h_f), __fmul_rn(0.5f, gmin));
+            float stp = __fsub_rn(u, Fp);
+            if (stp > capv) stp = capv;
+            if (stp < -capv) stp = -capv;
+            vn = __fadd_rn(Fp, stp);
+        }
     }
     if (vn == Fp) return false;
     if (cls_vals<ND>(vn, nb) != LAB_SAD) return false;   // (a)
@@ -693,14 +764,23 @@ __device__ bool saddle_candidate_rec(const float* F, const uint32_t* labels, con
 #pragma unroll
     for (int f = 0; f < 2 * ND; f++) {                   // (b)
         float qn[2 * ND], qo[2 * ND];
+        uint32_t present = 0;
 #pragma unroll
         for (int k = 0; k < 2 * ND; k++) {
             const int sl = S.nbr[f][k];
             qn[k] = sl < 0 ? vn : v[sl < 0 ? 0 : sl];
             qo[k] = sl < 0 ? Fp : v[sl < 0 ? 0 : sl];
+            present |= (sl < 0 || ((vm >> (sl < 0 ? 0 : sl)) & 1u) ? 1u : 0u) << k;
         }
         const float fq = nb[f];
-        const int tn = cls_vals<ND>(fq, qn), to = cls_vals<ND>(fq, qo);
+        int tn, to;
+        if (present == (1u << (2 * ND)) - 1u) {
+            tn = cls_vals<ND>(fq, qn);
+            to = cls_vals<ND>(fq, qo);
+        } else {
+            tn = cls_vals_cut<ND>(fq, qn, present);
+            to = cls_vals_cut<ND>(fq, qo, present);
+        }
         if (tn != to) {
             const uint32_t q = f & 1 ? p + st[f >> 1] : p - st[f >> 1];
             if (tn != label_at(labels, q)) return false;
@@ -711,16 +791,17 @@ __device__ bool saddle_candidate_rec(const float* F, const uint32_t* labels, con
     return true;
 }
 
-// Record dispatch on (ndim, r); false when that kind keeps the field reads.
+// Record dispatch on (ndim, r) (the kinds rec_supported() admits).
 __device__ __forceinline__ void rec_gather_any(int ndim, int r, const float* F, const uint32_t* labels,
-                                               const Geo& g, uint32_t p, uint32_t* rec) {
+                                               const Geo& g, uint32_t p, uint32_t x, uint32_t y, uint32_t z,
+                                               bool inside, uint32_t* rec) {
     if (ndim == 3) {
-        if (r == 1) rec_gather<3, 1>(F, labels, g, p, rec);
-        else rec_gather<3, 2>(F, labels, g, p, rec);
+        if (r == 1) rec_gather<3, 1>(F, labels, g, p, x, y, z, inside, rec);
+        else rec_gather<3, 2>(F, labels, g, p, x, y, z, inside, rec);
     } else {
-        if (r == 1) rec_gather<2, 1>(F, labels, g, p, rec);
-        else if (r == 2) rec_gather<2, 2>(F, labels, g, p, rec);
-        else rec_gather<2, 3>(F, labels, g, p, rec);
+        if (r == 1) rec_gather<2, 1>(F, labels, g, p, x, y, z, inside, rec);
+        else if (r == 2) rec_gather<2, 2>(F, labels, g, p, x, y, z, inside, rec);
+        else rec_gather<2, 3>(F, labels, g, p, x, y, z, inside, rec);
     }
 }
 
@@ -1577,7 +1658,8 @@ __global__ void __launch_bounds__(1024, 1) k_saddle_rounds(const uint8_t* __rest
         const int col = colour_of(g, x, y, z);
         const uint32_t slot = base[col] + s_base[col] + atomicAdd(&s_cnt[col], 1u);
         sadb[slot] = p;
-        if (use_rec && rec_inside(g, r, x, y, z)) rec_gather_any(g.ndim, r, out, labels, g, p, rec + (size_t)slot * RW);
+        if (use_rec)
+            rec_gather_any(g.ndim, r, out, labels, g, p, x, y, z, rec_inside(g, r, x, y, z), rec + (size_t)slot * RW);
     }
     grid.sync();
     unsigned long long fixed = 0;
@@ -1593,13 +1675,16 @@ __global__ void __launch_bounds__(1024, 1) k_saddle_rounds(const uint8_t* __rest
                 const uint32_t j = k0 + (threadIdx.x & 31);
                 if (j < nc) {
                     const uint32_t p = sadb[b0 + j];
-                    uint32_t x, y, z;
-                    coords(g, p, x, y, z);
                     float v;
-                    const bool ok = use_rec && rec_inside(g, r, x, y, z)
-                                        ? saddle_candidate_rec_any(g.ndim, r, out, labels, g, c, T.den_full, p,
-                                                                   rec + (size_t)(b0 + j) * RW, v)
-                                        : saddle_candidate(out, labels, g, c, T, p, x, y, z, v);
+                    bool ok;
+                    if (use_rec) {
+                        ok = saddle_candidate_rec_any(g.ndim, r, out, labels, g, c, T.den_full, p,
+                                                      rec + (size_t)(b0 + j) * RW, v);
+                    } else {
+                        uint32_t x, y, z;
+                        coords(g, p, x, y, z);
+                        ok = saddle_candidate(out, labels, g, c, T, p, x, y, z, v);
+                    }
                     sadv[b0 + j] = ok ? v : __int_as_float(0x7FC00000);
                 }
             }
