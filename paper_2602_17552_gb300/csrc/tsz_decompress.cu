@@ -507,6 +507,9 @@ __device__ bool saddle_candidate(const float* F, const uint32_t* labels, const G
     for (int ax = 0; ax < g.ndim; ax++) {                          // (b)
         for (int sg = -1; sg <= 1; sg += 2) {
             const uint32_t q = sg < 0 ? p - st[ax] : p + st[ax];
+            // q's type depends on p only through p's order against f(q)
+            const float fq0 = F[q];
+            if ((v > fq0) == (Fp > fq0) && (v < fq0) == (Fp < fq0)) continue;
             uint32_t qx = x, qy = y, qz = z;
             if (ax == 0) qx = sg < 0 ? x - 1 : x + 1;
             else if (ax == 1) qy = sg < 0 ? y - 1 : y + 1;
@@ -773,6 +776,9 @@ __device__ bool saddle_candidate_rec(const float* F, const uint32_t* labels, con
             present |= (sl < 0 || ((vm >> (sl < 0 ? 0 : sl)) & 1u) ? 1u : 0u) << k;
         }
         const float fq = nb[f];
+        // q's type depends on p only through p's order against f(q): if the
+        // move keeps it, the type is unchanged (exactly, not as a bound)
+        if ((vn > fq) == (Fp > fq) && (vn < fq) == (Fp < fq)) continue;
         int tn, to;
         if (present == (1u << (2 * ND)) - 1u) {
             tn = cls_vals<ND>(fq, qn);
