@@ -1068,7 +1068,7 @@ __global__ void __launch_bounds__(512) k_os_bases(const Ctrl* c, const uint32_t*
     base[row * OS_ND + threadIdx.x] = pre + inc - v;
 }
 
-__global__ void __launch_bounds__(OS_WARPS * 32) k_os_pass(const uint2* s0, const uint2* s1, uint2* d0, uint2* d1,
+__global__ void __launch_bounds__(OS_WARPS * 32, 2) k_os_pass(const uint2* s0, const uint2* s1, uint2* d0, uint2* d1,
                                                  const Ctrl* c, const uint32_t* base, uint32_t* desc,
                                                  uint32_t* desc_next, uint32_t desc_stride, uint32_t* tile_ctr,
                                                  int pass, int* status) {
