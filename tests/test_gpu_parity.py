@@ -175,6 +175,33 @@ def test_device_errors_reported():
     assert ei.value.status == _lib.CORRUPT_STREAM
 
 
+def test_device_errors_reported_tile_format():
+    """Damaged format-v2 streams come back as CORRUPT_STREAM, with no read
+    outside the buffer: a truncated stream, widths inflated to 32 (with and
+    without the predictor bit), the predictor bit on a constant block, and a
+    format-v1 stream relabelled as version 2 (its block count no longer
+    matches the grid's tiles)."""
+    a = synth.gaussian_bumps_2d(41, 50, count=5, seed=2).numpy()   # 65 runs of 32, 77 tiles
+    f = torch.from_numpy(a).cuda()
+    buf = codec.compress(f, 1e-3, "rel", tile_blocks=True)
+    h = oracle.header(buf.cpu().numpy().tobytes())
+    assert h["version"] == 2
+    bad = [buf[:200].clone()]
+    for v in (32, 0x80 | 32, 0x80):
+        d = buf.clone()
+        d[h["off_s2"]:h["off_s2"] + 16] = v
+        bad.append(d)
+    v1 = codec.compress(f, 1e-3, "rel").clone()
+    v1[4] = 2
+    bad.append(v1)
+    for d in bad:
+        with pytest.raises(_lib.TopoSZpError) as ei:
+            codec.decompress(d, a.shape)
+        assert ei.value.status == _lib.CORRUPT_STREAM
+    # the library still decodes a good stream afterwards
+    assert torch.equal(codec.decompress(buf, a.shape), codec.decompress(codec.compress(f, 1e-3, "rel"), a.shape))
+
+
 def test_parity_config2_full():
     """1800 x 3600 climate-like field, relative bounds 1e-2, 1e-3, 1e-4."""
     a = synth.climate_2d(1800, 3600, seed=2, device="cuda").cpu().numpy()
