@@ -224,7 +224,13 @@ uint64_t toposzp_noalloc_max_points(void);
  *                        without that table; -1: always the radix sort
  *   cd_columns           0: the range + CD pass of 3D fields walks z-columns
  *                        when each plane is a whole number of 128-point
- *                        chunks (default); -1: never */
+ *                        chunks (default); -1: never
+ *   launch_overlap       0: each kernel is launched as a programmatic
+ *                        dependent of the one before it on the stream, so
+ *                        that its CTAs are scheduled while that one ends and
+ *                        wait on the device for its results (default; plain
+ *                        launches inside a stream capture); -1: plain
+ *                        stream-ordered launches */
 typedef struct {
     int32_t cd_threads;
     int32_t cd_blocks_per_sm;
@@ -234,6 +240,7 @@ typedef struct {
     int32_t dec_split;
     int32_t rank_bitmap;
     int32_t cd_columns;
+    int32_t launch_overlap;
 } toposzp_tuning;
 toposzp_status toposzp_set_tuning(const toposzp_tuning* t);
 

@@ -38,7 +38,8 @@ class Tuning(ctypes.Structure):
     _fields_ = [("cd_threads", ctypes.c_int32), ("cd_blocks_per_sm", ctypes.c_int32),
                 ("rounds_blocks_per_sm", ctypes.c_int32), ("dec_slack_tiles", ctypes.c_int32),
                 ("saddle_records", ctypes.c_int32), ("dec_split", ctypes.c_int32),
-                ("rank_bitmap", ctypes.c_int32), ("cd_columns", ctypes.c_int32)]
+                ("rank_bitmap", ctypes.c_int32), ("cd_columns", ctypes.c_int32),
+                ("launch_overlap", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
@@ -135,7 +136,7 @@ tuning_source = "defaults"
 
 def tuning_struct(cfg: dict) -> Tuning:
     keys = ("cd_threads", "cd_blocks_per_sm", "rounds_blocks_per_sm", "dec_slack_tiles", "saddle_records",
-            "dec_split", "rank_bitmap", "cd_columns")
+            "dec_split", "rank_bitmap", "cd_columns", "launch_overlap")
     return Tuning(*[int(cfg.get(k, 0)) for k in keys])
 
 

@@ -30,7 +30,8 @@ from . import _lib, batch, codec, synth
 
 OUT = os.environ.get("TOPOSZP_TUNING_OUT", _lib.TUNING_FILE)
 DEFAULT = {"cd_threads": 256, "cd_blocks_per_sm": 8, "rounds_blocks_per_sm": 1, "dec_slack_tiles": 0,
-           "saddle_records": 0, "dec_split": 0, "rank_bitmap": 0, "cd_columns": 0, "batch_branches": 8}
+           "saddle_records": 0, "dec_split": 0, "rank_bitmap": 0, "cd_columns": 0, "launch_overlap": 0,
+           "batch_branches": 8}
 # representative sides per (ndim, size class)
 SIDES = {2: (192, 640, 2048, 6000), 3: (32, 80, 200, 512)}
 

@@ -111,6 +111,7 @@ DecompressWs decompress_ws(uint64_t n) {
 }
 
 __global__ void k_init_ctrl(Ctrl* c, Geo g, int rel, double eb, uint32_t flags, int sweeps, uint32_t nb_fmt) {
+    griddep_enter();
     c->g = g;
     c->nb_fmt = nb_fmt;
     c->rel = rel;
@@ -157,6 +158,7 @@ static bool make_tuning(const toposzp_tuning* t, Tuning& u) {
     if (t->dec_split < 0 || t->dec_split > 1) return false;
     if (t->rank_bitmap < -1 || t->rank_bitmap > 1) return false;
     if (t->cd_columns < -1 || t->cd_columns > 0) return false;
+    if (t->launch_overlap < -1 || t->launch_overlap > 0) return false;
     u = Tuning();
     if (t->cd_threads) u.cd_threads = t->cd_threads;
     if (t->cd_blocks_per_sm) u.cd_blocks_per_sm = t->cd_blocks_per_sm;
@@ -166,6 +168,7 @@ static bool make_tuning(const toposzp_tuning* t, Tuning& u) {
     u.dec_split = t->dec_split;
     u.rank_bitmap = t->rank_bitmap;
     u.cd_columns = t->cd_columns;
+    u.launch_overlap = t->launch_overlap;
     return true;
 }
 
@@ -178,6 +181,7 @@ static void export_tuning(const Tuning& u, toposzp_tuning* t) {
     t->dec_split = u.dec_split;
     t->rank_bitmap = u.rank_bitmap;
     t->cd_columns = u.cd_columns;
+    t->launch_overlap = u.launch_overlap;
 }
 
 
@@ -312,7 +316,7 @@ toposzp_status toposzp_compress(const float* field, int ndim, const uint64_t dim
 
     cudaMemsetAsync(status, 0, sizeof(int32_t), st);
     cudaMemsetAsync(ws, 0, w.os_desc_a, st);   // control block, per-tile counts, sort histograms and counters
-    k_init_ctrl<<<1, 1, 0, st>>>(c, g, mode == TOPOSZP_EB_REL ? 1 : 0, eb, p.flags, (int)p.rs_sweeps, nbf);
+    launch_pdl(k_init_ctrl, dim3(1), dim3(1), 0, st, c, g, mode == TOPOSZP_EB_REL ? 1 : 0, eb, p.flags, (int)p.rs_sweeps, nbf);
     stage(0, st);
     launch_range_cd(field, g, c, labels, topo, sms, st);
     stage(1, st);

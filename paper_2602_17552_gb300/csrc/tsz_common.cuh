@@ -167,6 +167,19 @@ struct Ctrl {
 
 // ------------------------------------------------------------------ helpers
 
+// Programmatic dependent launch: the kernels of the library are launched with
+// programmatic stream serialisation (launch_pdl) and start with
+// griddep_enter(): it lets the next kernel's CTAs be scheduled once all of
+// its own CTAs have started, then waits until every earlier kernel of the
+// stream has completed and its writes are visible.  A launch thus overlaps
+// the previous kernel's tail instead of following it; no memory access moves
+// before the wait.  (Without the launch attribute the wait returns at once.)
+__device__ __forceinline__ void griddep_enter() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+
 __device__ __forceinline__ void set_status(int* st, int code) {
     if (code) atomicCAS(st, 0, code);
 }

@@ -34,6 +34,7 @@ template <bool TOPO, bool COUNTS, bool STATS>
 __global__ void __launch_bounds__(256) k_range_cd(const float* __restrict__ a, const Geo g, Ctrl* c,
                                                   uint32_t* __restrict__ labels,
                                                   unsigned long long* counts) {
+    griddep_enter();
     const int lane = threadIdx.x & 31;
     const uint32_t nchunks = (g.n + 511) / 512;
     const uint32_t nwords = (g.n + 15) / 16;
@@ -182,6 +183,7 @@ template <bool TOPO, bool COUNTS, bool STATS, bool THREE>
 __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ a, const Geo g, Ctrl* c,
                                                       uint32_t* __restrict__ labels,
                                                       unsigned long long* counts) {
+    griddep_enter();
     const int lane = threadIdx.x & 31;
     const uint32_t nchunks = (g.n + 127) / 128;
     const uint32_t warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -314,6 +316,7 @@ constexpr uint32_t CD_ZSEG = 32;
 
 __global__ void __launch_bounds__(256) k_range_cd_col(const float* __restrict__ a, const Geo g, Ctrl* c,
                                                       uint32_t* __restrict__ labels) {
+    griddep_enter();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -391,6 +394,7 @@ __global__ void __launch_bounds__(256) k_range_cd_col(const float* __restrict__ 
 
 // counts[0] = n - (m + s + M)
 __global__ void k_count_regular(uint32_t n, unsigned long long* counts) {
+    griddep_enter();
     counts[0] = (unsigned long long)n - counts[1] - counts[2] - counts[3];
 }
 
@@ -400,6 +404,7 @@ __global__ void k_count_regular(uint32_t n, unsigned long long* counts) {
 // bins of width w = 2h, h = eps - (M + eps) 2^-21 so the binary32 round trip
 // stays within eps; constant fields are coded exactly.
 __global__ void k_qparams(Ctrl* c, int* status) {
+    griddep_enter();
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     if (c->nonfinite) {
         set_status(status, ST_NONFINITE);
@@ -486,6 +491,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
                                                          const uint32_t* __restrict__ labels, Ctrl* c,
                                                          uint2* tcnt, EncOut o, uint2* listM, uint2* listm,
                                                          uint32_t* region, int* status) {
+    griddep_enter();
     __shared__ __align__(16) uint32_t s_buf[ENC_TILE_BLOCKS * ENC_ROW];
     __shared__ uint32_t s_wsum[8][3];
     __shared__ uint32_t s_base[2];
@@ -666,6 +672,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
 template <int ND>
 __global__ void __launch_bounds__(256, 4) k_encode_tiles(const float* __restrict__ a, Ctrl* c, uint2* tcnt,
                                                          EncOut o, int* status) {
+    griddep_enter();
     using TS = TileShape<ND>;
     constexpr uint32_t BX = TS::BX, BY = TS::BY, BZ = TS::BZ;
     __shared__ __align__(16) uint32_t s_buf[TILE_PAY];
@@ -770,6 +777,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_tiles(const float* __restrict
 // consecutive tiles per thread.
 __global__ void __launch_bounds__(1024) k_enc_tile_scan(uint2* tcnt, uint32_t ntiles, Ctrl* c,
                                                         const int* status) {
+    griddep_enter();
     __shared__ unsigned long long s_w[33][2];
     if (*status) return;
     unsigned long long tw, tc;
@@ -806,6 +814,7 @@ __device__ __forceinline__ void copy_slot(const uint32_t* __restrict__ src, uint
 
 __global__ void __launch_bounds__(256) k_enc_copy(const uint32_t* __restrict__ scratch, const uint2* tpre,
                                                   uint32_t ntiles, uint32_t* pay, const int* status) {
+    griddep_enter();
     if (*status) return;
     for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const uint32_t p0 = tpre[t].x, cnt = tpre[t + 1].x - p0;
@@ -821,6 +830,7 @@ __global__ void __launch_bounds__(256) k_enc_copy(const uint32_t* __restrict__ s
 // depend on data-dependent sizes.
 __global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restrict__ delta, Ctrl* c, uint2* tcnt,
                                                          uint32_t* scratch, uint8_t* out, int* status) {
+    griddep_enter();
     __shared__ __align__(16) uint32_t s_buf[ENC_TILE_BLOCKS * ENC_ROW];
     __shared__ uint32_t s_wsum[8];
     if (*status) return;
@@ -916,6 +926,7 @@ __global__ void __launch_bounds__(256, 3) k_encode_ranks(const int32_t* __restri
 
 // Tile prefixes of the rank payload (tiles of the delta sequence); sets rank_words.
 __global__ void __launch_bounds__(1024) k_rank_tile_scan(uint2* tcnt, Ctrl* c, const int* status) {
+    griddep_enter();
     __shared__ unsigned long long s_w[33][2];
     if (*status) return;
     const uint32_t nbd = (uint32_t)cdiv(c->k_total, L);
@@ -934,6 +945,7 @@ __global__ void __launch_bounds__(1024) k_rank_tile_scan(uint2* tcnt, Ctrl* c, c
 // Rank payload slots to the rank payload section (a CTA per tile).
 __global__ void __launch_bounds__(256) k_rank_copy(const uint32_t* __restrict__ scratch, const uint2* tpre,
                                                    const Ctrl* c, uint8_t* out, const int* status) {
+    griddep_enter();
     if (*status) return;
     const uint64_t k = c->k_total;
     const uint32_t nbd = (uint32_t)cdiv(k, L);
@@ -1011,6 +1023,7 @@ __device__ __forceinline__ uint32_t list_count(const Ctrl* c, int list) {
 __global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s1, Ctrl* c,
                                                  uint32_t* ghist /* [2][4][512] */, uint32_t* desc_a,
                                                  uint32_t* desc_b, uint32_t desc_stride, const int* status) {
+    griddep_enter();
     __shared__ uint32_t h[4][4 * OS_ND];
     if (*status || c->rank_bitmap) return;
     const SortPlan sp = sort_plan(c);
@@ -1049,6 +1062,7 @@ __global__ void __launch_bounds__(256) k_os_hist(const uint2* s0, const uint2* s
 // exclusive scan of each digit histogram -> digit bases (a CTA of 512 per row)
 __global__ void __launch_bounds__(512) k_os_bases(const Ctrl* c, const uint32_t* ghist, uint32_t* base,
                                                   const int* status) {
+    griddep_enter();
     __shared__ uint32_t s_w[16];
     if (*status || c->rank_bitmap) return;
     const int row = blockIdx.x;   // list * 4 + pass
@@ -1072,6 +1086,7 @@ __global__ void __launch_bounds__(OS_WARPS * 32, 2) k_os_pass(const uint2* s0, c
                                                  const Ctrl* c, const uint32_t* base, uint32_t* desc,
                                                  uint32_t* desc_next, uint32_t desc_stride, uint32_t* tile_ctr,
                                                  int pass, int* status) {
+    griddep_enter();
     __shared__ uint32_t s_tile;
     __shared__ uint16_t wcnt[OS_WARPS][OS_ND];
     __shared__ uint32_t gofs[OS_ND];
@@ -1248,6 +1263,7 @@ __global__ void __launch_bounds__(256) k_rank_tiles(const uint2* l0, const uint2
                                                     const Ctrl* c,
                                                     uint2* agg, uint32_t agg_stride, int G,
                                                     const int* status) {
+    griddep_enter();
     __shared__ SegCnt s_tot[8];
     if (*status || c->rank_bitmap) return;
     const int list = blockIdx.y;
@@ -1272,6 +1288,7 @@ __global__ void __launch_bounds__(256) k_rank_tiles(const uint2* l0, const uint2
 // pass 2: exclusive scan of tile aggregates (one CTA per list, sequential chunks)
 __global__ void __launch_bounds__(256) k_rank_scan(uint2* agg, uint32_t agg_stride, const Ctrl* c,
                                                    const int* status) {
+    griddep_enter();
     __shared__ SegCnt sh[256];
     if (*status || c->rank_bitmap) return;
     const int list = blockIdx.x;
@@ -1306,6 +1323,7 @@ __global__ void __launch_bounds__(256) k_rank_scatter(const uint2* l0, const uin
                                                       const uint2* t1, const Ctrl* c,
                                                       const uint2* agg, uint32_t agg_stride, const uint2* tpre,
                                                       int32_t* delta, int G, const int* status) {
+    griddep_enter();
     __shared__ SegCnt s_tot[8];
     if (*status || c->rank_bitmap) return;
     const int list = blockIdx.y;
@@ -1353,6 +1371,7 @@ __device__ __forceinline__ void put(uint8_t* h, int off, T v) {
 // qmin)) over the integer codes (exact, order independent).
 __global__ void k_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k_over,
                            float rbf_sigma_over, const int* status) {
+    griddep_enter();
     __shared__ float s_g[9];
     __shared__ float s_sigma;
     __shared__ int32_t s_k;
@@ -1462,19 +1481,19 @@ void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bo
         if (topo && three && g.nxy % 128 == 0 && g_tuning.cd_columns >= 0) {
             const uint32_t work = (g.nxy / 128) * ((g.nz + CD_ZSEG - 1) / CD_ZSEG);   // warps
             const uint32_t cb = hmin<uint32_t>((work + 7) / 8, (uint32_t)sms * 8);
-            k_range_cd_col<<<cb ? cb : 1, 256, 0, st>>>(a, g, c, labels);
+            launch_pdl(k_range_cd_col, dim3(cb ? cb : 1), dim3(256), 0, st, a, g, c, labels);
             return;
         }
-        if (topo && three) k_range_cd_vec<true, false, true, true><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
-        else if (topo) k_range_cd_vec<true, false, true, false><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
-        else k_range_cd_vec<false, false, true, false><<<blocks, th, 0, st>>>(a, g, c, labels, nullptr);
+        if (topo && three) launch_pdl(k_range_cd_vec<true, false, true, true>, dim3(blocks), dim3(th), 0, st, a, g, c, labels, nullptr);
+        else if (topo) launch_pdl(k_range_cd_vec<true, false, true, false>, dim3(blocks), dim3(th), 0, st, a, g, c, labels, nullptr);
+        else launch_pdl(k_range_cd_vec<false, false, true, false>, dim3(blocks), dim3(th), 0, st, a, g, c, labels, nullptr);
         return;
     }
     uint32_t nchunks = (g.n + 511) / 512;
     uint32_t blocks = hmin<uint32_t>((nchunks + 7) / 8, (uint32_t)sms * 8);
     if (blocks == 0) blocks = 1;
-    if (topo) k_range_cd<true, false, true><<<blocks, 256, 0, st>>>(a, g, c, labels, nullptr);
-    else k_range_cd<false, false, true><<<blocks, 256, 0, st>>>(a, g, c, labels, nullptr);
+    if (topo) launch_pdl(k_range_cd<true, false, true>, dim3(blocks), dim3(256), 0, st, a, g, c, labels, nullptr);
+    else launch_pdl(k_range_cd<false, false, true>, dim3(blocks), dim3(256), 0, st, a, g, c, labels, nullptr);
 }
 
 void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsigned long long* counts,
@@ -1483,12 +1502,12 @@ void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsi
         uint32_t blocks = hmin<uint32_t>((g.n / 128 + 7) / 8 + 1, (uint32_t)sms * 8);
         const bool three = g.ndim == 3;
         if (counts) {
-            if (three) k_range_cd_vec<true, true, false, true><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, counts);
-            else k_range_cd_vec<true, true, false, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, counts);
-            k_count_regular<<<1, 1, 0, st>>>(g.n, counts);
+            if (three) launch_pdl(k_range_cd_vec<true, true, false, true>, dim3(blocks), dim3(256), 0, st, a, g, nullptr, labels, counts);
+            else launch_pdl(k_range_cd_vec<true, true, false, false>, dim3(blocks), dim3(256), 0, st, a, g, nullptr, labels, counts);
+            launch_pdl(k_count_regular, dim3(1), dim3(1), 0, st, g.n, counts);
         } else {
-            if (three) k_range_cd_vec<true, false, false, true><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, nullptr);
-            else k_range_cd_vec<true, false, false, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, nullptr);
+            if (three) launch_pdl(k_range_cd_vec<true, false, false, true>, dim3(blocks), dim3(256), 0, st, a, g, nullptr, labels, nullptr);
+            else launch_pdl(k_range_cd_vec<true, false, false, false>, dim3(blocks), dim3(256), 0, st, a, g, nullptr, labels, nullptr);
         }
         return;
     }
@@ -1496,15 +1515,16 @@ void launch_critical_points(const float* a, const Geo& g, uint32_t* labels, unsi
     uint32_t blocks = hmin<uint32_t>((nchunks + 7) / 8, (uint32_t)sms * 8);
     if (blocks == 0) blocks = 1;
     if (counts) {
-        k_range_cd<true, true, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, counts);
-        k_count_regular<<<1, 1, 0, st>>>(g.n, counts);
+        launch_pdl(k_range_cd<true, true, false>, dim3(blocks), dim3(256), 0, st, a, g, nullptr, labels, counts);
+        launch_pdl(k_count_regular, dim3(1), dim3(1), 0, st, g.n, counts);
     } else {
-        k_range_cd<true, false, false><<<blocks, 256, 0, st>>>(a, g, nullptr, labels, nullptr);
+        launch_pdl(k_range_cd<true, false, false>, dim3(blocks), dim3(256), 0, st, a, g, nullptr, labels, nullptr);
     }
 }
 
 // Section III-B error classes between two packed label maps.
 __global__ void k_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsigned long long* out) {
+    griddep_enter();
     __shared__ unsigned long long sh[12];
     if (threadIdx.x < 12) sh[threadIdx.x] = 0;
     __syncthreads();
@@ -1535,10 +1555,10 @@ void launch_topo_errors(const uint32_t* a, const uint32_t* b, uint64_t n, unsign
     uint64_t nwords = (n + 15) / 16;
     uint32_t blocks = (uint32_t)hmin<uint64_t>((nwords + 255) / 256, (uint64_t)sms * 4);
     if (blocks == 0) blocks = 1;
-    k_topo_errors<<<blocks, 256, 0, st>>>(a, b, n, out12);
+    launch_pdl(k_topo_errors, dim3(blocks), dim3(256), 0, st, a, b, n, out12);
 }
 
-void launch_qparams(Ctrl* c, int* status, cudaStream_t st) { k_qparams<<<1, 32, 0, st>>>(c, status); }
+void launch_qparams(Ctrl* c, int* status, cudaStream_t st) { launch_pdl(k_qparams, dim3(1), dim3(32), 0, st, c, status); }
 
 __global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsigned long long region_bytes,
                                                  unsigned long long slot_bytes, int mode, const int* status);
@@ -1555,21 +1575,21 @@ void launch_encode_field(const float* a, const uint32_t* labels, Ctrl* c, uint2*
     if (topo) {
         // the rank mode (key bitmaps or sort) is decided here, so the encoder can set the bits
         const unsigned long long slot_bytes = 4ull * TILE_PAY * ntiles;
-        k_bm_zero<<<(uint32_t)sms * 8, 256, 0, st>>>(c, scratch, region_bytes, slot_bytes, g_tuning.rank_bitmap,
+        launch_pdl(k_bm_zero, dim3((uint32_t)sms * 8), dim3(256), 0, st, c, scratch, region_bytes, slot_bytes, g_tuning.rank_bitmap,
                                                       status);
-        if (tiles) k_encode_field<true, false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
-        else k_encode_field<true, true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+        if (tiles) launch_pdl(k_encode_field<true, false>, dim3(ntiles), dim3(256), 0, st, a, labels, c, tcnt, o, listM, listm, scratch, status);
+        else launch_pdl(k_encode_field<true, true>, dim3(ntiles), dim3(256), 0, st, a, labels, c, tcnt, o, listM, listm, scratch, status);
     } else {
-        if (tiles) k_encode_field<false, false><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
-        else k_encode_field<false, true><<<ntiles, 256, 0, st>>>(a, labels, c, tcnt, o, listM, listm, scratch, status);
+        if (tiles) launch_pdl(k_encode_field<false, false>, dim3(ntiles), dim3(256), 0, st, a, labels, c, tcnt, o, listM, listm, scratch, status);
+        else launch_pdl(k_encode_field<false, true>, dim3(ntiles), dim3(256), 0, st, a, labels, c, tcnt, o, listM, listm, scratch, status);
     }
     if (tiles) {
-        if (g.ndim == 3) k_encode_tiles<3><<<ntiles, 256, 0, st>>>(a, c, tcnt, o, status);
-        else k_encode_tiles<2><<<ntiles, 256, 0, st>>>(a, c, tcnt, o, status);
+        if (g.ndim == 3) launch_pdl(k_encode_tiles<3>, dim3(ntiles), dim3(256), 0, st, a, c, tcnt, o, status);
+        else launch_pdl(k_encode_tiles<2>, dim3(ntiles), dim3(256), 0, st, a, c, tcnt, o, status);
     }
-    k_enc_tile_scan<<<SCAN_SLICES, 1024, 0, st>>>(tcnt, ntiles, c, status);
+    launch_pdl(k_enc_tile_scan, dim3(SCAN_SLICES), dim3(1024), 0, st, tcnt, ntiles, c, status);
     uint32_t cg = hmin<uint32_t>(ntiles, (uint32_t)sms * 8);
-    k_enc_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, ntiles, reinterpret_cast<uint32_t*>(out + lo.s5),
+    launch_pdl(k_enc_copy, dim3(cg ? cg : 1), dim3(256), 0, st, scratch, tcnt, ntiles, reinterpret_cast<uint32_t*>(out + lo.s5),
                                             status);
 }
 
@@ -1599,6 +1619,7 @@ __device__ __forceinline__ int32_t key_bin(uint32_t key, int list, float r) {
 // mode: < 0 the sort, 0 bitmaps and bin table when they fit, 1 no bin table.
 __global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsigned long long region_bytes,
                                                  unsigned long long slot_bytes, int mode, const int* status) {
+    griddep_enter();
     if (*status) return;
     const SortPlan sp = sort_plan(c);
     const uint32_t kmax = c->max_key, kmin = ~c->min_inv;
@@ -1629,6 +1650,7 @@ __global__ void __launch_bounds__(256) k_bm_zero(Ctrl* c, uint32_t* region, unsi
 // popcount of every BM_CHUNK-word chunk of both bitmaps
 __global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region, uint32_t* csum,
                                                  const int* status) {
+    griddep_enter();
     __shared__ uint32_t s_w[8];
     if (*status || !c->rank_bitmap) return;
     const uint32_t W = c->bm_words, nch = (W + BM_CHUNK - 1) / BM_CHUNK;
@@ -1662,6 +1684,7 @@ __global__ void __launch_bounds__(256) k_bm_sums(Ctrl* c, const uint32_t* region
 // the chunk sums (csum) before it.
 __global__ void __launch_bounds__(1024) k_bm_prefix(Ctrl* c, uint32_t* region, const uint32_t* csum,
                                                     const int* status) {
+    griddep_enter();
     __shared__ uint32_t s_o[32], s_wt[32];
     if (*status || !c->rank_bitmap) return;
     const uint32_t W = c->bm_words, nch = (W + BM_CHUNK - 1) / BM_CHUNK;
@@ -1763,6 +1786,7 @@ __device__ __forceinline__ uint32_t bin_first(int32_t q, uint32_t hi, uint32_t b
 
 // P(lo) of every bin of the field's range, both lists: table[list * bin_n + q - bin_q0]
 __global__ void __launch_bounds__(256) k_bin_table(Ctrl* c, uint32_t* region, const int* status) {
+    griddep_enter();
     if (*status || !c->rank_bitmap || !c->bin_n) return;
     const SortPlan sp = sort_plan(c);
     const uint32_t W = c->bm_words, nb = c->bin_n;
@@ -1782,6 +1806,7 @@ __global__ void __launch_bounds__(256) k_bin_table(Ctrl* c, uint32_t* region, co
 __global__ void __launch_bounds__(256) k_rank_delta(const uint2* s0, const uint2* s1, Ctrl* c,
                                                     const uint32_t* region, const uint2* tpre, int32_t* delta,
                                                     const int* status) {
+    griddep_enter();
     if (*status || !c->rank_bitmap) return;
     const SortPlan sp = sort_plan(c);
     const uint32_t W = c->bm_words, nb = c->bin_n;
@@ -1833,21 +1858,21 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
     uint32_t* region = reinterpret_cast<uint32_t*>(tmpM);
     uint32_t* csum = reinterpret_cast<uint32_t*>(agg);
     const uint32_t bg = (uint32_t)sms * 8;
-    k_bm_sums<<<bg, 256, 0, st>>>(c, region, csum, status);
-    k_bm_prefix<<<(uint32_t)sms * 2, 1024, 0, st>>>(c, region, csum, status);
-    k_bin_table<<<(uint32_t)sms * 2, 256, 0, st>>>(c, region, status);
-    k_rank_delta<<<dim3(bg, 2), 256, 0, st>>>(listM, listm, c, region, tpre, delta, status);
+    launch_pdl(k_bm_sums, dim3(bg), dim3(256), 0, st, c, region, csum, status);
+    launch_pdl(k_bm_prefix, dim3((uint32_t)sms * 2), dim3(1024), 0, st, c, region, csum, status);
+    launch_pdl(k_bin_table, dim3((uint32_t)sms * 2), dim3(256), 0, st, c, region, status);
+    launch_pdl(k_rank_delta, dim3(bg, 2), dim3(256), 0, st, listM, listm, c, region, tpre, delta, status);
     const uint32_t max_tiles = sw.max_tiles;
     uint32_t hg = hmin<uint32_t>((uint32_t)cdiv((uint64_t)max_tiles * OS_TILE, 256), (uint32_t)sms * 4);
     if (hg == 0) hg = 1;
-    k_os_hist<<<dim3(hg, 2), 256, 0, st>>>(listM, listm, c, sw.hist, sw.desc_a, sw.desc_b, sw.stride, status);
-    k_os_bases<<<8, OS_ND, 0, st>>>(c, sw.hist, sw.base, status);
+    launch_pdl(k_os_hist, dim3(hg, 2), dim3(256), 0, st, listM, listm, c, sw.hist, sw.desc_a, sw.desc_b, sw.stride, status);
+    launch_pdl(k_os_bases, dim3(8), dim3(OS_ND), 0, st, c, sw.hist, sw.base, status);
     uint2 *a0 = listM, *a1 = listm, *b0 = tmpM, *b1 = tmpm;
     const uint32_t pg = hmin<uint32_t>(max_tiles, (uint32_t)sms * 4);
     for (int pass = 0; pass < 4; pass++) {
         uint32_t* cur = (pass & 1) ? sw.desc_b : sw.desc_a;
         uint32_t* nxt = (pass & 1) ? sw.desc_a : sw.desc_b;
-        k_os_pass<<<dim3(pg ? pg : 1, 2), OS_WARPS * 32, 0, st>>>(a0, a1, b0, b1, c, sw.base, cur, nxt, sw.stride,
+        launch_pdl(k_os_pass, dim3(pg ? pg : 1, 2), dim3(OS_WARPS * 32), 0, st, a0, a1, b0, b1, c, sw.base, cur, nxt, sw.stride,
                                                          sw.ctr + 2 * pass, pass, status);
         uint2* t0 = a0; a0 = b0; b0 = t0;
         uint2* t1 = a1; a1 = b1; b1 = t1;
@@ -1855,9 +1880,9 @@ void launch_ranks(Ctrl* c, uint2* listM, uint2* listm, uint2* tmpM, uint2* tmpm,
     // the sorted lists are in listM / listm after an even number of passes,
     // in tmpM / tmpm after an odd one (the kernels read the count)
     dim3 grid(G, 2);
-    k_rank_tiles<<<grid, 256, 0, st>>>(listM, listm, tmpM, tmpm, c, agg, agg_stride, G, status);
-    k_rank_scan<<<2, 256, 0, st>>>(agg, agg_stride, c, status);
-    k_rank_scatter<<<grid, 256, 0, st>>>(listM, listm, tmpM, tmpm, c, agg, agg_stride, tpre, delta, G, status);
+    launch_pdl(k_rank_tiles, dim3(grid), dim3(256), 0, st, listM, listm, tmpM, tmpm, c, agg, agg_stride, G, status);
+    launch_pdl(k_rank_scan, dim3(2), dim3(256), 0, st, agg, agg_stride, c, status);
+    launch_pdl(k_rank_scatter, dim3(grid), dim3(256), 0, st, listM, listm, tmpM, tmpm, c, agg, agg_stride, tpre, delta, G, status);
 }
 
 void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* scratch, uint8_t* out,
@@ -1865,15 +1890,15 @@ void launch_encode_ranks(const int32_t* delta, Ctrl* c, uint2* tcnt, uint32_t* s
     const uint32_t max_tiles = (uint32_t)cdiv(cdiv(max_k, L), ENC_TILE_BLOCKS);
     uint32_t grid = hmin<uint32_t>(max_tiles, (uint32_t)sms * 3);
     if (grid == 0) grid = 1;
-    k_encode_ranks<<<grid, 256, 0, st>>>(delta, c, tcnt, scratch, out, status);
-    k_rank_tile_scan<<<SCAN_SLICES, 1024, 0, st>>>(tcnt, c, status);
+    launch_pdl(k_encode_ranks, dim3(grid), dim3(256), 0, st, delta, c, tcnt, scratch, out, status);
+    launch_pdl(k_rank_tile_scan, dim3(SCAN_SLICES), dim3(1024), 0, st, tcnt, c, status);
     uint32_t cg = hmin<uint32_t>(max_tiles, (uint32_t)sms * 8);
-    k_rank_copy<<<cg ? cg : 1, 256, 0, st>>>(scratch, tcnt, c, out, status);
+    launch_pdl(k_rank_copy, dim3(cg ? cg : 1), dim3(256), 0, st, scratch, tcnt, c, out, status);
 }
 
 void launch_finalize(Ctrl* c, uint8_t* out, uint64_t* out_size, int32_t rbf_k, float rbf_sigma,
                      int* status, cudaStream_t st) {
-    k_finalize<<<1, 32, 0, st>>>(c, out, out_size, rbf_k, rbf_sigma, status);
+    launch_pdl(k_finalize, dim3(1), dim3(32), 0, st, c, out, out_size, rbf_k, rbf_sigma, status);
 }
 
 }  // namespace tsz

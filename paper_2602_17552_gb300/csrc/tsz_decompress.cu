@@ -220,6 +220,7 @@ constexpr int RBF_SOLVE_SMEM = (RBF_MAX_NODES * RBF_MAX_NODES + 2 * RBF_MAX_NODE
 
 __global__ void __launch_bounds__(256) k_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out,
                                                       Ctrl* c, int* status, uint32_t test_hold) {
+    griddep_enter();
     extern __shared__ double sm_solve[];
     __shared__ int s_solve;
     if (threadIdx.x == 0) {
@@ -258,6 +259,7 @@ __device__ __forceinline__ int32_t decode_block(const uint32_t* pay, unsigned lo
 __global__ void __launch_bounds__(256, 3) k_decode_ranks(const uint8_t* __restrict__ in, Ctrl* c,
                                                          const uint32_t* rpre, int32_t* __restrict__ delta,
                                                          int* status) {
+    griddep_enter();
     __shared__ __align__(16) uint32_t s_buf[DT_BLOCKS * 36];
     __shared__ uint32_t s_w[8];
     if (*status || (c->flags & FLAG_NO_TOPO)) return;
@@ -832,6 +834,7 @@ __device__ __forceinline__ bool saddle_candidate_rec_any(int ndim, int r, const 
 __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict__ in, Ctrl* c,
                                                        uint32_t* tile_w, uint32_t* tile_c, uint32_t* rtile_w,
                                                        int* status) {
+    griddep_enter();
     // per-slice sums of this CTA's tiles (field words, extrema; rank words),
     // added to the control block once per slice at the end
     __shared__ unsigned long long s_sl[SCAN_SLICES][3];
@@ -910,6 +913,7 @@ __global__ void __launch_bounds__(256) k_dec_tile_sums(const uint8_t* __restrict
 __global__ void __launch_bounds__(1024) k_dec_tile_scan(Ctrl* c, const uint32_t* tile_w, const uint32_t* tile_c,
                                                         unsigned long long* pay_pre, uint32_t* cp_pre,
                                                         uint32_t* rtile_w, int* status) {
+    griddep_enter();
     __shared__ unsigned long long s_w[33][2];
     if (*status) return;
     const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
@@ -1452,6 +1456,7 @@ __device__ void fused_body(const FusedArgs& A, FusedSmem& S) {
 }
 
 __global__ void __launch_bounds__(256, 4) k_decode_fused(FusedArgs A) {
+    griddep_enter();
     __shared__ FusedSmem S;
     if (*A.status) return;
     if (A.c->flags & FLAG_NO_TOPO) fused_body<false>(A, S);
@@ -1462,6 +1467,7 @@ __global__ void __launch_bounds__(256, 4) k_decode_fused(FusedArgs A) {
 // kernel boundaries order the stages, so there are no waits).
 template <int K>
 __global__ void __launch_bounds__(256, 4) k_decode_stage(FusedArgs A) {
+    griddep_enter();
     __shared__ FusedSmem S;
     if (*A.status) return;
     Ctrl* c = A.c;
@@ -1627,6 +1633,7 @@ __device__ void tiles_cp_list(const uint8_t* in, const Ctrl* c, const Geo& g, co
 __global__ void __launch_bounds__(256) k_decode_tiles(const uint8_t* __restrict__ in, Ctrl* c, float* out,
                                                       const unsigned long long* pay_pre, const uint32_t* cp_pre,
                                                       uint32_t* cp_idx, int* status) {
+    griddep_enter();
     __shared__ __align__(16) uint32_t s_pay[DT_BLOCKS * 33];
     __shared__ uint32_t s_w[DT_WARPS], s_cp[DT_WARPS];
     if (*status || !(c->flags & FLAG_TILE_BLOCKS)) return;
@@ -1652,6 +1659,8 @@ __global__ void __launch_bounds__(1024, 1) k_saddle_rounds(const uint8_t* __rest
                                                        const uint32_t* sad, uint32_t* sadb, float* sadv,
                                                        uint32_t sad_cap, uint32_t* rec, uint32_t rec_cap,
                                                        int* status) {
+    // a cooperative launch, without programmatic serialisation: it starts
+    // after the previous kernel has completed, so it needs no griddep_enter()
     __shared__ RbfTable T;
     __shared__ uint32_t s_cnt[8], s_base[8];
     cg::grid_group grid = cg::this_grid();
@@ -1757,7 +1766,7 @@ void launch_parse_header(const uint8_t* in, uint64_t in_size, uint64_t n_out, Ct
         cudaFuncSetAttribute(k_parse_header, cudaFuncAttributeMaxDynamicSharedMemorySize, RBF_SOLVE_SMEM);
         if (dev >= 0 && dev < 64) attr_set[dev] = true;
     }
-    k_parse_header<<<1, 256, RBF_SOLVE_SMEM, st>>>(in, in_size, n_out, c, status, test_hold);
+    launch_pdl(k_parse_header, dim3(1), dim3(256), RBF_SOLVE_SMEM, st, in, in_size, n_out, c, status, test_hold);
 }
 
 void launch_decode_tiles(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
@@ -1765,14 +1774,14 @@ void launch_decode_tiles(const uint8_t* in, Ctrl* c, float* out, const unsigned 
                          cudaStream_t st) {
     // a format-v2 stream has at most n blocks; the CTAs step over the tiles
     const uint32_t grid = (uint32_t)hmax<uint64_t>(1, hmin<uint64_t>(cdiv(n, DT_BLOCKS), (uint64_t)sms * 8));
-    k_decode_tiles<<<grid, 256, 0, st>>>(in, c, out, pay_pre, cp_pre, cp_idx, status);
+    launch_pdl(k_decode_tiles, dim3(grid), dim3(256), 0, st, in, c, out, pay_pre, cp_pre, cp_idx, status);
 }
 
 void launch_decode_ranks(const uint8_t* in, Ctrl* c, const uint32_t* rpre, int32_t* delta, uint64_t max_k,
                          int sms, int* status, cudaStream_t st) {
     uint32_t grid = hmin<uint32_t>((uint32_t)cdiv(cdiv(max_k, L), DT_BLOCKS), (uint32_t)sms * 3);
     if (grid == 0) grid = 1;
-    k_decode_ranks<<<grid, 256, 0, st>>>(in, c, rpre, delta, status);
+    launch_pdl(k_decode_ranks, dim3(grid), dim3(256), 0, st, in, c, rpre, delta, status);
 }
 
 void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* tile_c,
@@ -1780,8 +1789,8 @@ void launch_dec_offsets(const uint8_t* in, Ctrl* c, uint32_t* tile_w, uint32_t* 
                         int* status, cudaStream_t st) {
     uint32_t blocks = hmin<uint32_t>((ntiles + 7) / 8, (uint32_t)sms * 8);
     if (blocks == 0) blocks = 1;
-    k_dec_tile_sums<<<blocks, 256, 0, st>>>(in, c, tile_w, tile_c, rtile_w, status);
-    k_dec_tile_scan<<<SCAN_SLICES, 1024, 0, st>>>(c, tile_w, tile_c, pay_pre, cp_pre, rtile_w, status);
+    launch_pdl(k_dec_tile_sums, dim3(blocks), dim3(256), 0, st, in, c, tile_w, tile_c, rtile_w, status);
+    launch_pdl(k_dec_tile_scan, dim3(SCAN_SLICES), dim3(1024), 0, st, c, tile_w, tile_c, pay_pre, cp_pre, rtile_w, status);
 }
 
 void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned long long* pay_pre,
@@ -1803,14 +1812,14 @@ void launch_decode_fused(const uint8_t* in, Ctrl* c, float* out, const unsigned 
     // started earlier, so any residency makes progress.
     if (g_tuning.dec_split > 0) {
         const uint32_t sg = hmin<uint32_t>(ntiles_dec, (uint32_t)(fit * sms) * 4u);
-        k_decode_stage<1><<<sg, 256, 0, st>>>(A);
-        k_decode_stage<2><<<sg, 256, 0, st>>>(A);
-        k_decode_stage<3><<<sg, 256, 0, st>>>(A);
-        k_decode_stage<4><<<sg, 256, 0, st>>>(A);
+        launch_pdl(k_decode_stage<1>, dim3(sg), dim3(256), 0, st, A);
+        launch_pdl(k_decode_stage<2>, dim3(sg), dim3(256), 0, st, A);
+        launch_pdl(k_decode_stage<3>, dim3(sg), dim3(256), 0, st, A);
+        launch_pdl(k_decode_stage<4>, dim3(sg), dim3(256), 0, st, A);
         return;
     }
     const uint32_t grid = ntiles_dec + 3 * hmin<uint32_t>(ntiles_dec, h_bound + slack);
-    k_decode_fused<<<grid, 256, 0, st>>>(A);
+    launch_pdl(k_decode_fused, dim3(grid), dim3(256), 0, st, A);
 }
 
 cudaError_t launch_saddle_rounds(const uint8_t* in, Ctrl* c, float* out, const uint32_t* sad, uint32_t* sadb,

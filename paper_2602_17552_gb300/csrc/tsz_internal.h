@@ -17,8 +17,35 @@ struct Tuning {
     int dec_split = 0;              // > 0: the decoder stages as separate launches instead of fused
     int rank_bitmap = 0;            // 0: key bitmaps (+ bin table) when they fit; 1: no bin table; < 0: the sort
     int cd_columns = 0;             // 0: z-column pass for 3D fields when the planes allow; < 0: never
+    int launch_overlap = 0;         // 0: programmatic dependent launches; < 0: plain stream ordering
 };
 extern Tuning g_tuning;
+
+// Launch with programmatic stream serialisation (griddep_enter() in
+// tsz_common.cuh).  A stream being captured into a graph, and every launch
+// while the launch_overlap tuning is negative, get plain launches (full
+// stream ordering).  The attribute relaxes only the ordering after a
+// preceding kernel: after a memset or an event wait the launch waits for it
+// as usual.  Errors also surface through cudaGetLastError, like those of a
+// <<<>>> launch.
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const bool plain = g_tuning.launch_overlap < 0 || cudaStreamIsCapturing(st, &cs) != cudaSuccess ||
+                       cs != cudaStreamCaptureStatusNone;
+    cfg.attrs = at;
+    cfg.numAttrs = plain ? 0 : 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<P>(args)...);
+}
 
 // ---- workspace carving (all offsets 256-byte aligned)
 struct CompressWs {

@@ -175,16 +175,18 @@ def test_tuning_classes_on_host(lib):
     base = _lib.Tuning()
     assert lib.toposzp_get_tuning(3, d(128, 128, 128), ctypes.byref(base)) == _lib.OK
     try:
-        t.cd_threads, t.cd_blocks_per_sm, t.dec_split = 512, 4, 1
+        t.cd_threads, t.cd_blocks_per_sm, t.dec_split, t.launch_overlap = 512, 4, 1, -1
         assert lib.toposzp_set_tuning_class(3, 2, ctypes.byref(t)) == _lib.OK
         got = _lib.Tuning()
         assert lib.toposzp_get_tuning(3, d(128, 128, 128), ctypes.byref(got)) == _lib.OK
-        assert (got.cd_threads, got.cd_blocks_per_sm, got.dec_split) == (512, 4, 1)
+        assert (got.cd_threads, got.cd_blocks_per_sm, got.dec_split, got.launch_overlap) == (512, 4, 1, -1)
         assert lib.toposzp_get_tuning(2, d(2000, 2000), ctypes.byref(got)) == _lib.OK   # the 2D row is untouched
         assert lib.toposzp_set_tuning_class(3, 2, None) == _lib.OK
         assert lib.toposzp_get_tuning(3, d(128, 128, 128), ctypes.byref(got)) == _lib.OK
         assert got.cd_threads != 512 or base.cd_threads == 512
-        t.cd_threads = 100
+        t.launch_overlap = 1
+        assert lib.toposzp_set_tuning_class(3, 1, ctypes.byref(t)) == _lib.INVALID_ARG
+        t.launch_overlap, t.cd_threads = 0, 100
         assert lib.toposzp_set_tuning_class(3, 1, ctypes.byref(t)) == _lib.INVALID_ARG
         assert lib.toposzp_set_tuning_class(4, 1, None) == _lib.INVALID_ARG
         assert lib.toposzp_set_tuning_class(2, 4, None) == _lib.INVALID_ARG

@@ -77,11 +77,13 @@ def test_launch_tuning_never_changes_bits():
     f2 = synth.climate_2d(300, 640, seed=6, device="cuda")
     want = [codec.compress(f, 1e-3, "rel") for f in (f3, f2)]
     try:
-        for th, bps, rb, sl, rec, sp, bm, col in ((128, 4, 1, 1, -1, 0, -1, -1), (512, 16, 2, 5000, 1, 1, 0, 0),
-                                                  (256, 32, 4, 37, -1, 1, 1, -1)):
+        for th, bps, rb, sl, rec, sp, bm, col, lo in ((128, 4, 1, 1, -1, 0, -1, -1, -1),
+                                                      (512, 16, 2, 5000, 1, 1, 0, 0, 0),
+                                                      (256, 32, 4, 37, -1, 1, 1, -1, 0),
+                                                      (256, 8, 1, 0, 0, 0, 0, 0, -1)):
             autotune.apply({"cd_threads": th, "cd_blocks_per_sm": bps, "rounds_blocks_per_sm": rb,
                             "dec_slack_tiles": sl, "saddle_records": rec, "dec_split": sp, "rank_bitmap": bm,
-                            "cd_columns": col})
+                            "cd_columns": col, "launch_overlap": lo})
             for f, w in zip((f3, f2), want):
                 got = codec.compress(f, 1e-3, "rel")
                 assert torch.equal(got, w)
