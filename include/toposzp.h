@@ -224,7 +224,9 @@ uint64_t toposzp_noalloc_max_points(void);
  *                        without that table; -1: always the radix sort
  *   cd_columns           0: the range + CD pass of 3D fields walks z-columns
  *                        when each plane is a whole number of 128-point
- *                        chunks (default); -1: never
+ *                        chunks and the columns, cut into segments of 4 to
+ *                        32 planes, give at least 24 warps per SM (default);
+ *                        1: whenever the planes allow; -1: never
  *   launch_overlap       0: each kernel is launched as a programmatic
  *                        dependent of the one before it on the stream, so
  *                        that its CTAs are scheduled while that one ends and

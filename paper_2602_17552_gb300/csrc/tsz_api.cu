@@ -157,7 +157,7 @@ static bool make_tuning(const toposzp_tuning* t, Tuning& u) {
     if (t->saddle_records < -1 || t->saddle_records > 1) return false;
     if (t->dec_split < 0 || t->dec_split > 1) return false;
     if (t->rank_bitmap < -1 || t->rank_bitmap > 1) return false;
-    if (t->cd_columns < -1 || t->cd_columns > 0) return false;
+    if (t->cd_columns < -1 || t->cd_columns > 1) return false;
     if (t->launch_overlap < -1 || t->launch_overlap > 0) return false;
     u = Tuning();
     if (t->cd_threads) u.cd_threads = t->cd_threads;

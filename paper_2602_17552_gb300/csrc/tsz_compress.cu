@@ -308,19 +308,21 @@ __global__ void __launch_bounds__(512) k_range_cd_vec(const float* __restrict__ 
 }
 
 // The compression pass for 3D fields whose planes hold a whole number of
-// 128-point chunks: a warp walks one chunk position down z (a segment of
-// CD_ZSEG planes) and keeps the rows z-1, z, z+1 in registers, so each value
-// comes from DRAM about once (the y-neighbour rows are the neighbouring
-// warps' rows, read from L2).  Same results as k_range_cd_vec.
-constexpr uint32_t CD_ZSEG = 32;
+// 128-point chunks: a warp walks one chunk position down z (a segment of zseg
+// planes) and keeps the rows z-1, z, z+1 in registers, so each value comes
+// from DRAM about once (the y-neighbour rows are the neighbouring warps'
+// rows, read from L2).  Same results as k_range_cd_vec.  The segment is
+// CD_ZSEG planes, shorter when the field has too few columns to give every
+// SM enough warps (each segment reads two planes more than it labels).
+constexpr uint32_t CD_ZSEG = 32, CD_ZSEG_MIN = 4;
 
 __global__ void __launch_bounds__(256) k_range_cd_col(const float* __restrict__ a, const Geo g, Ctrl* c,
-                                                      uint32_t* __restrict__ labels) {
+                                                      uint32_t* __restrict__ labels, uint32_t zseg) {
     griddep_enter();
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    const uint32_t ncols = g.nxy / 128, nsegs = (g.nz + CD_ZSEG - 1) / CD_ZSEG;
+    const uint32_t ncols = g.nxy / 128, nsegs = (g.nz + zseg - 1) / zseg;
     float vmin = __int_as_float(0x7F800000), vmax = __int_as_float(0xFF800000);
     float fin = 0.0f;   // sum of (v - v): +0 while every value is finite, NaN after an inf or NaN
     uint32_t cs = 0;
@@ -331,7 +333,7 @@ __global__ void __launch_bounds__(256) k_range_cd_col(const float* __restrict__ 
         const uint32_t t = fdiv(p0, g.fx);
         const uint32_t x = p0 - t * g.nx, y = t;       // one plane: t < ny
         const bool xl = x > 0, xr = x + 4 < g.nx, yin = y > 0 && y + 1 < g.ny;
-        const uint32_t z0 = seg * CD_ZSEG, z1 = min(g.nz, z0 + CD_ZSEG);
+        const uint32_t z0 = seg * zseg, z1 = min(g.nz, z0 + zseg);
         const float4* a4 = reinterpret_cast<const float4*>(a);
         float4 prev = make_float4(0.f, 0.f, 0.f, 0.f);
         if (z0 > 0) prev = __ldg(a4 + ((size_t)(z0 - 1) * g.nxy + p0) / 4);
@@ -1478,10 +1480,18 @@ void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bo
         uint32_t blocks = hmin<uint32_t>((g.n / 128 + per_cta_chunks - 1) / per_cta_chunks + 1,
                                          (uint32_t)sms * (uint32_t)g_tuning.cd_blocks_per_sm);
         const bool three = g.ndim == 3;
-        if (topo && three && g.nxy % 128 == 0 && g_tuning.cd_columns >= 0) {
-            const uint32_t work = (g.nxy / 128) * ((g.nz + CD_ZSEG - 1) / CD_ZSEG);   // warps
+        // column segments: at least 48 warps per SM, else (few, short columns)
+        // the chunk kernel below, whose n/128 warps are more (cd_columns = 1
+        // keeps the column pass there too)
+        const uint32_t ncols = g.nxy / 128, want = (uint32_t)sms * 48u;
+        uint32_t zseg = CD_ZSEG;
+        if ((uint64_t)ncols * ((g.nz + zseg - 1) / zseg) < want)
+            zseg = hmax<uint32_t>(CD_ZSEG_MIN, (uint32_t)(((uint64_t)g.nz * ncols + want - 1) / want));
+        const uint32_t work = ncols * ((g.nz + zseg - 1) / zseg);   // warps
+        if (topo && three && g.nxy % 128 == 0 && g_tuning.cd_columns >= 0 &&
+            (g_tuning.cd_columns > 0 || 2 * work >= want)) {
             const uint32_t cb = hmin<uint32_t>((work + 7) / 8, (uint32_t)sms * 8);
-            launch_pdl(k_range_cd_col, dim3(cb ? cb : 1), dim3(256), 0, st, a, g, c, labels);
+            launch_pdl(k_range_cd_col, dim3(cb ? cb : 1), dim3(256), 0, st, a, g, c, labels, zseg);
             return;
         }
         if (topo && three) launch_pdl(k_range_cd_vec<true, false, true, true>, dim3(blocks), dim3(th), 0, st, a, g, c, labels, nullptr);

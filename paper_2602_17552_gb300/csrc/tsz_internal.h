@@ -16,7 +16,7 @@ struct Tuning {
     int saddle_records = 0;         // >= 0: neighbourhood records in the saddle rounds; < 0: field reads
     int dec_split = 0;              // > 0: the decoder stages as separate launches instead of fused
     int rank_bitmap = 0;            // 0: key bitmaps (+ bin table) when they fit; 1: no bin table; < 0: the sort
-    int cd_columns = 0;             // 0: z-column pass for 3D fields when the planes allow; < 0: never
+    int cd_columns = 0;             // 0: z-column pass when the planes and its warp count allow; 1: when the planes allow; < 0: never
     int launch_overlap = 0;         // 0: programmatic dependent launches; < 0: plain stream ordering
 };
 extern Tuning g_tuning;

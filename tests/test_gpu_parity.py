@@ -91,6 +91,30 @@ def test_parity_degenerate_shapes(shape):
     assert_parity(a, 0.3, rel=False)
 
 
+@pytest.mark.parametrize("shape", [(5, 8, 16), (40, 16, 32), (70, 4, 64), (45, 32, 64), (3, 2, 64)])
+def test_parity_column_pass_forced(shape):
+    """cd_columns = 1: the z-column pass on fields whose columns are too few
+    for the default to take it (4-plane segments, the last one ragged)."""
+    from paper_2602_17552_gb300 import autotune
+    rng = np.random.default_rng(sum(shape) + 1)
+    a = rng.integers(-4, 5, size=shape).astype(np.float32) * np.float32(0.25)
+    b = np.exp(synth.grf(shape, -11 / 3, 7).numpy()) if min(shape) > 2 else a
+    try:
+        autotune.apply({"cd_columns": 1})
+        assert_parity(a, 1e-2, rel=True)
+        assert_parity(b, 1e-3, rel=True)
+    finally:
+        autotune.restore()
+
+
+@pytest.mark.parametrize("shape", [(128, 128, 128), (30, 256, 256)])
+def test_parity_column_pass_short_segments(shape):
+    """Default tuning on fields with few columns: the column pass with 4-plane
+    segments (30 planes: the last segment has 2)."""
+    a = np.exp(synth.grf(shape, -11 / 3, 8).numpy())
+    assert_parity(a, 1e-3, rel=True)
+
+
 def test_parity_constant_and_tiny_range():
     assert_parity(np.full((37, 41), -2.5, np.float32), 1e-3, rel=True)
     assert_parity(np.zeros((9, 10, 11), np.float32), 1e-3, rel=True)
