@@ -612,6 +612,16 @@ __host__ __device__ inline bool rec_supported(int ndim, int r) {
     return ndim == 3 ? (r == 1 || r == 2) : (r >= 1 && r <= 3);
 }
 
+constexpr uint32_t REC_W31 = RecStencil<3, 1>{}.words(), REC_W32 = RecStencil<3, 2>{}.words();
+constexpr uint32_t REC_W21 = RecStencil<2, 1>{}.words(), REC_W22 = RecStencil<2, 2>{}.words();
+constexpr uint32_t REC_W23 = RecStencil<2, 3>{}.words();
+// words of one record of a supported kind (at most REC_MAX_WORDS): the
+// records are packed at this stride, so that they fill whole sectors
+__host__ __device__ inline uint32_t rec_words(int ndim, int r) {
+    if (ndim == 3) return r == 1 ? REC_W31 : REC_W32;
+    return r == 1 ? REC_W21 : r == 2 ? REC_W22 : REC_W23;
+}
+
 // Candidates whose whole RBF neighbourhood and both face rings lie inside the
 // grid: their record has every slot (no bounds checks when it is gathered).
 __device__ __forceinline__ bool rec_inside(const Geo& g, int r, uint32_t x, uint32_t y, uint32_t z) {
@@ -1701,7 +1711,7 @@ __global__ void __launch_bounds__(1024, 1) k_saddle_rounds(const uint8_t* __rest
     // records (uniform across the grid): when the kind has them and they fit
     const int r = c->rbf_k / 2;
     const bool use_rec = rec_cap > 0 && ns <= rec_cap && rec_supported(g.ndim, r);
-    const uint32_t RW = REC_MAX_WORDS;
+    const uint32_t RW = use_rec ? rec_words(g.ndim, r) : REC_MAX_WORDS;   // rec_cap counts REC_MAX_WORDS each
     for (uint32_t j = tid; j < ns; j += nth) {
         const uint32_t p = sad[j];
         uint32_t x, y, z;
