@@ -53,7 +53,7 @@ KERNEL_SOURCES = {
     "k_encode_field": ("tsz_compress.cu", "tsz_common.cuh"),
     "k_range_cd": ("tsz_compress.cu", "tsz_common.cuh"),
 }
-E2E_IN_FLIGHT = int(os.environ.get("TOPOSZP_E2E_IN_FLIGHT", "4"))   # round trips in flight at once
+E2E_IN_FLIGHT = int(os.environ.get("TOPOSZP_E2E_IN_FLIGHT", "8"))   # round trips in flight at once
 
 
 def parse_args():
@@ -75,7 +75,9 @@ def parse_args():
     ap.add_argument("--eb", type=float, default=1e-3)
     ap.add_argument("--side", type=int, default=512, help="edge of the 3D turbulence field")
     ap.add_argument("--no-topo", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=9)
+    ap.add_argument("--e2e-steps", type=int, default=48,
+                    help="round trips per timed end-to-end sequence (long enough that filling and "
+                         "draining the in-flight pipeline is a small part of it)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="target CPU-baseline work")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
