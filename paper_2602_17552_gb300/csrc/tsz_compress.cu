@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
     __shared__ __align__(16) uint32_t s_buf[ENC_TILE_BLOCKS * ENC_ROW];
     __shared__ uint32_t s_wsum[8][3];
     __shared__ uint32_t s_base[2];
+    __shared__ uint32_t s_ext[8][2];
     __shared__ unsigned long long s_sum;
     if (*status) return;
     const uint32_t n = c->g.n, nb = c->g.nb;
@@ -526,7 +527,34 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
     }
     uint2 lw = make_uint2(0u, 0u);
     if (TOPO && b < nb) lw = reinterpret_cast<const uint2*>(labels)[b];
+    uint32_t xmM = 0, xmm = 0;   // extremum masks (bit e: element e), maxima / minima
+    if (TOPO) {
+        const uint32_t lo0 = lw.x & 0x55555555u, hi0 = (lw.x >> 1) & 0x55555555u;
+        const uint32_t lo1 = lw.y & 0x55555555u, hi1 = (lw.y >> 1) & 0x55555555u;
+        const uint32_t valid = b < nb ? (n - b * 32u >= 32u ? FULL : (1u << (n - b * 32u)) - 1u) : 0u;
+        xmM = (compact16(lo0 & hi0) | compact16(lo1 & hi1) << 16) & valid;    // M = 11
+        xmm = (compact16(lo0 & ~hi0) | compact16(lo1 & ~hi1) << 16) & valid;  // m = 01
+        // the tile's extremum counts are known from the labels alone: their list
+        // ranges are reserved now, so that the atomics' round trip overlaps the
+        // block codec instead of holding the whole CTA later
+        const uint32_t cMw = __reduce_add_sync(FULL, __popc(xmM)), cmw = __reduce_add_sync(FULL, __popc(xmm));
+        if (lane == 0) {
+            s_ext[warp][0] = cMw;
+            s_ext[warp][1] = cmw;
+        }
+    }
     __syncthreads();
+    uint32_t r_base0 = 0, r_base1 = 0;   // thread 0: the reserved list offsets, stored before the scan
+    if (TOPO && t == 0) {
+        uint32_t eM = 0, em = 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            eM += s_ext[k][0];
+            em += s_ext[k][1];
+        }
+        r_base0 = eM ? atomicAdd(&c->cnt_max, eM) : 0u;
+        r_base1 = em ? atomicAdd(&c->cnt_min, em) : 0u;
+    }
     // ---- this thread's block: codes, residuals, width, sign plane
     uint32_t m[32];
     uint32_t sgn = 0, orr = 0, sum = 0;
@@ -557,13 +585,9 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
     const uint32_t w = 32u - __clz(orr);   // bit length of max |d|
     const uint32_t W = __reduce_max_sync(FULL, w);   // the warp's widest block: picks the transpose
     const uint32_t words = (CODEC && b < nb && w) ? 1u + w : 0u;
-    uint32_t xmM = 0, xmm = 0;   // extremum masks (bit e: element e), maxima / minima
-    if (TOPO) {
-        const uint32_t lo0 = lw.x & 0x55555555u, hi0 = (lw.x >> 1) & 0x55555555u;
-        const uint32_t lo1 = lw.y & 0x55555555u, hi1 = (lw.y >> 1) & 0x55555555u;
-        const uint32_t valid = b < nb ? (n - b * 32u >= 32u ? FULL : (1u << (n - b * 32u)) - 1u) : 0u;
-        xmM = (compact16(lo0 & hi0) | compact16(lo1 & hi1) << 16) & valid;    // M = 11
-        xmm = (compact16(lo0 & ~hi0) | compact16(lo1 & ~hi1) << 16) & valid;  // m = 01
+    if (TOPO && t == 0) {   // read after the scan's barrier
+        s_base[0] = r_base0;
+        s_base[1] = r_base1;
     }
     // ---- exclusive prefixes over the tile's blocks: payload words, maxima, minima
     uint32_t iw = words, iM = __popc(xmM), im = __popc(xmm);
@@ -596,14 +620,9 @@ __global__ void __launch_bounds__(256, 4) k_encode_field(const float* __restrict
         unsigned long long* sl = c->sl_tile[tile / slice_len(gridDim.x)];
         if (tw) atomicAdd(sl, (unsigned long long)tw);
         if (tM + tm) atomicAdd(sl + 1, (unsigned long long)(tM + tm));
-        if (TOPO) {
-            s_base[0] = tM ? atomicAdd(&c->cnt_max, tM) : 0u;
-            s_base[1] = tm ? atomicAdd(&c->cnt_min, tm) : 0u;
-        }
         if (s_sum) atomicAdd(&c->sum_abs, s_sum);
     }
     if (TOPO) {
-        __syncthreads();
         // (key, position) pairs of this block's extrema, in index order; with
         // the bitmap ranks also each key's bit in its list's bitmap
         const uint32_t* row = s_buf + t * ENC_ROW;
