@@ -46,7 +46,7 @@ typedef enum {
     TOPOSZP_ERR_CORRUPT_STREAM = 5,  /* header / section / payload inconsistent */
     TOPOSZP_ERR_TIMEOUT = 6,         /* a bounded device wait gave up */
     TOPOSZP_ERR_CUDA = 7,            /* a CUDA launch or copy failed */
-    TOPOSZP_ERR_UNSUPPORTED = 8      /* outside this build's limits (n >= 2^31) */
+    TOPOSZP_ERR_UNSUPPORTED = 8      /* outside the library's limits (n >= 2^31) */
 } toposzp_status;
 
 typedef enum {

@@ -494,7 +494,7 @@ def test_rbf_parameters_grow_with_smoothness():
     to rough (Gaussian random fields with flatter and flatter spectra, then
     white noise) neither may grow; a gentle ramp takes the largest kernel and
     white noise the smallest kernel and sigma.  (The thresholds themselves
-    are this build's choice: the paper gives none.)"""
+    are the implementation's choice: the paper gives none.)"""
     ramp = (np.arange(1024, dtype=np.float64)[None, :] / 1024 +
             np.arange(64, dtype=np.float64)[:, None] / 640).astype(np.float32)
     fields = [ramp] + [synth.grf((128, 128), s, 7).numpy() for s in (-8, -4, -3, -2, -1)]

@@ -62,7 +62,7 @@ def test_noalloc_rejects_fields_over_the_limit():
 
 
 def test_noalloc_status_split_matches_the_workspace_entry_point():
-    """Nonzero dims too large for this build are UNSUPPORTED, as in
+    """Nonzero dims too large for the library are UNSUPPORTED, as in
     toposzp_compress; zero dims or a bad ndim are INVALID_ARG.  The dims are
     checked on the host before anything touches the (small) buffers."""
     L = _lib.load()
