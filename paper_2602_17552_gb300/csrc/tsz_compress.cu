@@ -1509,7 +1509,9 @@ void launch_range_cd(const float* a, const Geo& g, Ctrl* c, uint32_t* labels, bo
         const uint32_t work = ncols * ((g.nz + zseg - 1) / zseg);   // warps
         if (topo && three && g.nxy % 128 == 0 && g_tuning.cd_columns >= 0 &&
             (g_tuning.cd_columns > 0 || 2 * work >= want)) {
-            const uint32_t cb = hmin<uint32_t>((work + 7) / 8, (uint32_t)sms * 8);
+            // 16 CTAs per SM (four waves of the four that fit at 60 registers):
+            // shorter tails than one or two waves
+            const uint32_t cb = hmin<uint32_t>((work + 7) / 8, (uint32_t)sms * 16);
             launch_pdl(k_range_cd_col, dim3(cb ? cb : 1), dim3(256), 0, st, a, g, c, labels, zseg);
             return;
         }
